@@ -1,0 +1,336 @@
+"""FP64 CPU oracle for the spectral split-step Pade (SSSP) range marcher.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports this module:
+only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import or call it.  It shares
+no code with the CUDA path (no kernels, headers, tables or helpers).
+
+Every function is a plain, slow, obviously-correct restatement of the paper
+(Walsken, Ehrhardt, Petrov, "A Spectral Split-Step Pade Method for Guided Wave
+Propagation"), in complex128:
+
+* Section 2: the propagator P = exp(i h sqrt(d_z^2 + k^2)) and its [p/p] Pade
+  approximation in the sum form e^{ik0h}(d0 + sum_j d_j/(1 + b_j X)), with
+  X = (k^2 - k0^2 + d_z^2)/k0^2 = V + d_z^2/k0^2, V = n^2 - 1; Eq. (1dhelmholtz)
+  defines w_j by (1 + b_j X) w_j = u.
+* Section 3: the isovelocity inverse L_j^{-1} applied diagonally after a
+  discrete trigonometric transform (Eq. inverse_isovel; here the DST-I of the
+  Dirichlet case of Section 3.1), and the Neumann series Eq. (Neumann) for the
+  depth-dependent perturbation.
+* Algorithm 1 (SSSP): per range step, w_j for every Pade term, then
+  u_n = e^{ihk0}(d0 u_{n-1} + sum_j d_j w_j).
+
+The Pade coefficients are the definition of the [p/p] approximant (Baker's
+linear system for the denominator, then the numerator) solved with a library
+linear solve and polynomial root finder.  The DST-I is the explicit O(N^2) sine
+sum.  Readings of the paper where it is silent or garbled:
+
+* N is the number of interior depth points, dz = H/(N+1), z_n = n dz;
+* the isovelocity multiplier is 1/(1 + b_j lambda_m) with the continuous
+  eigenvalue lambda_m = -(pi m/(k0 H))^2 of d_z^2/k0^2 under Dirichlet BCs;
+* Algorithm 1's sums run over j = 1..p plus the d0 u term;
+* the Neumann series for w_j stops after term m >= 1 once
+  ||t_m||_2 <= tol * ||w_j||_2 (w_j including t_m) or when ``terms`` terms
+  (m = 0..terms-1) have been summed; terms <= 1 keeps only t_0 (V ignored);
+* the step r -> r + dr uses the profile node in force at the step midpoint
+  (the last node whose range is <= r + dr/2);
+* TL = -20 log10|u| + 10 log10(r / 1 m).
+
+Pins (tests/test_oracle_pins.py) tie each function to mathematics other than
+itself: mpmath's own Pade, the exact propagator by eigendecomposition, dense
+LU solves, closed-form sine modes, scipy's DST-I and norm conservation.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+
+# ----------------------------------------------------------------------------
+# Pade approximant of f(X) = exp(i sigma (sqrt(1+X) - 1))      (Section 2)
+# ----------------------------------------------------------------------------
+def taylor_coeffs(sigma: float, order: int) -> np.ndarray:
+    """Taylor coefficients c_0..c_order of f(X) = exp(i sigma (sqrt(1+X) - 1)) at X = 0.
+
+    g(X) = sqrt(1+X) - 1 = sum_{k>=1} binom(1/2, k) X^k, and f = exp(h) with
+    h = i sigma g obeys f' = h' f, i.e. k f_k = sum_{j=1..k} j h_j f_{k-j}.
+    """
+    g = np.zeros(order + 1, dtype=np.float64)
+    if order >= 1:
+        g[1] = 0.5
+    for k in range(1, order):
+        g[k + 1] = g[k] * (0.5 - k) / (k + 1)
+    h = 1j * sigma * g
+    f = np.zeros(order + 1, dtype=np.complex128)
+    f[0] = 1.0
+    for k in range(1, order + 1):
+        f[k] = sum(j * h[j] * f[k - j] for j in range(1, k + 1)) / k
+    return f
+
+
+@dataclasses.dataclass
+class PadePlan:
+    """[p/p] Pade data of exp(i sigma (sqrt(1+X) - 1)).
+
+    q, pc: ascending coefficients of Q (q[0] = 1) and P.
+    b, a : Q(X) = prod_j (1 + b_j X), P(X) = P(0) prod_j (1 + a_j X).
+    d0, d: sum form P/Q = d0 + sum_j d_j / (1 + b_j X).
+    """
+    sigma: float
+    p: int
+    q: np.ndarray
+    pc: np.ndarray
+    b: np.ndarray
+    a: np.ndarray
+    d0: complex
+    d: np.ndarray
+
+    def rational(self, x) -> np.ndarray:
+        """P(x)/Q(x) evaluated directly from the polynomial coefficients."""
+        x = np.asarray(x, dtype=np.complex128)
+        return np.polyval(self.pc[::-1], x) / np.polyval(self.q[::-1], x)
+
+    def sum_form(self, x) -> np.ndarray:
+        x = np.asarray(x, dtype=np.complex128)
+        out = np.full(x.shape, self.d0, dtype=np.complex128)
+        for bj, dj in zip(self.b, self.d):
+            out = out + dj / (1.0 + bj * x)
+        return out
+
+    def product_form(self, x) -> np.ndarray:
+        x = np.asarray(x, dtype=np.complex128)
+        out = np.full(x.shape, self.pc[0], dtype=np.complex128)
+        for aj, bj in zip(self.a, self.b):
+            out = out * (1.0 + aj * x) / (1.0 + bj * x)
+        return out
+
+
+def pade_plan(sigma: float, p: int) -> PadePlan:
+    """[p/p] Pade approximant (Section 2; coefficients 'according to Baker').
+
+    Q = 1 + q_1 X + .. + q_p X^p and P = p_0 + .. + p_p X^p with Q f - P = O(X^{2p+1}):
+    the rows k = p+1..2p give sum_{i=1..p} q_i c_{k-i} = -c_k, then p_k = sum_{i<=k} q_i c_{k-i}.
+    """
+    c = taylor_coeffs(sigma, 2 * p)
+    M = np.array([[c[k - i] for i in range(1, p + 1)] for k in range(p + 1, 2 * p + 1)], dtype=np.complex128)
+    rhs = -c[p + 1:2 * p + 1]
+    q = np.concatenate([[1.0 + 0j], np.linalg.solve(M, rhs)])
+    pc = np.array([sum(q[i] * c[k - i] for i in range(0, k + 1)) for k in range(p + 1)], dtype=np.complex128)
+    # Q(X) = prod (1 + b_j X): roots X_j = -1/b_j.  np.roots wants highest degree first.
+    b = -1.0 / np.roots(q[::-1])
+    a = -1.0 / np.roots(pc[::-1])
+    d0 = pc[p] / q[p]
+    d = np.empty(p, dtype=np.complex128)
+    for j in range(p):
+        Pval = np.polyval(pc[::-1], -1.0 / b[j])
+        den = np.prod([1.0 - b[l] / b[j] for l in range(p) if l != j])
+        d[j] = Pval / den
+    return PadePlan(sigma=sigma, p=p, q=q, pc=pc, b=b, a=a, d0=complex(d0), d=d)
+
+
+# ----------------------------------------------------------------------------
+# DST-I and the isovelocity operator                        (Section 3, 3.1)
+# ----------------------------------------------------------------------------
+_SINE_CACHE = {}
+
+
+def sine_matrix(N: int) -> np.ndarray:
+    """S[m-1, n-1] = sin(pi n m / (N+1)), n, m = 1..N (argument reduced exactly mod 2(N+1))."""
+    if N not in _SINE_CACHE:
+        L = N + 1
+        idx = np.arange(1, N + 1, dtype=np.int64)
+        nm = np.outer(idx, idx) % (2 * L)
+        _SINE_CACHE.clear()
+        _SINE_CACHE[N] = np.sin(np.pi * nm.astype(np.float64) / L)
+    return _SINE_CACHE[N]
+
+
+def dst1(x: np.ndarray) -> np.ndarray:
+    """DST-I along axis 0: X_m = sum_{n=1..N} x_n sin(pi n m/(N+1)), by the explicit sine sum."""
+    x = np.asarray(x)
+    N = x.shape[0]
+    if N <= 16383:
+        S = sine_matrix(N)
+        return S @ x.real + 1j * (S @ x.imag) if np.iscomplexobj(x) else S @ x
+    # large N: rows of the sine matrix in blocks
+    L = N + 1
+    idx = np.arange(1, N + 1, dtype=np.int64)
+    out = np.empty(x.shape, dtype=np.complex128 if np.iscomplexobj(x) else np.float64)
+    for s in range(0, N, 1024):
+        rows = idx[s:s + 1024]
+        Sb = np.sin(np.pi * (np.outer(rows, idx) % (2 * L)).astype(np.float64) / L)
+        out[s:s + 1024] = Sb @ x.real + 1j * (Sb @ x.imag) if np.iscomplexobj(x) else Sb @ x
+    return out
+
+
+def idst1(X: np.ndarray) -> np.ndarray:
+    """Inverse DST-I: x = (2/(N+1)) DST-I(X)."""
+    return (2.0 / (X.shape[0] + 1)) * dst1(X)
+
+
+def lambdas(N: int, H: float, k0: float) -> np.ndarray:
+    """Eigenvalues of d_z^2/k0^2 on sin(pi m z/H): lambda_m = -(pi m/(k0 H))^2, m = 1..N."""
+    m = np.arange(1, N + 1, dtype=np.float64)
+    return -(np.pi * m / (k0 * H)) ** 2
+
+
+def apply_Linv(x: np.ndarray, bj, lam: np.ndarray) -> np.ndarray:
+    """L_j^{-1} x = IDST[ DST[x] / (1 + b_j lambda) ]   (Eq. inverse_isovel, DST-I version).
+
+    ``bj`` may be a scalar or a row of p values (x then has p columns)."""
+    X = dst1(x)
+    if X.ndim == 1:
+        return idst1(X / (1.0 + bj * lam))
+    return idst1(X / (1.0 + np.asarray(bj)[None, :] * lam[:, None]))
+
+
+# ----------------------------------------------------------------------------
+# Neumann series and the SSSP step                     (Eq. Neumann, Algorithm 1)
+# ----------------------------------------------------------------------------
+def neumann_w(u: np.ndarray, V: np.ndarray, b: np.ndarray, lam: np.ndarray, terms: int, tol: float,
+              return_counts: bool = False):
+    """w_j = sum_{m=0..M} (-b_j L_j^{-1} V)^m L_j^{-1} u for every j (columns), Eq. (Neumann).
+
+    ``u`` is one field (N,) used by every j (sum form) or a matrix (N, p) of per-j inputs.
+    Term m >= 1 is t_m = -b_j L_j^{-1}(V t_{m-1}); column j stops after term m once
+    ||t_m|| <= tol ||w_j||, or after ``terms`` terms in all.
+    """
+    b = np.asarray(b, dtype=np.complex128)
+    p = b.shape[0]
+    U = np.repeat(u[:, None], p, axis=1) if u.ndim == 1 else u
+    t = apply_Linv(U, b, lam)
+    w = t.copy()
+    counts = np.ones(p, dtype=np.int64)
+    active = np.ones(p, dtype=bool)
+    for m in range(1, max(terms, 1)):
+        if not active.any():
+            break
+        t = -b[None, :] * apply_Linv(V[:, None] * t, b, lam)
+        t[:, ~active] = 0.0
+        w = w + t
+        counts[active] += 1
+        tn = np.linalg.norm(t, axis=0)
+        wn = np.linalg.norm(w, axis=0)
+        active &= ~(tn <= tol * wn)
+    return (w, counts) if return_counts else w
+
+
+@dataclasses.dataclass
+class Grid:
+    N: int
+    H: float
+    k0: float
+    dr: float
+
+    @property
+    def sigma(self) -> float:
+        return self.k0 * self.dr
+
+    @property
+    def lam(self) -> np.ndarray:
+        return lambdas(self.N, self.H, self.k0)
+
+
+def step_sum(u: np.ndarray, V: np.ndarray, grid: Grid, plan: PadePlan, terms: int, tol: float) -> np.ndarray:
+    """One SSSP range step in the paper's sum form (Algorithm 1):
+    u_n = e^{i k0 dr} (d0 u + sum_j d_j w_j)."""
+    w = neumann_w(u, V, plan.b, grid.lam, terms, tol)
+    return np.exp(1j * grid.sigma) * (plan.d0 * u + w @ plan.d)
+
+
+def step_product(u: np.ndarray, V: np.ndarray, grid: Grid, plan: PadePlan, terms: int, tol: float) -> np.ndarray:
+    """The same step in Collins' product form prod_j (1 + a_j X)(1 + b_j X)^{-1}: stage j maps
+    y -> (a_j/b_j) y + (1 - a_j/b_j) w_j with (1 + b_j X) w_j = y; then u_n = e^{i k0 dr} P(0) y."""
+    y = u.astype(np.complex128)
+    for aj, bj in zip(plan.a, plan.b):
+        w = neumann_w(y, V, np.array([bj]), grid.lam, terms, tol)[:, 0]
+        y = (aj / bj) * y + (1.0 - aj / bj) * w
+    return np.exp(1j * grid.sigma) * plan.pc[0] * y
+
+
+def profile_at(profiles: Sequence[Tuple[float, np.ndarray]], r_mid: float) -> np.ndarray:
+    """n^2 of the last profile node whose range is <= r_mid (the first node if none is)."""
+    chosen = profiles[0][1]
+    for rn, n2 in profiles:
+        if rn <= r_mid:
+            chosen = n2
+        else:
+            break
+    return np.asarray(chosen)
+
+
+def transmission_loss(u: np.ndarray, r: float) -> np.ndarray:
+    """TL = -20 log10|u| + 10 log10(r / 1 m)  [dB]."""
+    with np.errstate(divide="ignore"):
+        return -20.0 * np.log10(np.abs(u)) + 10.0 * np.log10(r)
+
+
+@dataclasses.dataclass
+class MarchResult:
+    u: np.ndarray                 # field after the last step (full field, carrier included)
+    r: float                      # range of u
+    tl: np.ndarray                # (records, N) TL rows
+    tl_ranges: np.ndarray         # range of each TL row
+
+
+def march(u0: np.ndarray, profiles, grid: Grid, pade_order: int, steps: int, terms: int, tol: float,
+          r0: float = 0.0, form: str = "sum", tl_every: int = 1, plan: Optional[PadePlan] = None,
+          record_steps: Optional[Sequence[int]] = None) -> MarchResult:
+    """Algorithm 1: march u0 from range r0 over ``steps`` steps of dr.
+
+    The step from r to r + dr uses V = n^2 - 1 of the node in force at r + dr/2.  TL is
+    recorded after every ``tl_every``-th step (tl_every = 0: never); ``record_steps``
+    overrides that with an explicit list of 1-based step numbers.
+    """
+    plan = plan or pade_plan(grid.sigma, pade_order)
+    stepper = step_sum if form == "sum" else step_product
+    u = np.asarray(u0, dtype=np.complex128).copy()
+    r = r0
+    tls, trs = [], []
+    rec = set(record_steps) if record_steps is not None else None
+    for n in range(1, steps + 1):
+        V = profile_at(profiles, r + 0.5 * grid.dr) - 1.0
+        u = stepper(u, V, grid, plan, terms if terms > 1 else 1, tol)
+        r = r0 + n * grid.dr
+        want = (n in rec) if rec is not None else (tl_every > 0 and n % tl_every == 0)
+        if want:
+            tls.append(transmission_loss(u, r))
+            trs.append(r)
+    tl = np.array(tls) if tls else np.zeros((0, u.shape[0]))
+    return MarchResult(u=u, r=r, tl=tl, tl_ranges=np.array(trs))
+
+
+# ----------------------------------------------------------------------------
+# dense brute force (tiny N only)
+# ----------------------------------------------------------------------------
+def dense_X(grid: Grid, V: np.ndarray) -> np.ndarray:
+    """X = S^{-1} diag(lambda) S + diag(V) as a dense N x N matrix (S the DST-I matrix)."""
+    S = sine_matrix(grid.N)
+    Sinv = (2.0 / (grid.N + 1)) * S
+    return Sinv @ np.diag(grid.lam) @ S + np.diag(np.asarray(V, dtype=np.complex128))
+
+
+def dense_pade_step(X: np.ndarray, plan: PadePlan, form: str = "product") -> np.ndarray:
+    """e^{i sigma} times the Pade operator as a dense matrix, each (I + b_j X)^{-1} by LU."""
+    N = X.shape[0]
+    I = np.eye(N, dtype=np.complex128)
+    if form == "product":
+        Op = plan.pc[0] * I
+        for aj, bj in zip(plan.a, plan.b):
+            Op = (I + aj * X) @ np.linalg.solve(I + bj * X, Op)
+    else:
+        Op = plan.d0 * I
+        for bj, dj in zip(plan.b, plan.d):
+            Op = Op + dj * np.linalg.solve(I + bj * X, I)
+    return np.exp(1j * plan.sigma) * Op
+
+
+def exact_propagator(X: np.ndarray, sigma: float) -> np.ndarray:
+    """exp(i sigma sqrt(I + X)) for Hermitian X by eigendecomposition (principal root;
+    eigenvalues below -1 give evanescent, decaying factors)."""
+    ev, Q = np.linalg.eigh(X)
+    root = np.sqrt((1.0 + ev).astype(np.complex128))
+    return (Q * np.exp(1j * sigma * root)[None, :]) @ Q.conj().T
