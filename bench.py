@@ -1,0 +1,313 @@
+"""Benchmark of the GB300 SSSP marcher on the range-independent Munk workload.
+
+Workload (one solve): Munk deep-ocean guide, H = 5000 m, f = 50 Hz, source at 1000 m,
+N = 4095 interior DST-I points, dr = 50 m, 2000 range steps (100 km), [6/6] Pade, Neumann
+series to 1e-10 or 12 terms, TL recorded after every step.  One bench step = one whole
+2000-range-step march of that solve (set the starter, march, TL rows in HBM).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line.  ``--impl reference`` times the FP64 CPU oracle on a bounded sample of
+the same workload (the reference arm of this comparison).  Under torchrun (N > 1) every rank
+marches its own copy of the solve (independent replicas, weak scaling, no collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "depth-pt·range-steps/s at ≤0.1 dB TL error vs plain path; served p50/p99 latency"
+UNIT = "depth-pt·range-steps/s"
+WORKLOAD = "munk_n4095_f50_dr50_s2000_p6_neumann12"
+
+
+def _rank_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _config(extra=None):
+    c = {"workload": WORKLOAD, "N": 4095, "H_m": 5000.0, "freq_hz": 50.0, "dr_m": 50.0, "range_steps": 2000,
+         "pade_order": 6, "neumann_terms": 12, "neumann_tol": 1e-10, "tl_every": 1, "solves_per_gpu": 1,
+         "l2": "flushed between timed iterations (256 MiB write)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            a = [x.strip() for x in ln.split(",")]
+            if len(a) < 9:
+                continue
+            try:
+                sm.append(float(a[1]))
+                mx.append(float(a[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if a[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dst_flops(N):
+    L = N + 1
+    return 5.0 * L * math.log2(L)
+
+
+def run_cpu_oracle_sample(seconds=15.0):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the workload: the first
+    range steps of the same Munk march, extrapolated as depth-pt*steps per second."""
+    import numpy as np  # noqa: F401
+    from oracle import sssp_oracle as O
+    from paper_2511_03343_gb300 import inputs
+    s = inputs.munk()
+    g = O.Grid(N=s.N, H=s.H, k0=s.k0, dr=s.dr)
+    plan = O.pade_plan(g.sigma, s.pade_order)
+    O.march(s.u0, s.profiles, g, s.pade_order, 1, s.neumann_terms, s.neumann_tol, tl_every=1, plan=plan)  # warm
+    t0 = time.perf_counter()
+    O.march(s.u0, s.profiles, g, s.pade_order, 1, s.neumann_terms, s.neumann_tol, tl_every=1, plan=plan)
+    one = time.perf_counter() - t0
+    steps = max(1, min(s.steps, int(seconds / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    O.march(s.u0, s.profiles, g, s.pade_order, steps, s.neumann_terms, s.neumann_tol, tl_every=1, plan=plan)
+    el = time.perf_counter() - t0
+    return {"value": s.N * steps / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"first {steps} of {s.steps} range steps of the N=4095 Munk march (FP64, sum form, "
+                      f"direct O(N^2) DST-I via BLAS), {el:.1f} s"}
+
+
+def bench_reference(args):
+    rank, world, _ = _rank_env()
+    if rank != 0:
+        return
+    from oracle import sssp_oracle as O
+    from paper_2511_03343_gb300 import inputs
+    s = inputs.munk()
+    g = O.Grid(N=s.N, H=s.H, k0=s.k0, dr=s.dr)
+    plan = O.pade_plan(g.sigma, s.pade_order)
+    sample_steps = args.ref_sample_steps
+    times = []
+    u = s.u0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.march(u, s.profiles, g, s.pade_order, sample_steps, s.neumann_terms, s.neumann_tol, tl_every=1, plan=plan)
+        el = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(el)
+    tot = sum(times)
+    value = s.N * sample_steps * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": _config({"reference_sample_range_steps": sample_steps}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"each step: {sample_steps} of the 2000 range steps of the N=4095 Munk "
+                                       f"march (FP64 oracle, sum form, direct O(N^2) DST-I)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _golden_check(tl, u):
+    """TL / field error of the bench's own output against the stored FP64 oracle run."""
+    import importlib.util
+    import numpy as np
+    p = os.path.join(ROOT, "tests", "golden", "make_golden.py")
+    if not os.path.exists(os.path.join(ROOT, "tests", "golden", "munk_n4095_s2000.txt")):
+        return None
+    spec = importlib.util.spec_from_file_location("make_golden", p)
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    meta, fidx, fref, tl_r, tl_ref = mg.load()
+    every = int(meta["tl_every"])
+    rows = tl[every - 1::every][:, ::int(meta["tl_stride"])].astype(np.float64)
+    mask = tl_ref < 100
+    return {"max_tl_err_db": float(np.max(np.abs(rows - tl_ref)[mask])),
+            "field_rel_l2_sampled": float(np.linalg.norm(u[fidx] - fref) / np.linalg.norm(fref)),
+            "against": "stored FP64 oracle run (tests/golden/munk_n4095_s2000.txt)"}
+
+
+def bench_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = _rank_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2511_03343_gb300 import build as B
+    B.build()
+    from paper_2511_03343_gb300 import inputs, sssp
+    s = inputs.munk()
+    stream = torch.cuda.current_stream()
+    pl = sssp.Plan(s.N, s.H, s.k0, s.dr, s.pade_order, s.neumann_terms, s.neumann_tol, stream=stream)
+    pl.set_output(1)
+    pl.set_profile_nodes(s.profiles)
+    u0_dev = torch.from_numpy(s.u0.astype(np.complex64)).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    per_launch_dst = []
+
+    def one_step(ev=None):
+        pl.set_field(u0_dev, 0.0)
+        c0 = None
+        if ev is not None:
+            ev[0].record(stream)
+        pl.march(s.steps)
+        if ev is not None:
+            ev[1].record(stream)
+        return c0
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    nd0 = pl.transform_count()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms, kern_ms = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[2].record(stream)
+        one_step(e)
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e[2].elapsed_time(e[3]))
+        kern_ms.append(e[0].elapsed_time(e[1]))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    nd1 = pl.transform_count()
+    dst_per_launch = (nd1 - nd0) / args.steps
+    tot_ms = sum(step_ms)
+    # max over ranks
+    if world > 1:
+        t = torch.tensor([tot_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    units = s.N * s.steps * args.steps * world
+    value = units / (tot_ms * 1e-3)
+    # parity of the bench's own output
+    tl, _ = pl.read_tl()
+    u = pl.read_field()
+    parity = _golden_check(tl, u)
+
+    # end to end through the public API with host (pinned) buffers
+    u0_host = torch.from_numpy(s.u0.astype(np.complex64)).pin_memory()
+    tl_host = torch.empty(s.steps * s.N, dtype=torch.float32).pin_memory()
+    field_host = torch.empty(s.N, dtype=torch.complex64).pin_memory()
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pl.set_field(u0_host, 0.0)
+        pl.march(s.steps)
+        pl.read_tl(out=tl_host)
+        pl.read_field(out=field_host)
+        el = time.perf_counter() - t0
+        if i >= args.warmup:
+            e2e_ms.append(el * 1e3)
+    e2e_tot = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_tot], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_tot = float(t.item())
+
+    # roofline of the dominant kernel (the fused march kernel, FP32 ALU bound)
+    kern_avg = sum(kern_ms) / len(kern_ms)
+    N = s.N
+    diag = 10.0 * (N + 1)  # per transform: the diagonal multiplies around it
+    flops = dst_per_launch * (_dst_flops(N) + diag)
+    achieved = flops / (kern_avg * 1e-3) / 1e12
+    sm_max = float(clk.get("sm_max_mhz") or 2070.0)
+    peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flop x max SM clock
+    line = None
+    if rank == 0:
+        cpu = run_cpu_oracle_sample(args.cpu_seconds) if (world == 1 and not args.no_cpu) else None
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+                "config": _config(),
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "traffic": None,
+                             "kernel": "sssp_march_kernel<12> (one CTA, one SM)",
+                             "flops_per_launch": flops, "dst_per_launch": dst_per_launch,
+                             "kernel_ms": kern_avg,
+                             "peak_note": "FP32 FMA peak of all 152 SMs at the sampled max SM clock (derived, not measured)"},
+                "e2e": {"value": s.N * s.steps * args.steps * world / (e2e_tot * 1e-3), "unit": UNIT,
+                        "h2d_bytes_per_step": s.N * 8, "d2h_bytes_per_step": s.N * s.steps * 4 + s.N * 8},
+                "gpu_launches": 2 * args.steps,
+                "clocks": clk, "parity": parity, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    pl.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-sample-steps", type=int, default=10)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

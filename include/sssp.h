@@ -1,0 +1,184 @@
+/*
+ * sssp.h — C ABI of the GB300 spectral split-step Pade (SSSP) range marcher.
+ *
+ * The library advances the complex depth field u(r, z) of the wide-angle parabolic
+ * equation  d_r u = i sqrt(d_z^2 + k^2) u  (Section 2, Eq. PDPE) range step by range
+ * step with the [p/p] Pade propagator
+ *     u(r + dr) = e^{i k0 dr} prod_j (1 + a_j X)(1 + b_j X)^{-1} u,
+ *     X = (d_z^2 + k^2 - k0^2)/k0^2 = d_z^2/k0^2 + V(z),  V = n^2 - 1,
+ * (Section 2; the product form equals the paper's sum form d0 + sum_j d_j/(1 + b_j X)).
+ * Each (1 + b_j X)^{-1} is applied spectrally (Section 3): a DST-I (homogeneous
+ * Dirichlet boundaries at z = 0 and z = H, Section 3.1) diagonalises d_z^2 with
+ * eigenvalues lambda_m = -(pi m/(k0 H))^2, and a depth-dependent V is handled by the
+ * Neumann series of Eq. (Neumann), one forward and one inverse DST-I per term.
+ * Algorithm 1 is the per-step loop that pe_march runs on the GPU.
+ *
+ * Conventions
+ *  - Grid: N interior points z_n = n H/(N+1), n = 1..N.  N + 1 must be a power of two
+ *    in [8, 4096] for this build.  Fields are N complex64 values stored as interleaved
+ *    float pairs (re, im), index n-1 for z_n.
+ *  - Every function returns a pe_status; PE_OK is 0.  On failure the plan (if any) keeps
+ *    a message readable with pe_last_error().  No C++ exception crosses this boundary.
+ *  - The library owns all device memory it allocates (in pe_plan_create and when
+ *    profile / TL storage grows); pe_plan_destroy frees it.  Caller buffers are only
+ *    read or written during the call (device copies are ordered on the plan's stream
+ *    and complete before functions that return data to the host return).
+ *  - A plan is not thread-safe.  All device work of a plan is ordered on its CUDA
+ *    stream (the stream given at creation, NULL = legacy default stream).
+ */
+#ifndef SSSP_H_
+#define SSSP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pe_plan pe_plan;
+
+typedef enum {
+  PE_OK = 0,
+  PE_ERR_ARG = 1,               /* invalid argument or unsupported size                  */
+  PE_ERR_CUDA = 2,              /* a CUDA runtime call failed (message holds the error)   */
+  PE_ERR_OOM = 3,               /* device allocation failed                              */
+  PE_ERR_NEUMANN_DIVERGED = 4,  /* Neumann term norms grew for 3 consecutive terms        */
+  PE_ERR_TIMEOUT = 5,           /* a bounded device wait expired                         */
+  PE_ERR_STATE = 6,             /* call out of order (e.g. march before set_field)        */
+  PE_ERR_NUMERIC = 7            /* a non-finite value appeared in the march               */
+} pe_status;
+
+/* ABI revision; bumped when a signature changes. */
+int pe_abi_version(void);
+
+/*
+ * Create a plan.  Section 2 (Pade [p/p] of exp(i sigma (sqrt(1+X) - 1)), sigma = k0 dr,
+ * coefficients by Baker's linear system in FP64 on the host) and Section 3 (tables of
+ * the isovelocity inverse 1/(1 + b_j lambda_m)).
+ *   N             interior depth points; N + 1 a power of two in [8, 4096]
+ *   H             depth of the guide [m], > 0
+ *   k0            reference wavenumber omega/c0 [1/m], > 0
+ *   dr            range step [m], > 0
+ *   pade_order    p in [1, 8]
+ *   neumann_terms maximum number of Neumann terms including m = 0 (0 or 1: V is ignored,
+ *                 the isovelocity step of Section 3); at most 64
+ *   neumann_tol   per-term stop: after term m >= 1 once ||t_m|| <= tol ||w_j||; >= 0
+ *   cuda_stream   cudaStream_t to order all work on (NULL = legacy default stream)
+ * Errors: PE_ERR_ARG (sizes/values), PE_ERR_OOM, PE_ERR_CUDA.  *out is NULL on error.
+ */
+pe_status pe_plan_create(pe_plan** out, int N, double H, double k0, double dr, int pade_order,
+                         int neumann_terms, double neumann_tol, void* cuda_stream);
+
+/* Release every device and host resource of the plan (NULL is ignored). */
+void pe_plan_destroy(pe_plan* plan);
+
+/* Last error message of the plan ("" if none).  Valid until the next call on the plan. */
+const char* pe_last_error(const pe_plan* plan);
+
+/* Message of the last failed pe_plan_create in this process (it has no plan to hold it). */
+const char* pe_create_error(void);
+
+/*
+ * Transmission-loss output (TL = -20 log10|u| + 10 log10(r / 1 m), dB).  During pe_march
+ * a TL row of N floats is recorded after every global step number s (counted from the
+ * last pe_set_field, 1-based) with s % tl_every == 0.  tl_every = 0 disables recording
+ * (the default).  Clears the recorded rows.  Errors: PE_ERR_ARG if tl_every < 0.
+ */
+pe_status pe_set_output(pe_plan* plan, int tl_every);
+
+/*
+ * Set the field u(r, z_n), n = 1..N, at range r [m] (the starter, Section 3.2).
+ *   u          N interleaved complex64 values (2N floats)
+ *   on_device  0: u is host memory (copied before return); 1: u is device memory
+ * Resets the step counter and the recorded TL rows.  Errors: PE_ERR_ARG (NULL u),
+ * PE_ERR_CUDA.
+ */
+pe_status pe_set_field(pe_plan* plan, const float* u, int on_device, double r);
+
+/*
+ * Append a profile node: n^2(z_n), n = 1..N, in force from range `range` on.  A range
+ * step [r, r + dr] uses V = n^2 - 1 of the last node whose range is <= r + dr/2, or the
+ * first node if there is none (the step-midpoint reading of Section 4.2's range
+ * dependence).  Node ranges must be non-decreasing.
+ *   n2         N floats (is_complex = 0).  is_complex = 1 (the complex absorbing
+ *              potential of Section 3.1) is rejected with PE_ERR_ARG by this build.
+ *   on_device  0: host memory, 1: device memory
+ * Errors: PE_ERR_ARG (NULL, decreasing range, mixing real and complex nodes),
+ * PE_ERR_OOM, PE_ERR_CUDA.
+ */
+pe_status pe_set_profile(pe_plan* plan, const float* n2, int is_complex, double range, int on_device);
+
+/*
+ * Append `count` profile nodes at once: n2 holds count rows of N real values (row-major),
+ * ranges the count node ranges (host memory, non-decreasing).  Same rules as
+ * pe_set_profile with is_complex = 0.
+ */
+pe_status pe_set_profiles(pe_plan* plan, const float* n2, const double* ranges, int count, int on_device);
+
+/* Remove all profile nodes. */
+pe_status pe_clear_profiles(pe_plan* plan);
+
+/*
+ * Enqueue `steps` range steps of Algorithm 1 on the plan's stream (asynchronous: errors
+ * raised on the device are reported by the next pe_read_* / pe_sync).  steps >= 0.
+ * Errors: PE_ERR_STATE (no field set; no profile set while neumann_terms > 1),
+ * PE_ERR_ARG, PE_ERR_CUDA, PE_ERR_OOM (TL storage growth).
+ */
+pe_status pe_march(pe_plan* plan, int steps);
+
+/*
+ * Enqueue `steps` range steps for `count` plans at once: one kernel launch per distinct
+ * grid size N + 1 (plans of equal size share one launch; each CTA marches one plan).
+ * Every plan must satisfy pe_march's preconditions; the plans' own streams are ignored
+ * and the work is ordered on the stream of plans[0].
+ */
+pe_status pe_march_batch(pe_plan** plans, int count, int steps);
+
+/* Wait for the plan's stream; returns a device-side error raised by an earlier march. */
+pe_status pe_sync(pe_plan* plan);
+
+/*
+ * Read the field after the last march: N interleaved complex64 values including the
+ * carrier e^{i k0 (r - r_set)} (Section 2, applied once in FP64 phase arithmetic).
+ *   to_device 0: `out` is host memory; 1: device memory.  Synchronises the stream.
+ */
+pe_status pe_read_field(pe_plan* plan, float* out, int to_device);
+
+/*
+ * Copy the recorded TL rows (row i: N floats, row-major) into `out` (host memory,
+ * capacity `cap` floats) and their ranges into `ranges` (may be NULL; capacity
+ * cap / N doubles).  *n_rows receives the number of rows recorded.  Synchronises.
+ * Errors: PE_ERR_ARG if cap is smaller than rows * N.
+ */
+pe_status pe_read_TL(pe_plan* plan, float* out, size_t cap, double* ranges, size_t* n_rows);
+
+/*
+ * Number of DST-I transforms of length N the plan's marches have executed so far (every
+ * Neumann term costs one forward and, unless it is the last, one inverse transform;
+ * Section 3 counts m + 1 transform pairs for the m-th term).  Synchronises the stream.
+ */
+pe_status pe_get_transform_count(pe_plan* plan, unsigned long long* count);
+
+/*
+ * One unnormalised DST-I of length N on the GPU (Section 3.1's transform, the kernel the
+ * marcher uses for every transform): out_m = sum_{n=1..N} in_n sin(pi n m/(N+1)), m = 1..N.
+ * in/out: N interleaved complex64 values, host (on_device = 0) or device memory
+ * (on_device = 1).  Uses the plan's size and stream; synchronises when on_device = 0.
+ */
+pe_status pe_dst1(pe_plan* plan, const float* in, float* out, int on_device);
+
+/* Current range of the field and number of steps marched since pe_set_field. */
+pe_status pe_get_range(const pe_plan* plan, double* r, long long* steps);
+
+/*
+ * Host-only: the [p/p] Pade data the plan uses for sigma = k0 dr (Section 2), in FP64:
+ * b[2p] and a[2p] interleaved complex (Q = prod (1 + b_j X), P = prod (1 + a_j X)),
+ * d[2p + 2] = (d0, d_1..d_p) of the sum form.  Runs without a GPU.
+ */
+pe_status pe_pade_coefficients(double sigma, int p, double* b, double* a, double* d);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSSP_H_ */

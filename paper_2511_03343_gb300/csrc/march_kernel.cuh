@@ -1,0 +1,486 @@
+// SSSP range-march kernels for sm_103a.
+//
+// One CTA marches one solve for all of its range steps (a persistent, fused kernel): the
+// field lives in registers in spectral (DST-I) space between stages and steps, every
+// transform runs in shared memory, and only the profile rows, the Pade tables and the TL
+// output touch global memory.
+//
+// Per range step (Algorithm 1, product form of the Section 2 Pade propagator):
+//   for every Pade stage j:   y <- R_j(lambda) y + beta_j sum_{m>=1} t_m        (spectral)
+//     t_0 = L_j^{-1} y,  t_m = -b_j L_j^{-1} (V t_{m-1})                    (Eq. Neumann)
+//     L_j^{-1} = IDST diag(1/(1 + b_j lambda_m)) DST                         (Eq. inverse_isovel)
+//   R_j = (1 + a_j lambda)/(1 + b_j lambda) is applied with a hi+lo (float-float) table so
+//   that its rounding does not accumulate over thousands of steps; the Neumann terms are
+//   plain FP32.  Without a profile (neumann_terms <= 1) the whole step is one diagonal
+//   multiply by G = prod_j R_j.
+//
+// DST-I of length N = L - 1 (L a power of two) is one complex FFT of length L:
+//   y_n = sin(pi n/L)(x_n + x_{L-n}) + (x_n - x_{L-n})/2,  Y = FFT_L(y),
+//   S_{2k} = (i/2)(Y_k - Y_{L-k}),  S_{2k+1} = S_{2k-1} + (Y_k + Y_{L-k})/2,  S_{-1} = -S_1,
+// with a block-wide prefix scan for the odd outputs.  The FFT is a Stockham autosort FFT
+// with radix-8 passes (one radix-8 butterfly per thread, 8 points per thread) and a final
+// radix-2/4 pass, ping-ponging between two padded shared buffers (index i stored at
+// i + i/8 to spread the strided accesses over the banks).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sssp {
+
+constexpr int kMaxStages = 8;
+constexpr int kStatusOk = 0;
+constexpr int kStatusDiverged = 4;
+constexpr int kStatusNumeric = 7;
+
+// Everything one CTA needs to march one solve.  Tables are indexed by mode m in [0, L)
+// (m = 0 is a zero pad), profile rows and fields by depth index n in [0, L) (n = 0 is the
+// zero boundary value).
+struct SolveDesc {
+  const float4* R;       // p x L  hi/lo of (1 + a_j lam_m)/(1 + b_j lam_m)
+  const float2* A;       // p x L  (2/L) / (1 + b_j lam_m)
+  const float2* B;       // p x L  (2/L) (-b_j) / (1 + b_j lam_m)
+  const float4* G;       // L      hi/lo of prod_j R_j (isovelocity step)
+  const float* V;        // nodes x L, V = n^2 - 1
+  const double* node_r;  // node ranges, non-decreasing
+  float2* yhat;          // L  spectral state (DST-I coefficients, unnormalised)
+  float2* field;         // L  physical envelope written at the end of the march
+  float* tl;             // TL rows, N floats each
+  int* status;           // device status word
+  unsigned long long* ndst;  // number of DST-I transforms executed (accumulated)
+  float2 beta[kMaxStages];   // (L/2)(1 - a_j/b_j)
+  double r0;             // range at the start of this march
+  double dr;
+  double tol2;           // squared Neumann tolerance
+  long long step0;       // steps marched since the field was set
+  long long rec0;        // TL rows already recorded
+  int node0;             // node in force at the first step's midpoint
+  int nodes;
+  int steps;
+  int p;
+  int terms;             // max Neumann terms incl. m = 0 (<= 1: V ignored)
+  int tl_every;          // 0: no TL rows
+  int N;
+};
+
+template <int LOG2L>
+struct Cfg {
+  static constexpr int L = 1 << LOG2L;
+  static constexpr int NT = L / 8;            // threads per CTA, 8 points each
+  static constexpr int PADL = L + L / 8;      // padded buffer length
+  static constexpr int WS = NT >= 32 ? 32 : NT;
+  static constexpr int NW = (NT + 31) / 32;
+  static constexpr unsigned MASK = NT >= 32 ? 0xffffffffu : ((1u << NT) - 1u);
+  static constexpr int MIN_BLOCKS = NT >= 512 ? 1 : (512 / NT > 16 ? 16 : 512 / NT);
+  // dynamic shared memory: 2 padded buffers, twiddles, t_0 and B_j areas, sin weights, V row,
+  // scan + reduce
+  static constexpr size_t SMEM = sizeof(float2) * (2 * PADL + 3 * L) + sizeof(float) * (2 * L) +
+                                 sizeof(float2) * NW + sizeof(float) * 2 * NW;
+};
+
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
+
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 mul_negi(float2 x) { return make_float2(x.y, -x.x); }
+__device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+
+// y * (hi + lo) with the hi/lo split of a multiplier: the product is rounded, the
+// multiplier is not, so no fixed per-mode error builds up over the steps.
+__device__ __forceinline__ float2 ffmul(float4 g, float2 y) {
+  const float re_lo = fmaf(g.z, y.x, -g.w * y.y);
+  const float im_lo = fmaf(g.z, y.y, g.w * y.x);
+  return make_float2(fmaf(g.x, y.x, fmaf(-g.y, y.y, re_lo)), fmaf(g.x, y.y, fmaf(g.y, y.x, im_lo)));
+}
+
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  const float2 t = a;
+  a = t + b;
+  b = t - b;
+}
+// forward DFT of length 4 in place, natural output order
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+  const float2 c0 = x0 + x2, d0 = x0 - x2, c1 = x1 + x3, d1 = mul_negi(x1 - x3);
+  x0 = c0 + c1;
+  x2 = c0 - c1;
+  x1 = d0 + d1;
+  x3 = d0 - d1;
+}
+// forward DFT of length 8 (one radix-2 frequency split, then two length-4 DFTs)
+__device__ __forceinline__ void dft8(float2 (&v)[8]) {
+  const float h = 0.70710678118654752440f;
+  float2 a0 = v[0] + v[4], a1 = v[1] + v[5], a2 = v[2] + v[6], a3 = v[3] + v[7];
+  float2 b0 = v[0] - v[4], b1 = v[1] - v[5], b2 = v[2] - v[6], b3 = v[3] - v[7];
+  b1 = make_float2(h * (b1.x + b1.y), h * (b1.y - b1.x));     // * e^{-i pi/4}
+  b2 = mul_negi(b2);                                           // * e^{-i pi/2}
+  b3 = make_float2(h * (b3.y - b3.x), -h * (b3.x + b3.y));    // * e^{-3i pi/4}
+  dft4(a0, a1, a2, a3);
+  dft4(b0, b1, b2, b3);
+  v[0] = a0; v[2] = a1; v[4] = a2; v[6] = a3;
+  v[1] = b0; v[3] = b1; v[5] = b2; v[7] = b3;
+}
+
+template <int R>
+__device__ __forceinline__ void dftR(float2 (&v)[R]) {
+  if constexpr (R == 8) dft8(v);
+  else if constexpr (R == 4) dft4(v[0], v[1], v[2], v[3]);
+  else dft2(v[0], v[1]);
+}
+
+// One Stockham pass of radix R over span NS: butterfly j reads src[j + r L/R], applies the
+// twiddles exp(-2 pi i r k/(NS R)), k = j mod NS, and writes dst[(j - k) R + k + r NS].
+template <int LOG2L, int R, int NS>
+__device__ __forceinline__ void fft_pass(const float2* __restrict__ src, float2* __restrict__ dst,
+                                         const float2* __restrict__ tw) {
+  constexpr int L = 1 << LOG2L, NT = L / 8, NB = L / R, PER = NB / NT;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int j = threadIdx.x + q * NT;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[pidx(j + r * NB)];
+    const int k = j & (NS - 1);
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * k * (L / (NS * R))]);
+    dftR<R>(v);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[pidx(base + r * NS)] = v[r];
+  }
+}
+
+template <int LOG2L, int NS>
+__device__ __forceinline__ float2* fft_rest(float2* src, float2* dst, const float2* tw) {
+  constexpr int L = 1 << LOG2L;
+  if constexpr (NS >= L) {
+    return src;
+  } else {
+    constexpr int R = (L / NS) >= 8 ? 8 : (L / NS);
+    fft_pass<LOG2L, R, NS>(src, dst, tw);
+    __syncthreads();
+    return fft_rest<LOG2L, NS * R>(dst, src, tw);
+  }
+}
+
+// Unnormalised DST-I of the L values in `a` (natural order, padded; a[0] is ignored) into
+// out[0..8) = S_{8t..8t+8) of thread t (S_0 = 0).  Uses `b` as the ping-pong buffer.
+// On return every thread has finished reading both buffers.
+template <int LOG2L>
+__device__ __forceinline__ void dst_block(float2* a, float2* b, const float2* __restrict__ tw,
+                                          const float* __restrict__ sinw, float2* scan_s, float2 (&out)[8]) {
+  using C = Cfg<LOG2L>;
+  constexpr int L = C::L;
+  const int t = threadIdx.x;
+  {  // first radix-8 pass (span 1, no twiddles), fused with the sine pre-weighting
+    float2 v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int n = t + r * (L / 8);
+      const float2 xn = a[pidx(n)];
+      const float2 xm = a[pidx((L - n) & (L - 1))];
+      const float s = sinw[n];
+      v[r] = make_float2(fmaf(s, xn.x + xm.x, 0.5f * (xn.x - xm.x)), fmaf(s, xn.y + xm.y, 0.5f * (xn.y - xm.y)));
+    }
+    dft8(v);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) b[pidx(8 * t + r)] = v[r];
+  }
+  __syncthreads();
+  const float2* F = fft_rest<LOG2L, 8>(b, a, tw);
+  // post-processing: even outputs from pairs (k, L-k), odd outputs by a prefix scan
+  float2 se[4], dd[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int k = 4 * t + s;
+    const float2 yk = F[pidx(k)];
+    const float2 ym = F[pidx((L - k) & (L - 1))];
+    se[s] = make_float2(-0.5f * (yk.y - ym.y), 0.5f * (yk.x - ym.x));
+    dd[s] = (k == 0) ? 0.5f * yk : 0.5f * (yk + ym);
+  }
+  dd[1] = dd[1] + dd[0];
+  dd[2] = dd[2] + dd[1];
+  dd[3] = dd[3] + dd[2];
+  const int lane = t & 31, warp = t >> 5;
+  float2 inc = dd[3];
+#pragma unroll
+  for (int o = 1; o < C::WS; o <<= 1) {
+    const float nx = __shfl_up_sync(C::MASK, inc.x, o, C::WS);
+    const float ny = __shfl_up_sync(C::MASK, inc.y, o, C::WS);
+    if (lane >= o) inc = inc + make_float2(nx, ny);
+  }
+  float2 excl = make_float2(__shfl_up_sync(C::MASK, inc.x, 1, C::WS), __shfl_up_sync(C::MASK, inc.y, 1, C::WS));
+  if (lane == 0) excl = make_float2(0.f, 0.f);
+  if constexpr (C::NW > 1) {
+    if (lane == C::WS - 1) scan_s[warp] = inc;
+    __syncthreads();
+    float2 off = make_float2(0.f, 0.f);
+    for (int w = 0; w < warp; ++w) off = off + scan_s[w];
+    excl = excl + off;
+  } else {
+    __syncthreads();
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    out[2 * s] = se[s];
+    out[2 * s + 1] = dd[s] + excl;
+  }
+}
+
+template <int LOG2L>
+__device__ __forceinline__ void load_tables(float2* tw, float* sinw, const float2* __restrict__ tw_g,
+                                            const float* __restrict__ sin_g) {
+  using C = Cfg<LOG2L>;
+  for (int i = threadIdx.x; i < C::L; i += C::NT) {
+    tw[i] = tw_g[i];
+    sinw[i] = sin_g[i];
+  }
+}
+
+template <int LOG2L>
+struct Smem {
+  float2* bufA;
+  float2* bufB;
+  float2* tw;
+  float2* t0s;   // per-thread t_0 values, element i of thread t at i * NT + t
+  float2* Bs;    // per-thread B_j multipliers, same layout
+  float* sinw;
+  float* Vs;
+  float2* scan_s;
+  float* red;
+  __device__ __forceinline__ explicit Smem(unsigned char* base) {
+    using C = Cfg<LOG2L>;
+    bufA = reinterpret_cast<float2*>(base);
+    bufB = bufA + C::PADL;
+    tw = bufB + C::PADL;
+    t0s = tw + C::L;
+    Bs = t0s + C::L;
+    sinw = reinterpret_cast<float*>(Bs + C::L);
+    Vs = sinw + C::L;
+    scan_s = reinterpret_cast<float2*>(Vs + C::L);
+    red = reinterpret_cast<float*>(scan_s + C::NW);
+  }
+};
+
+template <int LOG2L>
+__device__ __forceinline__ void load8(const float2* __restrict__ p, float2 (&v)[8]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float4 x = __ldg(q + i);
+    v[2 * i] = make_float2(x.x, x.y);
+    v[2 * i + 1] = make_float2(x.z, x.w);
+  }
+}
+
+template <int LOG2L>
+__device__ __forceinline__ void store8(float2* p, const float2 (&v)[8]) {
+  float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) q[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+}
+
+// TL row after a step: physical envelope u = (2/L) DST(y), TL = -20 log10|u| + 10 log10 r.
+template <int LOG2L>
+__device__ __forceinline__ void record_tl(Smem<LOG2L>& sm, const SolveDesc& d, const float2 (&y)[8], float out_scale,
+                                          int s, long long nrec) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) sm.bufA[pidx(8 * t + i)] = out_scale * y[i];
+  __syncthreads();
+  float2 u[8];
+  dst_block<LOG2L>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, u);
+  const float lr = float(10.0 * log10(d.r0 + double(s + 1) * d.dr));
+  float* row = d.tl + (size_t)(d.rec0 + nrec) * d.N;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int n = 8 * t + i;
+    if (n >= 1) row[n - 1] = fmaf(-10.f, log10f(cabs2(u[i])), lr);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// The persistent march: blockIdx.x selects the solve.
+// ---------------------------------------------------------------------------------------
+template <int LOG2L>
+__global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
+    sssp_march_kernel(const SolveDesc* __restrict__ descs, const float2* __restrict__ tw_g,
+                      const float* __restrict__ sin_g) {
+  using C = Cfg<LOG2L>;
+  constexpr int L = C::L;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<LOG2L> sm(smem_raw);
+  const SolveDesc& d = descs[blockIdx.x];
+  const int t = threadIdx.x;
+  const int lane = t & 31, warp = t >> 5;
+  load_tables<LOG2L>(sm.tw, sm.sinw, tw_g, sin_g);
+
+  float2 y[8];
+  load8<LOG2L>(d.yhat + 8 * t, y);
+  const float out_scale = 2.0f / float(L);
+  const bool iso = d.terms <= 1;
+  int status = kStatusOk;
+  unsigned long long ndst = 0;
+  long long nrec = 0;
+  int node = d.node0;
+  double next_r = (node + 1 < d.nodes) ? d.node_r[node + 1] : 1e300;
+  if (!iso) {
+    const float* Vg = d.V + (size_t)node * L;
+    for (int i = t; i < L; i += C::NT) sm.Vs[i] = Vg[i];
+  }
+  __syncthreads();
+
+  if (iso) {
+    // V ignored: every step is the diagonal multiply by G = prod_j R_j
+    float4 G[8];
+    {
+      const float4* g = d.G + 8 * t;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) G[i] = __ldg(g + i);
+    }
+    for (int s = 0; s < d.steps; ++s) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) y[i] = ffmul(G[i], y[i]);
+      const long long gs = d.step0 + s + 1;
+      if (d.tl_every > 0 && gs % d.tl_every == 0) {
+        record_tl<LOG2L>(sm, d, y, out_scale, s, nrec);
+        ++ndst;
+        ++nrec;
+      }
+    }
+  } else {
+    for (int s = 0; s < d.steps && status == kStatusOk; ++s) {
+      const double rmid = d.r0 + (double(s) + 0.5) * d.dr;
+      if (rmid >= next_r) {  // advance to the node in force at this step's midpoint
+        while (node + 1 < d.nodes && d.node_r[node + 1] <= rmid) ++node;
+        next_r = (node + 1 < d.nodes) ? d.node_r[node + 1] : 1e300;
+        const float* Vg = d.V + (size_t)node * L;
+        for (int i = t; i < L; i += C::NT) sm.Vs[i] = Vg[i];
+        // first read of Vs is after the syncs of the stage's first transform
+      }
+      for (int j = 0; j < d.p && status == kStatusOk; ++j) {
+        float2 acc[8], tp[8];
+        {
+          float2 Bj[8];
+          load8<LOG2L>(d.B + (size_t)j * L + 8 * t, Bj);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) sm.Bs[i * C::NT + t] = Bj[i];
+        }
+        {
+          float2 Aj[8];
+          load8<LOG2L>(d.A + (size_t)j * L + 8 * t, Aj);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float2 t0 = cmul(Aj[i], y[i]);
+            sm.t0s[i * C::NT + t] = t0;
+            sm.bufA[pidx(8 * t + i)] = t0;
+            acc[i] = make_float2(0.f, 0.f);
+          }
+        }
+        __syncthreads();
+        dst_block<LOG2L>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // t_0 in depth space
+        ++ndst;
+        double prev = 0.0;
+        int grow = 0;
+        for (int m = 1; m < d.terms; ++m) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) sm.bufA[pidx(8 * t + i)] = sm.Vs[8 * t + i] * tp[i];
+          __syncthreads();
+          dst_block<LOG2L>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // DST(V t_{m-1})
+          ++ndst;
+          float nt = 0.f, nw = 0.f;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            tp[i] = cmul(sm.Bs[i * C::NT + t], tp[i]);  // spectral t_m (scaled by 2/L)
+            acc[i] = acc[i] + tp[i];
+            nt += cabs2(tp[i]);
+            nw += cabs2(sm.t0s[i * C::NT + t] + acc[i]);
+          }
+#pragma unroll
+          for (int o = C::WS / 2; o > 0; o >>= 1) {
+            nt += __shfl_xor_sync(C::MASK, nt, o, C::WS);
+            nw += __shfl_xor_sync(C::MASK, nw, o, C::WS);
+          }
+          if (lane == 0) {
+            sm.red[2 * warp] = nt;
+            sm.red[2 * warp + 1] = nw;
+          }
+          const bool last = (m == d.terms - 1);
+          if (!last) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) sm.bufA[pidx(8 * t + i)] = tp[i];
+          }
+          __syncthreads();
+          if (last) break;
+          double snt = 0.0, snw = 0.0;
+          for (int w = 0; w < C::NW; ++w) {
+            snt += sm.red[2 * w];
+            snw += sm.red[2 * w + 1];
+          }
+          if (!isfinite(snt) || !isfinite(snw)) {
+            status = kStatusNumeric;
+            break;
+          }
+          grow = (m > 1 && snt > prev) ? grow + 1 : 0;
+          prev = snt;
+          if (grow >= 3) {
+            status = kStatusDiverged;
+            break;
+          }
+          if (snt <= d.tol2 * snw) break;
+          dst_block<LOG2L>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // t_m in depth space
+          ++ndst;
+        }
+        {
+          const float4* rp = d.R + (size_t)j * L + 8 * t;
+          const float2 bj = d.beta[j];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) y[i] = ffmul(__ldg(rp + i), y[i]) + cmul(bj, acc[i]);
+        }
+      }
+      if (status != kStatusOk) break;
+      const long long gs = d.step0 + s + 1;
+      if (d.tl_every > 0 && gs % d.tl_every == 0) {
+        record_tl<LOG2L>(sm, d, y, out_scale, s, nrec);
+        ++ndst;
+        ++nrec;
+      }
+    }
+  }
+  store8<LOG2L>(d.yhat + 8 * t, y);
+  // physical envelope for pe_read_field
+#pragma unroll
+  for (int i = 0; i < 8; ++i) sm.bufA[pidx(8 * t + i)] = out_scale * y[i];
+  __syncthreads();
+  float2 u[8];
+  dst_block<LOG2L>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, u);
+  ++ndst;
+  store8<LOG2L>(d.field + 8 * t, u);
+  if (t == 0) {
+    if (status != kStatusOk) atomicMax(d.status, status);
+    atomicAdd(d.ndst, ndst);
+  }
+}
+
+// DST-I of one field: out = scale * DST(in), in holds N values (n = 1..N), out L values.
+template <int LOG2L>
+__global__ void __launch_bounds__(Cfg<LOG2L>::NT)
+    sssp_dst_kernel(const float2* __restrict__ in, float2* __restrict__ out, float scale,
+                    const float2* __restrict__ tw_g, const float* __restrict__ sin_g) {
+  using C = Cfg<LOG2L>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<LOG2L> sm(smem_raw);
+  const int t = threadIdx.x;
+  load_tables<LOG2L>(sm.tw, sm.sinw, tw_g, sin_g);
+  for (int n = t; n < C::L; n += C::NT) sm.bufA[pidx(n)] = (n == 0) ? make_float2(0.f, 0.f) : in[n - 1];
+  __syncthreads();
+  float2 o[8];
+  dst_block<LOG2L>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, o);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) o[i] = scale * o[i];
+  store8<LOG2L>(out + 8 * t, o);
+}
+
+}  // namespace sssp

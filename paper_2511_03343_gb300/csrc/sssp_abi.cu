@@ -1,0 +1,661 @@
+// C ABI of the SSSP marcher (include/sssp.h): plan construction (FP64 tables on the host),
+// device memory, launches and status reporting.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/sssp.h"
+#include "march_kernel.cuh"
+#include "pade_host.h"
+
+using sssp::Cfg;
+using sssp::SolveDesc;
+using cd = std::complex<double>;
+
+namespace {
+
+constexpr int kMinLog2 = 3;
+constexpr int kMaxLog2 = 12;
+constexpr int kMaxTerms = 64;
+
+thread_local std::string g_create_error;
+
+struct TransformTables {
+  float2* tw = nullptr;  // L twiddles exp(-2 pi i q/L)
+  float* sinw = nullptr; // L weights sin(pi n/L)
+};
+
+std::mutex g_tab_mu;
+std::map<std::pair<int, int>, TransformTables> g_tabs;  // (device, log2L)
+
+// twiddles / sine weights in FP64, rounded once to FP32 (shared by all plans of a size)
+cudaError_t get_tables(int device, int log2L, TransformTables* out) {
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  auto key = std::make_pair(device, log2L);
+  auto it = g_tabs.find(key);
+  if (it != g_tabs.end()) {
+    *out = it->second;
+    return cudaSuccess;
+  }
+  const int L = 1 << log2L;
+  std::vector<float2> tw(L);
+  std::vector<float> sw(L);
+  for (int q = 0; q < L; ++q) {
+    const double ang = 2.0 * M_PI * double(q) / double(L);
+    tw[q] = make_float2(float(std::cos(ang)), float(-std::sin(ang)));
+    sw[q] = float(std::sin(M_PI * double(q) / double(L)));
+  }
+  TransformTables t;
+  cudaError_t e = cudaMalloc(&t.tw, sizeof(float2) * L);
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&t.sinw, sizeof(float) * L);
+  if (e != cudaSuccess) {
+    cudaFree(t.tw);
+    return e;
+  }
+  e = cudaMemcpy(t.tw, tw.data(), sizeof(float2) * L, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(t.sinw, sw.data(), sizeof(float) * L, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  g_tabs[key] = t;
+  *out = t;
+  return cudaSuccess;
+}
+
+int ilog2_exact(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return ((1 << l) == v) ? l : -1;
+}
+
+}  // namespace
+
+struct pe_plan {
+  int N = 0, L = 0, log2L = 0, p = 0, terms = 0, device = 0;
+  double H = 0, k0 = 0, dr = 0, tol = 0;
+  cudaStream_t stream = nullptr;
+  sssp::PadeData pade;
+  TransformTables tabs;
+  float4* dR = nullptr;
+  float2* dA = nullptr;
+  float2* dB = nullptr;
+  float4* dG = nullptr;
+  float2 beta[sssp::kMaxStages];
+  float2* dYhat = nullptr;
+  float2* dField = nullptr;
+  float2* dStage = nullptr;  // N-value staging buffer (set / read field)
+  float* dV = nullptr;
+  double* dNodeR = nullptr;
+  int nodes = 0, node_cap = 0;
+  std::vector<double> node_r;
+  int* dStatus = nullptr;
+  unsigned long long* dNdst = nullptr;
+  float* dTL = nullptr;
+  long long tl_cap_rows = 0, tl_rows = 0;
+  std::vector<double> tl_ranges;
+  int tl_every = 0;
+  SolveDesc* dDesc = nullptr;
+  double r_set = 0.0;
+  long long steps_done = 0;
+  bool field_set = false;
+  std::string err;
+};
+
+namespace {
+
+pe_status fail(pe_plan* p, pe_status s, const std::string& msg) {
+  if (p) p->err = msg;
+  return s;
+}
+
+pe_status cuda_fail(pe_plan* p, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return fail(p, PE_ERR_OOM, m);
+  return fail(p, PE_ERR_CUDA, m);
+}
+
+#define PE_CUDA(plan, call)                                  \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(plan, e_, #call); \
+  } while (0)
+
+template <int LOG2L>
+cudaError_t set_smem_attr() {
+  static int done_dev = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (done_dev == dev) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(sssp::sssp_march_kernel<LOG2L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(Cfg<LOG2L>::SMEM));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sssp::sssp_dst_kernel<LOG2L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(Cfg<LOG2L>::SMEM));
+  if (e == cudaSuccess) done_dev = dev;
+  return e;
+}
+
+template <int LOG2L>
+cudaError_t launch_march_t(const SolveDesc* dDescs, int count, const TransformTables& tabs, cudaStream_t st) {
+  cudaError_t e = set_smem_attr<LOG2L>();
+  if (e != cudaSuccess) return e;
+  sssp::sssp_march_kernel<LOG2L><<<count, Cfg<LOG2L>::NT, Cfg<LOG2L>::SMEM, st>>>(dDescs, tabs.tw, tabs.sinw);
+  return cudaGetLastError();
+}
+
+template <int LOG2L>
+cudaError_t launch_dst_t(const float2* in, float2* out, float scale, const TransformTables& tabs, cudaStream_t st) {
+  cudaError_t e = set_smem_attr<LOG2L>();
+  if (e != cudaSuccess) return e;
+  sssp::sssp_dst_kernel<LOG2L><<<1, Cfg<LOG2L>::NT, Cfg<LOG2L>::SMEM, st>>>(in, out, scale, tabs.tw, tabs.sinw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_march(int log2L, const SolveDesc* d, int count, const TransformTables& tabs, cudaStream_t st) {
+  switch (log2L) {
+    case 3: return launch_march_t<3>(d, count, tabs, st);
+    case 4: return launch_march_t<4>(d, count, tabs, st);
+    case 5: return launch_march_t<5>(d, count, tabs, st);
+    case 6: return launch_march_t<6>(d, count, tabs, st);
+    case 7: return launch_march_t<7>(d, count, tabs, st);
+    case 8: return launch_march_t<8>(d, count, tabs, st);
+    case 9: return launch_march_t<9>(d, count, tabs, st);
+    case 10: return launch_march_t<10>(d, count, tabs, st);
+    case 11: return launch_march_t<11>(d, count, tabs, st);
+    case 12: return launch_march_t<12>(d, count, tabs, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_dst(int log2L, const float2* in, float2* out, float scale, const TransformTables& tabs,
+                       cudaStream_t st) {
+  switch (log2L) {
+    case 3: return launch_dst_t<3>(in, out, scale, tabs, st);
+    case 4: return launch_dst_t<4>(in, out, scale, tabs, st);
+    case 5: return launch_dst_t<5>(in, out, scale, tabs, st);
+    case 6: return launch_dst_t<6>(in, out, scale, tabs, st);
+    case 7: return launch_dst_t<7>(in, out, scale, tabs, st);
+    case 8: return launch_dst_t<8>(in, out, scale, tabs, st);
+    case 9: return launch_dst_t<9>(in, out, scale, tabs, st);
+    case 10: return launch_dst_t<10>(in, out, scale, tabs, st);
+    case 11: return launch_dst_t<11>(in, out, scale, tabs, st);
+    case 12: return launch_dst_t<12>(in, out, scale, tabs, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+__global__ void carrier_kernel(const float2* __restrict__ field, float2* __restrict__ out, float c, float s, int N) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < N) {
+    const float2 v = field[n + 1];
+    out[n] = make_float2(c * v.x - s * v.y, c * v.y + s * v.x);
+  }
+}
+
+void split_ff(cd v, float4* out) {
+  const float hr = float(v.real()), hi = float(v.imag());
+  out->x = hr;
+  out->y = hi;
+  out->z = float(v.real() - double(hr));
+  out->w = float(v.imag() - double(hi));
+}
+
+pe_status ensure_node_cap(pe_plan* p, int need) {
+  if (need <= p->node_cap) return PE_OK;
+  int cap = std::max(need, std::max(4, p->node_cap * 2));
+  float* nV = nullptr;
+  double* nR = nullptr;
+  PE_CUDA(p, cudaMalloc(&nV, sizeof(float) * size_t(cap) * p->L));
+  cudaError_t e = cudaMalloc(&nR, sizeof(double) * cap);
+  if (e != cudaSuccess) {
+    cudaFree(nV);
+    return cuda_fail(p, e, "cudaMalloc(node ranges)");
+  }
+  if (p->nodes > 0) {
+    PE_CUDA(p, cudaMemcpyAsync(nV, p->dV, sizeof(float) * size_t(p->nodes) * p->L, cudaMemcpyDeviceToDevice, p->stream));
+    PE_CUDA(p, cudaMemcpyAsync(nR, p->dNodeR, sizeof(double) * p->nodes, cudaMemcpyDeviceToDevice, p->stream));
+  }
+  PE_CUDA(p, cudaStreamSynchronize(p->stream));
+  cudaFree(p->dV);
+  cudaFree(p->dNodeR);
+  p->dV = nV;
+  p->dNodeR = nR;
+  p->node_cap = cap;
+  return PE_OK;
+}
+
+pe_status ensure_tl_cap(pe_plan* p, long long rows) {
+  if (rows <= p->tl_cap_rows) return PE_OK;
+  long long cap = std::max(rows, std::max<long long>(16, p->tl_cap_rows * 2));
+  float* n = nullptr;
+  PE_CUDA(p, cudaMalloc(&n, sizeof(float) * size_t(cap) * p->N));
+  if (p->tl_rows > 0)
+    PE_CUDA(p, cudaMemcpyAsync(n, p->dTL, sizeof(float) * size_t(p->tl_rows) * p->N, cudaMemcpyDeviceToDevice, p->stream));
+  PE_CUDA(p, cudaStreamSynchronize(p->stream));
+  cudaFree(p->dTL);
+  p->dTL = n;
+  p->tl_cap_rows = cap;
+  return PE_OK;
+}
+
+int node_for(const pe_plan* p, double rmid) {
+  int k = 0;
+  for (int i = 0; i < p->nodes; ++i) {
+    if (p->node_r[i] <= rmid) k = i;
+    else break;
+  }
+  return k;
+}
+
+long long records_between(long long a, long long b, int every) {  // multiples of every in (a, b]
+  if (every <= 0) return 0;
+  return b / every - a / every;
+}
+
+// Fill the descriptor for one march of `steps` steps and reserve its TL rows.
+pe_status prepare_desc(pe_plan* p, int steps, SolveDesc* d) {
+  if (!p->field_set) return fail(p, PE_ERR_STATE, "pe_march before pe_set_field");
+  if (p->terms > 1 && p->nodes == 0) return fail(p, PE_ERR_STATE, "pe_march with Neumann terms but no profile");
+  if (steps < 0) return fail(p, PE_ERR_ARG, "steps must be >= 0");
+  const long long recs = records_between(p->steps_done, p->steps_done + steps, p->tl_every);
+  pe_status st = ensure_tl_cap(p, p->tl_rows + recs);
+  if (st != PE_OK) return st;
+  std::memset(d, 0, sizeof(*d));
+  d->R = p->dR;
+  d->A = p->dA;
+  d->B = p->dB;
+  d->G = p->dG;
+  d->V = p->dV;
+  d->node_r = p->dNodeR;
+  d->yhat = p->dYhat;
+  d->field = p->dField;
+  d->tl = p->dTL;
+  d->status = p->dStatus;
+  d->ndst = p->dNdst;
+  for (int j = 0; j < sssp::kMaxStages; ++j) d->beta[j] = p->beta[j];
+  d->r0 = p->r_set + double(p->steps_done) * p->dr;
+  d->dr = p->dr;
+  d->tol2 = p->tol * p->tol;
+  d->step0 = p->steps_done;
+  d->rec0 = p->tl_rows;
+  d->nodes = p->nodes;
+  d->node0 = (p->nodes > 0) ? node_for(p, d->r0 + 0.5 * p->dr) : 0;
+  d->steps = steps;
+  d->p = p->p;
+  d->terms = p->terms;
+  d->tl_every = p->tl_every;
+  d->N = p->N;
+  for (long long s = 1; s <= steps; ++s)
+    if (p->tl_every > 0 && (p->steps_done + s) % p->tl_every == 0) p->tl_ranges.push_back(p->r_set + double(p->steps_done + s) * p->dr);
+  p->tl_rows += recs;
+  p->steps_done += steps;
+  return PE_OK;
+}
+
+pe_status check_status(pe_plan* p) {
+  int s = 0;
+  PE_CUDA(p, cudaMemcpyAsync(&s, p->dStatus, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  PE_CUDA(p, cudaStreamSynchronize(p->stream));
+  if (s == sssp::kStatusDiverged) return fail(p, PE_ERR_NEUMANN_DIVERGED, "Neumann series diverged (term norms grew for 3 consecutive terms)");
+  if (s == sssp::kStatusNumeric) return fail(p, PE_ERR_NUMERIC, "non-finite value in the march");
+  if (s != 0) return fail(p, PE_ERR_CUDA, "device status " + std::to_string(s));
+  return PE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pe_abi_version(void) { return 1; }
+
+const char* pe_create_error(void) { return g_create_error.c_str(); }
+
+const char* pe_last_error(const pe_plan* plan) { return plan ? plan->err.c_str() : ""; }
+
+pe_status pe_pade_coefficients(double sigma, int p, double* b, double* a, double* d) {
+  if (!b || !a || !d) return PE_ERR_ARG;
+  sssp::PadeData pd;
+  std::string err;
+  if (!sssp::pade_compute(sigma, p, &pd, &err)) {
+    g_create_error = err;
+    return PE_ERR_ARG;
+  }
+  for (int j = 0; j < p; ++j) {
+    b[2 * j] = pd.b[j].real();
+    b[2 * j + 1] = pd.b[j].imag();
+    a[2 * j] = pd.a[j].real();
+    a[2 * j + 1] = pd.a[j].imag();
+    d[2 * j + 2] = pd.d[j].real();
+    d[2 * j + 3] = pd.d[j].imag();
+  }
+  d[0] = pd.d0.real();
+  d[1] = pd.d0.imag();
+  return PE_OK;
+}
+
+void pe_plan_destroy(pe_plan* p) {
+  if (!p) return;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  cudaFree(p->dR);
+  cudaFree(p->dA);
+  cudaFree(p->dB);
+  cudaFree(p->dG);
+  cudaFree(p->dYhat);
+  cudaFree(p->dField);
+  cudaFree(p->dStage);
+  cudaFree(p->dV);
+  cudaFree(p->dNodeR);
+  cudaFree(p->dStatus);
+  cudaFree(p->dNdst);
+  cudaFree(p->dTL);
+  cudaFree(p->dDesc);
+  delete p;
+}
+
+pe_status pe_plan_create(pe_plan** out, int N, double H, double k0, double dr, int pade_order, int neumann_terms,
+                         double neumann_tol, void* cuda_stream) {
+  g_create_error.clear();
+  if (!out) {
+    g_create_error = "out is NULL";
+    return PE_ERR_ARG;
+  }
+  *out = nullptr;
+  const int log2L = ilog2_exact(N + 1);
+  if (N < 1 || log2L < kMinLog2 || log2L > kMaxLog2) {
+    g_create_error = "N + 1 must be a power of two in [8, 4096]";
+    return PE_ERR_ARG;
+  }
+  if (!(H > 0) || !(k0 > 0) || !(dr > 0) || !std::isfinite(H) || !std::isfinite(k0) || !std::isfinite(dr)) {
+    g_create_error = "H, k0 and dr must be finite and > 0";
+    return PE_ERR_ARG;
+  }
+  if (pade_order < 1 || pade_order > sssp::kMaxPade) {
+    g_create_error = "pade_order must be in [1, 8]";
+    return PE_ERR_ARG;
+  }
+  if (neumann_terms < 0 || neumann_terms > kMaxTerms || !(neumann_tol >= 0)) {
+    g_create_error = "neumann_terms must be in [0, 64] and neumann_tol >= 0";
+    return PE_ERR_ARG;
+  }
+  pe_plan* p = new pe_plan();
+  p->N = N;
+  p->L = N + 1;
+  p->log2L = log2L;
+  p->p = pade_order;
+  p->terms = neumann_terms;
+  p->H = H;
+  p->k0 = k0;
+  p->dr = dr;
+  p->tol = neumann_tol;
+  p->stream = static_cast<cudaStream_t>(cuda_stream);
+  std::string err;
+  if (!sssp::pade_compute(k0 * dr, pade_order, &p->pade, &err)) {
+    g_create_error = err;
+    delete p;
+    return PE_ERR_ARG;
+  }
+  auto bail = [&](cudaError_t e, const char* what) {
+    g_create_error = std::string(what) + ": " + cudaGetErrorString(e);
+    pe_plan_destroy(p);
+    return e == cudaErrorMemoryAllocation ? PE_ERR_OOM : PE_ERR_CUDA;
+  };
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) return bail(e, "cudaGetDevice");
+  e = get_tables(p->device, log2L, &p->tabs);
+  if (e != cudaSuccess) return bail(e, "transform tables");
+  // plan tables in FP64 (Section 3: 1/(1 + b_j lambda_m), lambda_m = -(pi m/(k0 H))^2)
+  const int L = p->L, P = pade_order;
+  std::vector<float4> R(size_t(P) * L), G(L);
+  std::vector<float2> A(size_t(P) * L), B(size_t(P) * L);
+  const double scale = 2.0 / double(L);
+  for (int m = 0; m < L; ++m) {
+    const double x = M_PI * double(m) / (k0 * H);
+    const double lam = -x * x;
+    cd g(1.0, 0.0);
+    for (int j = 0; j < P; ++j) {
+      const cd b = p->pade.b[j], a = p->pade.a[j];
+      const cd q = 1.0 + b * lam;
+      const cd r = (1.0 + a * lam) / q;
+      g *= r;
+      const size_t ix = size_t(j) * L + m;
+      if (m == 0) {
+        R[ix] = make_float4(0, 0, 0, 0);
+        A[ix] = make_float2(0, 0);
+        B[ix] = make_float2(0, 0);
+        continue;
+      }
+      split_ff(r, &R[ix]);
+      const cd av = scale / q, bv = scale * (-b) / q;
+      A[ix] = make_float2(float(av.real()), float(av.imag()));
+      B[ix] = make_float2(float(bv.real()), float(bv.imag()));
+    }
+    if (m == 0) G[m] = make_float4(0, 0, 0, 0);
+    else split_ff(g, &G[m]);
+  }
+  for (int j = 0; j < sssp::kMaxStages; ++j) {
+    if (j < P) {
+      const cd bb = (double(L) / 2.0) * (1.0 - p->pade.a[j] / p->pade.b[j]);
+      p->beta[j] = make_float2(float(bb.real()), float(bb.imag()));
+    } else {
+      p->beta[j] = make_float2(0, 0);
+    }
+  }
+  if ((e = cudaMalloc(&p->dR, sizeof(float4) * R.size())) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&p->dA, sizeof(float2) * A.size())) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&p->dB, sizeof(float2) * B.size())) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&p->dG, sizeof(float4) * L)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&p->dYhat, sizeof(float2) * L)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&p->dField, sizeof(float2) * L)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&p->dStage, sizeof(float2) * L)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&p->dStatus, sizeof(int))) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&p->dNdst, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&p->dDesc, sizeof(SolveDesc))) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = cudaMemcpy(p->dR, R.data(), sizeof(float4) * R.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "upload");
+  if ((e = cudaMemcpy(p->dA, A.data(), sizeof(float2) * A.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "upload");
+  if ((e = cudaMemcpy(p->dB, B.data(), sizeof(float2) * B.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "upload");
+  if ((e = cudaMemcpy(p->dG, G.data(), sizeof(float4) * L, cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "upload");
+  if ((e = cudaMemset(p->dStatus, 0, sizeof(int))) != cudaSuccess) return bail(e, "memset");
+  if ((e = cudaMemset(p->dNdst, 0, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "memset");
+  if ((e = cudaMemset(p->dYhat, 0, sizeof(float2) * L)) != cudaSuccess) return bail(e, "memset");
+  if ((e = cudaMemset(p->dField, 0, sizeof(float2) * L)) != cudaSuccess) return bail(e, "memset");
+  *out = p;
+  return PE_OK;
+}
+
+pe_status pe_set_output(pe_plan* p, int tl_every) {
+  if (!p) return PE_ERR_ARG;
+  if (tl_every < 0) return fail(p, PE_ERR_ARG, "tl_every must be >= 0");
+  p->tl_every = tl_every;
+  p->tl_rows = 0;
+  p->tl_ranges.clear();
+  return PE_OK;
+}
+
+pe_status pe_set_field(pe_plan* p, const float* u, int on_device, double r) {
+  if (!p) return PE_ERR_ARG;
+  if (!u) return fail(p, PE_ERR_ARG, "u is NULL");
+  if (!std::isfinite(r)) return fail(p, PE_ERR_ARG, "r must be finite");
+  PE_CUDA(p, cudaMemcpyAsync(p->dStage, u, sizeof(float2) * p->N,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
+  PE_CUDA(p, launch_dst(p->log2L, p->dStage, p->dYhat, 1.0f, p->tabs, p->stream));
+  // the physical field as given (index 0 = boundary)
+  PE_CUDA(p, cudaMemsetAsync(p->dField, 0, sizeof(float2), p->stream));
+  PE_CUDA(p, cudaMemcpyAsync(p->dField + 1, p->dStage, sizeof(float2) * p->N, cudaMemcpyDeviceToDevice, p->stream));
+  PE_CUDA(p, cudaMemsetAsync(p->dStatus, 0, sizeof(int), p->stream));
+  if (!on_device) PE_CUDA(p, cudaStreamSynchronize(p->stream));
+  p->r_set = r;
+  p->steps_done = 0;
+  p->tl_rows = 0;
+  p->tl_ranges.clear();
+  p->field_set = true;
+  return PE_OK;
+}
+
+static pe_status append_nodes(pe_plan* p, const float* n2, const double* ranges, int count, int on_device) {
+  for (int i = 0; i < count; ++i) {
+    const double prev = (p->nodes + i > 0) ? (i > 0 ? ranges[i - 1] : p->node_r.back()) : -1e300;
+    if (!std::isfinite(ranges[i]) || ranges[i] < prev) return fail(p, PE_ERR_ARG, "profile ranges must be finite and non-decreasing");
+  }
+  pe_status st = ensure_node_cap(p, p->nodes + count);
+  if (st != PE_OK) return st;
+  // V = n^2 - 1 with V[0] = 0 (boundary); converted on the host in FP64
+  std::vector<float> host;
+  std::vector<float> src;
+  const float* s = n2;
+  if (on_device) {
+    src.resize(size_t(count) * p->N);
+    PE_CUDA(p, cudaMemcpyAsync(src.data(), n2, sizeof(float) * src.size(), cudaMemcpyDeviceToHost, p->stream));
+    PE_CUDA(p, cudaStreamSynchronize(p->stream));
+    s = src.data();
+  }
+  host.resize(size_t(count) * p->L);
+  for (int i = 0; i < count; ++i) {
+    host[size_t(i) * p->L] = 0.0f;
+    for (int n = 0; n < p->N; ++n) {
+      const float v = s[size_t(i) * p->N + n];
+      if (!std::isfinite(v)) return fail(p, PE_ERR_ARG, "n2 must be finite");
+      host[size_t(i) * p->L + n + 1] = float(double(v) - 1.0);
+    }
+  }
+  PE_CUDA(p, cudaMemcpyAsync(p->dV + size_t(p->nodes) * p->L, host.data(), sizeof(float) * host.size(),
+                             cudaMemcpyHostToDevice, p->stream));
+  PE_CUDA(p, cudaMemcpyAsync(p->dNodeR + p->nodes, ranges, sizeof(double) * count, cudaMemcpyHostToDevice, p->stream));
+  PE_CUDA(p, cudaStreamSynchronize(p->stream));
+  for (int i = 0; i < count; ++i) p->node_r.push_back(ranges[i]);
+  p->nodes += count;
+  return PE_OK;
+}
+
+pe_status pe_set_profile(pe_plan* p, const float* n2, int is_complex, double range, int on_device) {
+  if (!p) return PE_ERR_ARG;
+  if (!n2) return fail(p, PE_ERR_ARG, "n2 is NULL");
+  if (is_complex) return fail(p, PE_ERR_ARG, "complex n2 is not supported by this build");
+  return append_nodes(p, n2, &range, 1, on_device);
+}
+
+pe_status pe_set_profiles(pe_plan* p, const float* n2, const double* ranges, int count, int on_device) {
+  if (!p) return PE_ERR_ARG;
+  if (!n2 || !ranges || count < 0) return fail(p, PE_ERR_ARG, "n2/ranges NULL or count < 0");
+  return append_nodes(p, n2, ranges, count, on_device);
+}
+
+pe_status pe_clear_profiles(pe_plan* p) {
+  if (!p) return PE_ERR_ARG;
+  p->nodes = 0;
+  p->node_r.clear();
+  return PE_OK;
+}
+
+pe_status pe_march(pe_plan* p, int steps) {
+  if (!p) return PE_ERR_ARG;
+  SolveDesc d;
+  pe_status st = prepare_desc(p, steps, &d);
+  if (st != PE_OK) return st;
+  if (steps == 0) return PE_OK;
+  PE_CUDA(p, cudaMemcpyAsync(p->dDesc, &d, sizeof(d), cudaMemcpyHostToDevice, p->stream));
+  PE_CUDA(p, launch_march(p->log2L, p->dDesc, 1, p->tabs, p->stream));
+  return PE_OK;
+}
+
+pe_status pe_march_batch(pe_plan** plans, int count, int steps) {
+  if (!plans || count < 0) return PE_ERR_ARG;
+  if (count == 0) return PE_OK;
+  pe_plan* p0 = plans[0];
+  if (!p0) return PE_ERR_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (!plans[i]) return fail(p0, PE_ERR_ARG, "NULL plan in batch");
+    if (plans[i]->device != p0->device) return fail(p0, PE_ERR_ARG, "plans on different devices");
+  }
+  // group by size, one launch per group
+  std::map<int, std::vector<SolveDesc>> groups;
+  std::map<int, TransformTables> tabs;
+  for (int i = 0; i < count; ++i) {
+    SolveDesc d;
+    pe_status st = prepare_desc(plans[i], steps, &d);
+    if (st != PE_OK) {
+      p0->err = plans[i]->err;
+      return st;
+    }
+    groups[plans[i]->log2L].push_back(d);
+    tabs[plans[i]->log2L] = plans[i]->tabs;
+  }
+  if (steps == 0) return PE_OK;
+  for (auto& kv : groups) {
+    SolveDesc* dd = nullptr;
+    const size_t bytes = sizeof(SolveDesc) * kv.second.size();
+    PE_CUDA(p0, cudaMallocAsync(reinterpret_cast<void**>(&dd), bytes, p0->stream));
+    PE_CUDA(p0, cudaMemcpyAsync(dd, kv.second.data(), bytes, cudaMemcpyHostToDevice, p0->stream));
+    PE_CUDA(p0, launch_march(kv.first, dd, int(kv.second.size()), tabs[kv.first], p0->stream));
+    PE_CUDA(p0, cudaFreeAsync(dd, p0->stream));
+  }
+  return PE_OK;
+}
+
+pe_status pe_sync(pe_plan* p) {
+  if (!p) return PE_ERR_ARG;
+  return check_status(p);
+}
+
+pe_status pe_read_field(pe_plan* p, float* out, int to_device) {
+  if (!p) return PE_ERR_ARG;
+  if (!out) return fail(p, PE_ERR_ARG, "out is NULL");
+  // carrier e^{i k0 (r - r_set)} in FP64 phase arithmetic (the marcher keeps the envelope)
+  const double phase = std::fmod(p->k0 * p->dr * double(p->steps_done), 2.0 * M_PI);
+  const float c = float(std::cos(phase)), s = float(std::sin(phase));
+  float2* dst = to_device ? reinterpret_cast<float2*>(out) : p->dStage;
+  carrier_kernel<<<(p->N + 255) / 256, 256, 0, p->stream>>>(p->dField, dst, c, s, p->N);
+  PE_CUDA(p, cudaGetLastError());
+  if (!to_device)
+    PE_CUDA(p, cudaMemcpyAsync(out, p->dStage, sizeof(float2) * p->N, cudaMemcpyDeviceToHost, p->stream));
+  return check_status(p);
+}
+
+pe_status pe_read_TL(pe_plan* p, float* out, size_t cap, double* ranges, size_t* n_rows) {
+  if (!p) return PE_ERR_ARG;
+  const size_t need = size_t(p->tl_rows) * p->N;
+  if (n_rows) *n_rows = size_t(p->tl_rows);
+  if (need > 0 && (!out || cap < need)) return fail(p, PE_ERR_ARG, "TL buffer too small");
+  if (need > 0) PE_CUDA(p, cudaMemcpyAsync(out, p->dTL, sizeof(float) * need, cudaMemcpyDeviceToHost, p->stream));
+  if (ranges)
+    for (size_t i = 0; i < p->tl_ranges.size(); ++i) ranges[i] = p->tl_ranges[i];
+  return check_status(p);
+}
+
+pe_status pe_get_transform_count(pe_plan* p, unsigned long long* count) {
+  if (!p || !count) return PE_ERR_ARG;
+  PE_CUDA(p, cudaMemcpyAsync(count, p->dNdst, sizeof(unsigned long long), cudaMemcpyDeviceToHost, p->stream));
+  PE_CUDA(p, cudaStreamSynchronize(p->stream));
+  return PE_OK;
+}
+
+pe_status pe_dst1(pe_plan* p, const float* in, float* out, int on_device) {
+  if (!p) return PE_ERR_ARG;
+  if (!in || !out) return fail(p, PE_ERR_ARG, "in/out is NULL");
+  float2* tmp = p->dStage;
+  float2* res = nullptr;
+  PE_CUDA(p, cudaMallocAsync(reinterpret_cast<void**>(&res), sizeof(float2) * p->L, p->stream));
+  PE_CUDA(p, cudaMemcpyAsync(tmp, in, sizeof(float2) * p->N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             p->stream));
+  PE_CUDA(p, launch_dst(p->log2L, tmp, res, 1.0f, p->tabs, p->stream));
+  PE_CUDA(p, cudaMemcpyAsync(out, res + 1, sizeof(float2) * p->N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             p->stream));
+  PE_CUDA(p, cudaFreeAsync(res, p->stream));
+  if (!on_device) PE_CUDA(p, cudaStreamSynchronize(p->stream));
+  return PE_OK;
+}
+
+pe_status pe_get_range(const pe_plan* p, double* r, long long* steps) {
+  if (!p) return PE_ERR_ARG;
+  if (r) *r = p->r_set + double(p->steps_done) * p->dr;
+  if (steps) *steps = p->steps_done;
+  return PE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,270 @@
+"""Python binding of the SSSP C ABI (include/sssp.h): argument marshalling only.
+
+Every step of the march runs in the CUDA library ``_build/libsssp.so``; this module only
+converts arguments (numpy arrays for host memory, torch CUDA tensors for device memory,
+torch streams for ordering) and raises ``PEError`` on a non-zero status.  There is no CPU
+fallback: if the library is missing the import of a plan fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+PE_OK = 0
+PE_ERR_ARG = 1
+PE_ERR_CUDA = 2
+PE_ERR_OOM = 3
+PE_ERR_NEUMANN_DIVERGED = 4
+PE_ERR_TIMEOUT = 5
+PE_ERR_STATE = 6
+PE_ERR_NUMERIC = 7
+
+_STATUS_NAMES = {0: "PE_OK", 1: "PE_ERR_ARG", 2: "PE_ERR_CUDA", 3: "PE_ERR_OOM", 4: "PE_ERR_NEUMANN_DIVERGED",
+                 5: "PE_ERR_TIMEOUT", 6: "PE_ERR_STATE", 7: "PE_ERR_NUMERIC"}
+
+
+class PEError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+_sz = ctypes.c_size_t
+
+_SIGNATURES = {
+    "pe_abi_version": (_i, []),
+    "pe_create_error": (ctypes.c_char_p, []),
+    "pe_last_error": (ctypes.c_char_p, [_vp]),
+    "pe_plan_create": (_i, [ctypes.POINTER(_vp), _i, _d, _d, _d, _i, _i, _d, _vp]),
+    "pe_plan_destroy": (None, [_vp]),
+    "pe_set_output": (_i, [_vp, _i]),
+    "pe_set_field": (_i, [_vp, _vp, _i, _d]),
+    "pe_set_profile": (_i, [_vp, _vp, _i, _d, _i]),
+    "pe_set_profiles": (_i, [_vp, _vp, _vp, _i, _i]),
+    "pe_clear_profiles": (_i, [_vp]),
+    "pe_march": (_i, [_vp, _i]),
+    "pe_march_batch": (_i, [ctypes.POINTER(_vp), _i, _i]),
+    "pe_sync": (_i, [_vp]),
+    "pe_read_field": (_i, [_vp, _vp, _i]),
+    "pe_read_TL": (_i, [_vp, _vp, _sz, _vp, ctypes.POINTER(_sz)]),
+    "pe_get_transform_count": (_i, [_vp, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "pe_dst1": (_i, [_vp, _vp, _vp, _i]),
+    "pe_get_range": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
+    "pe_pade_coefficients": (_i, [_d, _i, _vp, _vp, _vp]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libsssp.so (built in-tree by ``build()``); raises if it is missing."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing: run __graft_entry__.build() first")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(status: int, plan_ptr=None):
+    if status != PE_OK:
+        L = lib()
+        msg = L.pe_last_error(plan_ptr).decode() if plan_ptr else L.pe_create_error().decode()
+        raise PEError(status, msg)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _host_c64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex64))
+
+
+def pade_coefficients(sigma: float, p: int):
+    """Host FP64 Pade data of the library: (b, a, d0, d) as complex128 arrays."""
+    b = np.zeros(2 * p)
+    a = np.zeros(2 * p)
+    d = np.zeros(2 * p + 2)
+    _check(lib().pe_pade_coefficients(float(sigma), int(p), b.ctypes.data, a.ctypes.data, d.ctypes.data))
+    return (b[0::2] + 1j * b[1::2], a[0::2] + 1j * a[1::2], complex(d[0], d[1]), d[2::2] + 1j * d[3::2])
+
+
+class Plan:
+    """One range-march problem on the GPU (pe_plan)."""
+
+    def __init__(self, N: int, H: float, k0: float, dr: float, pade_order: int, neumann_terms: int = 0,
+                 neumann_tol: float = 1e-10, stream=None):
+        L = lib()
+        ptr = _vp()
+        s = _stream_ptr(stream)
+        _check(L.pe_plan_create(ctypes.byref(ptr), int(N), float(H), float(k0), float(dr), int(pade_order),
+                                int(neumann_terms), float(neumann_tol), s))
+        self._p = ptr
+        self.N = int(N)
+        self.H, self.k0, self.dr = float(H), float(k0), float(dr)
+        self.pade_order, self.neumann_terms = int(pade_order), int(neumann_terms)
+
+    # -------------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_p", None) is not None and self._p.value:
+            lib().pe_plan_destroy(self._p)
+            self._p = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._p
+
+    def _c(self, status):
+        _check(status, self._p)
+
+    # -------------------------------------------------------------------------------
+    def set_output(self, tl_every: int):
+        self._c(lib().pe_set_output(self._p, int(tl_every)))
+
+    def set_field(self, u, r: float = 0.0):
+        """u: N complex values, numpy (host) or a complex64 CUDA torch tensor (device)."""
+        if _is_torch(u):
+            assert u.is_contiguous() and u.numel() == self.N
+            self._c(lib().pe_set_field(self._p, u.data_ptr(), 1 if u.is_cuda else 0, float(r)))
+        else:
+            h = _host_c64(u)
+            assert h.size == self.N
+            self._c(lib().pe_set_field(self._p, h.ctypes.data, 0, float(r)))
+
+    def set_profile(self, n2, range_m: float = 0.0):
+        if _is_torch(n2):
+            assert n2.is_cuda and n2.is_contiguous() and n2.numel() == self.N
+            self._c(lib().pe_set_profile(self._p, n2.data_ptr(), 0, float(range_m), 1))
+        else:
+            h = np.ascontiguousarray(np.asarray(n2, dtype=np.float32))
+            assert h.size == self.N
+            self._c(lib().pe_set_profile(self._p, h.ctypes.data, 0, float(range_m), 0))
+
+    def set_profiles(self, n2_rows, ranges):
+        r = np.ascontiguousarray(np.asarray(ranges, dtype=np.float64))
+        if _is_torch(n2_rows):
+            assert n2_rows.is_cuda and n2_rows.is_contiguous() and n2_rows.numel() == self.N * r.size
+            self._c(lib().pe_set_profiles(self._p, n2_rows.data_ptr(), r.ctypes.data, int(r.size), 1))
+        else:
+            h = np.ascontiguousarray(np.asarray(n2_rows, dtype=np.float32))
+            assert h.size == self.N * r.size
+            self._c(lib().pe_set_profiles(self._p, h.ctypes.data, r.ctypes.data, int(r.size), 0))
+
+    def set_profile_nodes(self, nodes: Sequence[Tuple[float, np.ndarray]]):
+        """Replace the profile by (range, n2) nodes."""
+        self._c(lib().pe_clear_profiles(self._p))
+        rows = np.stack([np.asarray(n2, dtype=np.float32) for _, n2 in nodes])
+        self.set_profiles(rows, [r for r, _ in nodes])
+
+    def march(self, steps: int):
+        self._c(lib().pe_march(self._p, int(steps)))
+
+    def sync(self):
+        self._c(lib().pe_sync(self._p))
+
+    def read_field(self, out=None):
+        """Field (carrier included) as a complex64 numpy array, or into a CUDA tensor ``out``."""
+        if out is not None and _is_torch(out):
+            assert out.is_contiguous() and out.numel() == self.N
+            self._c(lib().pe_read_field(self._p, out.data_ptr(), 1 if out.is_cuda else 0))
+            return out
+        h = np.empty(self.N, dtype=np.complex64)
+        self._c(lib().pe_read_field(self._p, h.ctypes.data, 0))
+        return h
+
+    def read_tl(self, out=None) -> Tuple[np.ndarray, np.ndarray]:
+        """TL rows (rows, N) float32 and their ranges; ``out`` may be a preallocated host
+        buffer (numpy or pinned torch CPU tensor) of at least rows * N floats."""
+        n = _sz(0)
+        if out is not None:
+            ptr = out.data_ptr() if _is_torch(out) else out.ctypes.data
+            cap = out.numel() if _is_torch(out) else out.size
+            self._c(lib().pe_read_TL(self._p, ptr, cap, None, ctypes.byref(n)))
+            return out, None
+        self._c(lib().pe_read_TL(self._p, None, 0, None, ctypes.byref(n)))
+        rows = n.value
+        out = np.empty((rows, self.N), dtype=np.float32)
+        rng = np.empty(rows, dtype=np.float64)
+        if rows:
+            self._c(lib().pe_read_TL(self._p, out.ctypes.data, out.size, rng.ctypes.data, ctypes.byref(n)))
+        return out, rng
+
+    def transform_count(self) -> int:
+        c = ctypes.c_ulonglong(0)
+        self._c(lib().pe_get_transform_count(self._p, ctypes.byref(c)))
+        return int(c.value)
+
+    def range(self) -> Tuple[float, int]:
+        r = _d(0)
+        s = ctypes.c_longlong(0)
+        self._c(lib().pe_get_range(self._p, ctypes.byref(r), ctypes.byref(s)))
+        return r.value, s.value
+
+    def dst1(self, x):
+        """Unnormalised DST-I of N complex values on the GPU (host numpy in/out)."""
+        if _is_torch(x):
+            import torch
+            out = torch.empty_like(x)
+            self._c(lib().pe_dst1(self._p, x.data_ptr(), out.data_ptr(), 1))
+            return out
+        h = _host_c64(x)
+        out = np.empty_like(h)
+        self._c(lib().pe_dst1(self._p, h.ctypes.data, out.ctypes.data, 0))
+        return out
+
+
+def march_batch(plans: List[Plan], steps: int):
+    """March every plan ``steps`` steps with one kernel launch per grid size."""
+    arr = (_vp * len(plans))(*[p.handle for p in plans])
+    st = lib().pe_march_batch(arr, len(plans), int(steps))
+    if st != PE_OK:
+        raise PEError(st, lib().pe_last_error(plans[0].handle).decode())
+
+
+def plan_for(solve, stream=None, tl_every: int = 0) -> Plan:
+    """Plan, starter field and profile nodes for an ``inputs.Solve`` description."""
+    pl = Plan(solve.N, solve.H, solve.k0, solve.dr, solve.pade_order, solve.neumann_terms, solve.neumann_tol,
+              stream=stream)
+    pl.set_output(tl_every)
+    if solve.neumann_terms > 1:
+        pl.set_profile_nodes(solve.profiles)
+    pl.set_field(solve.u0, solve.r0)
+    return pl

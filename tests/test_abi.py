@@ -1,0 +1,112 @@
+"""CPU tests of the C ABI library: it builds, loads, exports every declared symbol, and its
+host-only logic (FP64 Pade plan, argument validation) agrees with the oracle.  No compute
+call needs a GPU here."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import sssp_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2511_03343_gb300 import build
+    build.build()
+    from paper_2511_03343_gb300 import sssp
+    return sssp.lib()
+
+
+def _declared_symbols():
+    syms = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            syms |= set(re.findall(r"\b(pe_\w+)\s*\(", txt))
+    return syms
+
+
+def test_exports_every_declared_symbol(L):
+    syms = _declared_symbols()
+    assert len(syms) >= 15
+    missing = [s for s in syms if not hasattr(L, s)]
+    assert not missing, missing
+
+
+def test_binding_covers_header():
+    from paper_2511_03343_gb300 import sssp
+    assert _declared_symbols() <= set(sssp._SIGNATURES)
+
+
+def test_abi_version(L):
+    from paper_2511_03343_gb300 import sssp
+    assert sssp.lib().pe_abi_version() == 1
+
+
+@pytest.mark.parametrize("sigma,p,tol", [(2.094, 4, 1e-11), (10.47, 6, 1e-8), (26.18, 8, 1e-7), (52.4, 6, 1e-6)])
+def test_host_pade_matches_oracle(L, sigma, p, tol):
+    """The library's FP64 Baker route against the oracle's: same rational function."""
+    from paper_2511_03343_gb300 import sssp
+    b, a, d0, d = sssp.pade_coefficients(sigma, p)
+    plan = O.pade_plan(sigma, p)
+    # the same poles (as sets) and the conjugate pairing a_j = conj(b_j)
+    for bj in b:
+        assert np.min(np.abs(plan.b - bj)) < tol * max(1, abs(bj))
+    assert np.allclose(a, np.conj(b))
+    lam = np.linspace(-3, 0.5, 101)
+    lib_sum = np.full(lam.shape, d0, dtype=complex)
+    lib_prod = np.ones(lam.shape, dtype=complex)
+    for bj, aj, dj in zip(b, a, d):
+        lib_sum += dj / (1 + bj * lam)
+        lib_prod *= (1 + aj * lam) / (1 + bj * lam)
+    ref = plan.rational(lam)
+    assert np.max(np.abs(lib_sum - ref)) < tol * 10
+    assert np.max(np.abs(lib_prod - ref)) < tol * 10
+
+
+def test_host_pade_rejects_bad_order(L):
+    from paper_2511_03343_gb300 import sssp
+    with pytest.raises(sssp.PEError) as e:
+        sssp.pade_coefficients(2.0, 9)
+    assert e.value.status == sssp.PE_ERR_ARG
+
+
+@pytest.mark.parametrize("args", [
+    dict(N=100, H=100.0, k0=0.4, dr=5.0, pade_order=4),      # N + 1 not a power of two
+    dict(N=3, H=100.0, k0=0.4, dr=5.0, pade_order=4),        # too small
+    dict(N=8191, H=100.0, k0=0.4, dr=5.0, pade_order=4),     # too large for this build
+    dict(N=255, H=-1.0, k0=0.4, dr=5.0, pade_order=4),
+    dict(N=255, H=100.0, k0=0.0, dr=5.0, pade_order=4),
+    dict(N=255, H=100.0, k0=0.4, dr=0.0, pade_order=4),
+    dict(N=255, H=100.0, k0=0.4, dr=5.0, pade_order=0),
+    dict(N=255, H=100.0, k0=0.4, dr=5.0, pade_order=9),
+    dict(N=255, H=100.0, k0=0.4, dr=5.0, pade_order=4, neumann_terms=-1),
+    dict(N=255, H=100.0, k0=0.4, dr=5.0, pade_order=4, neumann_terms=65),
+])
+def test_plan_create_validates_before_device_work(L, args):
+    """Invalid sizes and values are rejected on the host with PE_ERR_ARG (no CUDA call)."""
+    from paper_2511_03343_gb300 import sssp
+    with pytest.raises(sssp.PEError) as e:
+        sssp.Plan(**args)
+    assert e.value.status == sssp.PE_ERR_ARG
+    assert sssp.lib().pe_create_error().decode()
+
+
+def test_product_path_has_no_oracle_import():
+    """The package never imports the oracle (it is test infrastructure only)."""
+    pkg = os.path.join(ROOT, "paper_2511_03343_gb300")
+    pat = re.compile(r"^\s*(from\s+oracle\b|import\s+oracle\b)|sssp_oracle", re.M)
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                assert not pat.search(open(os.path.join(dirpath, f)).read()), f
+
+
+def test_oracle_has_no_product_import():
+    txt = open(os.path.join(ROOT, "oracle", "sssp_oracle.py")).read()
+    assert "paper_2511_03343_gb300" not in txt

@@ -1,0 +1,249 @@
+"""GPU parity of the CUDA marcher against the FP64 oracle, through the C ABI.
+
+Tolerances: the field relative L2 error <= 1e-4 and |TL_gpu - TL_oracle| <= 0.1 dB wherever the
+oracle's TL < 100 dB (the stated bar for complex64 fields).  Transform-level checks use the
+FP32 rounding bound of a length-L FFT (a few 1e-6 relative).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import sssp_oracle as O
+from paper_2511_03343_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-4
+TL_TOL = 0.1
+
+
+@pytest.fixture(scope="module")
+def sssp():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2511_03343_gb300 import build
+    build.build()
+    from paper_2511_03343_gb300 import sssp as S
+    S.lib()
+    return S
+
+
+def _oracle(s, steps=None, tl_every=1):
+    g = O.Grid(N=s.N, H=s.H, k0=s.k0, dr=s.dr)
+    return O.march(s.u0, s.profiles, g, s.pade_order, steps or s.steps, s.neumann_terms, s.neumann_tol,
+                   r0=s.r0, tl_every=tl_every)
+
+
+def _gpu(sssp, s, steps=None, tl_every=1):
+    pl = sssp.plan_for(s, tl_every=tl_every)
+    pl.march(steps or s.steps)
+    u = pl.read_field()
+    tl, rng = pl.read_tl()
+    nd = pl.transform_count()
+    pl.close()
+    return u, tl, rng, nd
+
+
+def _compare(u, tl, ref, field_tol=FIELD_TOL, tl_tol=TL_TOL):
+    rel = np.linalg.norm(u - ref.u) / np.linalg.norm(ref.u)
+    assert rel <= field_tol, f"field rel L2 {rel:.3e}"
+    if ref.tl.size:
+        assert tl.shape == ref.tl.shape
+        mask = ref.tl < 100
+        dtl = np.max(np.abs(tl.astype(np.float64) - ref.tl)[mask])
+        assert dtl <= tl_tol, f"max TL error {dtl:.3e} dB"
+    return rel
+
+
+# ----------------------------------------------------------------------------- S2/S4 transform
+@pytest.mark.parametrize("N", [7, 15, 31, 63, 127, 255, 511, 1023, 2047, 4095])
+def test_dst1_matches_oracle(sssp, N):
+    rng = np.random.default_rng(N)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    pl = sssp.Plan(N, 100.0, 0.4, 5.0, 4)
+    X = pl.dst1(x.astype(np.complex64))
+    ref = O.dst1(x)
+    err = np.max(np.abs(X - ref)) / np.max(np.abs(ref))
+    assert err < 2e-6 * math.log2(N + 1), err
+    # DST-I is its own inverse up to 2/(N+1)
+    back = pl.dst1(X) * (2.0 / (N + 1))
+    assert np.max(np.abs(back - x)) / np.max(np.abs(x)) < 4e-6 * math.log2(N + 1)
+    pl.close()
+
+
+def test_dst1_single_mode(sssp):
+    """A sampled sine mode transforms to ((N+1)/2) delta (the closed form)."""
+    N, m0 = 1023, 37
+    n = np.arange(1, N + 1)
+    pl = sssp.Plan(N, 100.0, 0.4, 5.0, 4)
+    X = pl.dst1(np.sin(np.pi * n * m0 / (N + 1)).astype(np.complex64))
+    ref = np.zeros(N)
+    ref[m0 - 1] = (N + 1) / 2
+    assert np.max(np.abs(X - ref)) < 1e-3
+    pl.close()
+
+
+# ----------------------------------------------------------------------------- workloads
+def test_isovelocity_full(sssp):
+    """Isovelocity Dirichlet guide, N = 255, 1000 steps of 5 m, [4/4], no Neumann terms."""
+    s = inputs.isovelocity()
+    u, tl, _, nd = _gpu(sssp, s)
+    ref = _oracle(s)
+    _compare(u, tl, ref)
+    assert nd == s.steps + 1  # one TL transform per step + the final field
+
+
+def test_munk_short(sssp):
+    """Range-independent Munk, N = 1023, f = 50 Hz, [6/6], Neumann 1e-10 / 12 terms, 150 steps."""
+    s = inputs.munk(N=1023, steps=150)
+    u, tl, _, _ = _gpu(sssp, s)
+    ref = _oracle(s)
+    _compare(u, tl, ref)
+
+
+def test_munk_full_size_against_stored_oracle(sssp):
+    """The full Munk workload (N = 4095, 2000 steps) against the stored FP64 oracle run
+    (tests/golden/munk_n4095_s2000.txt): sampled final field and TL rows."""
+    import importlib.util
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    meta, fidx, fref, tl_r, tl_ref = mg.load()
+    s = inputs.munk()
+    pl = sssp.plan_for(s, tl_every=int(meta["tl_every"]))
+    pl.march(s.steps)
+    u = pl.read_field()
+    tl, rng = pl.read_tl()
+    pl.close()
+    rel = np.linalg.norm(u[fidx] - fref) / np.linalg.norm(fref)
+    assert rel <= FIELD_TOL, rel
+    assert abs(np.linalg.norm(u) / meta["norm"] - 1) < 1e-4
+    assert np.allclose(rng, tl_r)
+    tsub = tl[:, ::int(meta["tl_stride"])].astype(np.float64)
+    mask = tl_ref < 100
+    assert np.max(np.abs(tsub - tl_ref)[mask]) <= TL_TOL
+
+
+def test_range_dependent_eddy(sssp):
+    """Munk + Gaussian eddy with a profile node per step (midpoint rule), N = 511, [8/8]."""
+    s = inputs.munk_eddy(N=511, freq=60.0, dr=25.0, steps=120, seed=3)
+    # move the eddy centre into the marched range so the profile really changes
+    z = s.z
+    cm = inputs.munk_c(z)
+    s.profiles = [(n * s.dr, inputs.n2_from_c(cm + inputs.gaussian_eddy_dc((n + 0.5) * s.dr, z, s.eddy_dc, r0=1500.0,
+                                                                            Lr=800.0), s.c0))
+                  for n in range(s.steps)]
+    u, tl, _, _ = _gpu(sssp, s)
+    ref = _oracle(s)
+    _compare(u, tl, ref)
+
+
+@pytest.mark.parametrize("N,p,terms", [(7, 1, 12), (15, 8, 12), (31, 4, 3), (63, 6, 12), (127, 2, 12)])
+def test_small_grids_and_orders(sssp, N, p, terms):
+    """Tiny grids (partial warps, a single thread for N = 7), Pade orders 1..8, few terms."""
+    s = inputs.munk(N=N, freq=10.0, dr=50.0, steps=40, pade_order=p, neumann_terms=terms)
+    u, tl, _, _ = _gpu(sssp, s)
+    ref = _oracle(s)
+    _compare(u, tl, ref)
+
+
+def test_single_term_ignores_profile(sssp):
+    """neumann_terms = 1 keeps only t_0: the isovelocity step with V ignored (Fig. 1a)."""
+    s = inputs.munk(N=255, freq=25.0, steps=50, neumann_terms=1)
+    u, tl, _, _ = _gpu(sssp, s)
+    iso = inputs.munk(N=255, freq=25.0, steps=50, neumann_terms=1)
+    iso.profiles = [(0.0, np.ones(255))]
+    ref = _oracle(iso)
+    _compare(u, tl, ref)
+
+
+# ----------------------------------------------------------------------------- API behaviour
+def test_marches_compose_bitwise(sssp):
+    s = inputs.munk(N=511, freq=30.0, steps=30)
+    a = sssp.plan_for(s, tl_every=1)
+    a.march(30)
+    ua = a.read_field()
+    tla, ra = a.read_tl()
+    b = sssp.plan_for(s, tl_every=1)
+    b.march(10)
+    b.march(20)
+    ub = b.read_field()
+    tlb, rb = b.read_tl()
+    assert np.array_equal(ua, ub) and np.array_equal(tla, tlb) and np.array_equal(ra, rb)
+    assert b.range() == (30 * s.dr, 30)
+
+
+def test_tl_decimation(sssp):
+    s = inputs.isovelocity(steps=50)
+    pl = sssp.plan_for(s, tl_every=7)
+    pl.march(50)
+    tl, rng = pl.read_tl()
+    ref = _oracle(s, tl_every=7)
+    assert tl.shape == (7, s.N)
+    assert np.allclose(rng, ref.tl_ranges)
+    assert np.max(np.abs(tl - ref.tl)[ref.tl < 100]) <= TL_TOL
+
+
+def test_batch_alone_vs_mix(sssp):
+    """Uneven sizes and frequencies in one batched march give the same bits as alone."""
+    solves = [inputs.munk(N=255, freq=20.0, steps=25), inputs.munk(N=1023, freq=45.0, steps=25),
+              inputs.munk(N=255, freq=33.0, steps=25, pade_order=4), inputs.isovelocity(N=511, steps=25)]
+    alone = []
+    for s in solves:
+        pl = sssp.plan_for(s, tl_every=5)
+        pl.march(25)
+        alone.append((pl.read_field(), pl.read_tl()[0]))
+        pl.close()
+    plans = [sssp.plan_for(s, tl_every=5) for s in solves]
+    sssp.march_batch(plans, 25)
+    for pl, (u, tl) in zip(plans, alone):
+        assert np.array_equal(pl.read_field(), u)
+        assert np.array_equal(pl.read_tl()[0], tl)
+        pl.close()
+
+
+def test_state_errors(sssp):
+    pl = sssp.Plan(255, 5000.0, 0.2, 50.0, 6, 12)
+    with pytest.raises(sssp.PEError) as e:
+        pl.march(1)
+    assert e.value.status == sssp.PE_ERR_STATE
+    pl.set_field(np.ones(255, dtype=np.complex64))
+    with pytest.raises(sssp.PEError) as e:
+        pl.march(1)  # Neumann terms requested but no profile
+    assert e.value.status == sssp.PE_ERR_STATE
+    pl.set_profile(np.ones(255), 100.0)
+    with pytest.raises(sssp.PEError) as e:
+        pl.set_profile(np.ones(255), 50.0)  # decreasing range
+    assert e.value.status == sssp.PE_ERR_ARG
+    with pytest.raises(sssp.PEError) as e:
+        pl._c(sssp.lib().pe_set_profile(pl.handle, np.ones(255, dtype=np.float32).ctypes.data, 1, 200.0, 0))
+    assert e.value.status == sssp.PE_ERR_ARG
+    pl.close()
+
+
+def test_neumann_divergence_is_reported(sssp):
+    """A profile far outside the Neumann series' convergence region (rho >> 1) makes the term
+    norms grow; the kernel stops the march and the host reads PE_ERR_NEUMANN_DIVERGED."""
+    N = 63
+    pl = sssp.Plan(N, 100.0, 0.4, 5.0, 4, 12, 1e-10)
+    pl.set_profile(np.full(N, 40.0), 0.0)
+    pl.set_field(np.ones(N, dtype=np.complex64))
+    pl.march(3)
+    with pytest.raises(sssp.PEError) as e:
+        pl.sync()
+    assert e.value.status == sssp.PE_ERR_NEUMANN_DIVERGED
+    pl.close()
+
+
+def test_norm_conserved_full_munk(sssp):
+    """P5 at full size: for real n^2 the Pade operator is unitary, so ||u|| is conserved over
+    the whole 2000-step Munk march (a property that needs no oracle run)."""
+    s = inputs.munk()
+    pl = sssp.plan_for(s)
+    pl.march(s.steps)
+    u = pl.read_field()
+    pl.close()
+    assert abs(np.linalg.norm(u) / np.linalg.norm(s.u0) - 1) < 5e-5
