@@ -43,7 +43,7 @@ typedef enum {
   PE_ERR_ARG = 1,               /* invalid argument or unsupported size                  */
   PE_ERR_CUDA = 2,              /* a CUDA runtime call failed (message holds the error)   */
   PE_ERR_OOM = 3,               /* device allocation failed                              */
-  PE_ERR_NEUMANN_DIVERGED = 4,  /* Neumann term norms grew for 3 consecutive terms        */
+  PE_ERR_NEUMANN_DIVERGED = 4,  /* a Neumann term grew to 1e4 x the first correction term */
   PE_ERR_TIMEOUT = 5,           /* a bounded device wait expired                         */
   PE_ERR_STATE = 6,             /* call out of order (e.g. march before set_field)        */
   PE_ERR_NUMERIC = 7            /* a non-finite value appeared in the march               */
@@ -148,7 +148,8 @@ pe_status pe_read_field(pe_plan* plan, float* out, int to_device);
 /*
  * Copy the recorded TL rows (row i: N floats, row-major) into `out` (host memory,
  * capacity `cap` floats) and their ranges into `ranges` (may be NULL; capacity
- * cap / N doubles).  *n_rows receives the number of rows recorded.  Synchronises.
+ * cap / N doubles).  *n_rows receives the number of rows recorded.  With out = NULL only
+ * *n_rows is set (size query).  Synchronises.
  * Errors: PE_ERR_ARG if cap is smaller than rows * N.
  */
 pe_status pe_read_TL(pe_plan* plan, float* out, size_t cap, double* ranges, size_t* n_rows);

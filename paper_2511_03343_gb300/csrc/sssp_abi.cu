@@ -303,7 +303,8 @@ pe_status check_status(pe_plan* p) {
   int s = 0;
   PE_CUDA(p, cudaMemcpyAsync(&s, p->dStatus, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
   PE_CUDA(p, cudaStreamSynchronize(p->stream));
-  if (s == sssp::kStatusDiverged) return fail(p, PE_ERR_NEUMANN_DIVERGED, "Neumann series diverged (term norms grew for 3 consecutive terms)");
+  if (s == sssp::kStatusDiverged)
+    return fail(p, PE_ERR_NEUMANN_DIVERGED, "Neumann series diverged (a term grew to 1e4 times the first correction)");
   if (s == sssp::kStatusNumeric) return fail(p, PE_ERR_NUMERIC, "non-finite value in the march");
   if (s != 0) return fail(p, PE_ERR_CUDA, "device status " + std::to_string(s));
   return PE_OK;
@@ -621,7 +622,8 @@ pe_status pe_read_TL(pe_plan* p, float* out, size_t cap, double* ranges, size_t*
   if (!p) return PE_ERR_ARG;
   const size_t need = size_t(p->tl_rows) * p->N;
   if (n_rows) *n_rows = size_t(p->tl_rows);
-  if (need > 0 && (!out || cap < need)) return fail(p, PE_ERR_ARG, "TL buffer too small");
+  if (!out) return PE_OK;  // size query
+  if (cap < need) return fail(p, PE_ERR_ARG, "TL buffer too small");
   if (need > 0) PE_CUDA(p, cudaMemcpyAsync(out, p->dTL, sizeof(float) * need, cudaMemcpyDeviceToHost, p->stream));
   if (ranges)
     for (size_t i = 0; i < p->tl_ranges.size(); ++i) ranges[i] = p->tl_ranges[i];
