@@ -183,7 +183,7 @@ def bench_ours(args):
     from paper_2511_03343_gb300 import build as B
     B.build()
     from paper_2511_03343_gb300 import inputs, sssp
-    s = inputs.munk()
+    s = inputs.munk(steps=args.range_steps)
     stream = torch.cuda.current_stream()
     pl = sssp.Plan(s.N, s.H, s.k0, s.dr, s.pade_order, s.neumann_terms, s.neumann_tol, stream=stream)
     pl.set_output(1)
@@ -238,14 +238,14 @@ def bench_ours(args):
     # parity of the bench's own output
     tl, _ = pl.read_tl()
     u = pl.read_field()
-    parity = _golden_check(tl, u)
+    parity = _golden_check(tl, u) if s.steps == 2000 else None
 
     # end to end through the public API with host (pinned) buffers
     u0_host = torch.from_numpy(s.u0.astype(np.complex64)).pin_memory()
     tl_host = torch.empty(s.steps * s.N, dtype=torch.float32).pin_memory()
     field_host = torch.empty(s.N, dtype=torch.complex64).pin_memory()
     e2e_ms = []
-    for i in range(args.warmup + args.steps):
+    for i in range(0 if args.no_e2e else args.warmup + args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -256,7 +256,7 @@ def bench_ours(args):
         el = time.perf_counter() - t0
         if i >= args.warmup:
             e2e_ms.append(el * 1e3)
-    e2e_tot = sum(e2e_ms)
+    e2e_tot = sum(e2e_ms) if e2e_ms else float("nan")
     if world > 1:
         t = torch.tensor([e2e_tot], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -302,6 +302,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-sample-steps", type=int, default=10)
+    ap.add_argument("--range-steps", type=int, default=2000,
+                    help="range steps per march (2000 = the workload; fewer only for profiler captures)")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)

@@ -285,7 +285,7 @@ __device__ __forceinline__ void store8(float2* p, const float2 (&v)[8]) {
 // TL row after a step: physical envelope u = (2/L) DST(y), TL = -20 log10|u| + 10 log10 r.
 template <int LOG2L>
 __device__ __forceinline__ void record_tl(Smem<LOG2L>& sm, const SolveDesc& d, const float2 (&y)[8], float out_scale,
-                                          int s, long long nrec) {
+                                          int s, int nrec) {
   const int t = threadIdx.x;
 #pragma unroll
   for (int i = 0; i < 8; ++i) sm.bufA[pidx(8 * t + i)] = out_scale * y[i];
@@ -312,18 +312,25 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
   constexpr int L = C::L;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<LOG2L> sm(smem_raw);
-  const SolveDesc& d = descs[blockIdx.x];
+  __shared__ SolveDesc d;
   const int t = threadIdx.x;
   const int lane = t & 31, warp = t >> 5;
+  {  // the descriptor lives in shared memory so its fields need no registers
+    const int* src = reinterpret_cast<const int*>(descs + blockIdx.x);
+    int* dst = reinterpret_cast<int*>(&d);
+    for (int i = t; i < int(sizeof(SolveDesc) / sizeof(int)); i += C::NT) dst[i] = src[i];
+  }
   load_tables<LOG2L>(sm.tw, sm.sinw, tw_g, sin_g);
+  __syncthreads();
 
   float2 y[8];
   load8<LOG2L>(d.yhat + 8 * t, y);
   const float out_scale = 2.0f / float(L);
   const bool iso = d.terms <= 1;
+  const float tol2f = float(d.tol2);
   int status = kStatusOk;
-  unsigned long long ndst = 0;
-  long long nrec = 0;
+  unsigned int ndst = 0;
+  int nrec = 0;
   int node = d.node0;
   double next_r = (node + 1 < d.nodes) ? d.node_r[node + 1] : 1e300;
   if (!iso) {
@@ -382,7 +389,7 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
         __syncthreads();
         dst_block<LOG2L>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // t_0 in depth space
         ++ndst;
-        double first = 0.0;
+        float first = 0.f;
         for (int m = 1; m < d.terms; ++m) {
 #pragma unroll
           for (int i = 0; i < 8; ++i) sm.bufA[pidx(8 * t + i)] = sm.Vs[8 * t + i] * tp[i];
@@ -413,10 +420,13 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
           }
           __syncthreads();
           if (last) break;
-          double snt = 0.0, snw = 0.0;
-          for (int w = 0; w < C::NW; ++w) {
-            snt += sm.red[2 * w];
-            snw += sm.red[2 * w + 1];
+          // block totals: lane w of every warp holds warp w's partials, then a shuffle sum
+          float snt = (lane < C::NW) ? sm.red[2 * lane] : 0.f;
+          float snw = (lane < C::NW) ? sm.red[2 * lane + 1] : 0.f;
+#pragma unroll
+          for (int o = C::NW / 2; o > 0; o >>= 1) {
+            snt += __shfl_xor_sync(C::MASK, snt, o, C::WS);
+            snw += __shfl_xor_sync(C::MASK, snw, o, C::WS);
           }
           if (!isfinite(snt) || !isfinite(snw)) {
             status = kStatusNumeric;
@@ -426,11 +436,11 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
           // alone is no evidence: the operator b_j L_j^{-1} V is not normal, so convergent
           // series can grow transiently.)
           if (m == 1) first = snt;
-          else if (snt > 1e8 * first) {
+          else if (first > 0.f && snt > 1e8f * first) {
             status = kStatusDiverged;
             break;
           }
-          if (snt <= d.tol2 * snw) break;
+          if (snt <= tol2f * snw) break;
           dst_block<LOG2L>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // t_m in depth space
           ++ndst;
         }
@@ -461,7 +471,7 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
   store8<LOG2L>(d.field + 8 * t, u);
   if (t == 0) {
     if (status != kStatusOk) atomicMax(d.status, status);
-    atomicAdd(d.ndst, ndst);
+    atomicAdd(d.ndst, (unsigned long long)ndst);
   }
 }
 

@@ -128,16 +128,18 @@ def test_munk_full_size_against_stored_oracle(sssp):
 
 
 def test_range_dependent_eddy(sssp):
-    """Munk + Gaussian eddy with a profile node per step (midpoint rule), N = 511, [8/8]."""
-    s = inputs.munk_eddy(N=511, freq=60.0, dr=25.0, steps=120, seed=3)
-    # move the eddy centre into the marched range so the profile really changes
+    """Munk + Gaussian eddy with a profile node per step (midpoint rule), N = 511, 100 Hz, [8/8].
+    The eddy is centred inside the marched range so the profile changes every step."""
+    s = inputs.munk_eddy(N=511, freq=100.0, dr=25.0, steps=80, seed=3)
     z = s.z
     cm = inputs.munk_c(z)
-    s.profiles = [(n * s.dr, inputs.n2_from_c(cm + inputs.gaussian_eddy_dc((n + 0.5) * s.dr, z, s.eddy_dc, r0=1500.0,
-                                                                            Lr=800.0), s.c0))
+    s.profiles = [(n * s.dr, inputs.n2_from_c(cm + inputs.gaussian_eddy_dc((n + 0.5) * s.dr, z, s.eddy_dc, r0=1000.0,
+                                                                            Lr=600.0), s.c0))
                   for n in range(s.steps)]
     u, tl, _, _ = _gpu(sssp, s)
     ref = _oracle(s)
+    # the oracle run itself is inside the Neumann series' convergence region
+    assert abs(np.linalg.norm(ref.u) / np.linalg.norm(s.u0) - 1) < 1e-7
     _compare(u, tl, ref)
 
 
@@ -145,6 +147,9 @@ def test_range_dependent_eddy(sssp):
 def test_small_grids_and_orders(sssp, N, p, terms):
     """Tiny grids (partial warps, a single thread for N = 7), Pade orders 1..8, few terms."""
     s = inputs.munk(N=N, freq=10.0, dr=50.0, steps=40, pade_order=p, neumann_terms=terms)
+    # an O(1) field made of the low sine modes (the 10 Hz Gaussian is below the grid scale)
+    n = np.arange(1, N + 1)
+    s.u0 = sum(np.sin(np.pi * n * m / (N + 1)) * (1.0 + 0.5j * m) / m for m in range(1, min(N, 5) + 1))
     u, tl, _, _ = _gpu(sssp, s)
     ref = _oracle(s)
     _compare(u, tl, ref)
