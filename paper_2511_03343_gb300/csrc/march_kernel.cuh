@@ -420,11 +420,13 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
           }
           __syncthreads();
           if (last) break;
-          // block totals: lane w of every warp holds warp w's partials, then a shuffle sum
+          // block totals: lane w of every warp holds warp w's partials (0 beyond NW), then a
+          // butterfly sum over the whole warp so that EVERY lane holds the same total — the
+          // stop decision below must be uniform across the block (it guards __syncthreads).
           float snt = (lane < C::NW) ? sm.red[2 * lane] : 0.f;
           float snw = (lane < C::NW) ? sm.red[2 * lane + 1] : 0.f;
 #pragma unroll
-          for (int o = C::NW / 2; o > 0; o >>= 1) {
+          for (int o = C::WS / 2; o > 0; o >>= 1) {
             snt += __shfl_xor_sync(C::MASK, snt, o, C::WS);
             snw += __shfl_xor_sync(C::MASK, snw, o, C::WS);
           }
