@@ -66,7 +66,7 @@ template <int LOG2L>
 struct Cfg {
   static constexpr int L = 1 << LOG2L;
   static constexpr int NT = L / 8;            // threads per CTA, 8 points each
-  static constexpr int PADL = L + L / 8;      // padded buffer length
+  static constexpr int PADL = L + L / 16;     // padded buffer length
   static constexpr int WS = NT >= 32 ? 32 : NT;
   static constexpr int NW = (NT + 31) / 32;
   static constexpr unsigned MASK = NT >= 32 ? 0xffffffffu : ((1u << NT) - 1u);
@@ -77,7 +77,9 @@ struct Cfg {
                                  sizeof(float2) * NW + sizeof(float) * 2 * NW;
 };
 
-__device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
+// padded shared-memory index: one pad element per 16 (128 B), so contiguous half-warp
+// accesses stay conflict-free and the stride-4 / stride-8 patterns spread over the banks
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
 
 __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -132,10 +134,13 @@ __device__ __forceinline__ void dftR(float2 (&v)[R]) {
 
 // One Stockham pass of radix R over span NS: butterfly j reads src[j + r L/R], applies the
 // twiddles exp(-2 pi i r k/(NS R)), k = j mod NS, and writes dst[(j - k) R + k + r NS].
+// Twiddles come from a per-pass table tw[(NS - 8) + (r - 1) NS + k] (k contiguous, so a
+// half-warp reads 16 consecutive entries or broadcasts).
 template <int LOG2L, int R, int NS>
 __device__ __forceinline__ void fft_pass(const float2* __restrict__ src, float2* __restrict__ dst,
                                          const float2* __restrict__ tw) {
   constexpr int L = 1 << LOG2L, NT = L / 8, NB = L / R, PER = NB / NT;
+  constexpr int OFF = NS - 8;
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int j = threadIdx.x + q * NT;
@@ -144,7 +149,7 @@ __device__ __forceinline__ void fft_pass(const float2* __restrict__ src, float2*
     for (int r = 0; r < R; ++r) v[r] = src[pidx(j + r * NB)];
     const int k = j & (NS - 1);
 #pragma unroll
-    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * k * (L / (NS * R))]);
+    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[OFF + (r - 1) * NS + k]);
     dftR<R>(v);
     const int base = (j - k) * R + k;
 #pragma unroll

@@ -29,7 +29,7 @@ constexpr int kMaxTerms = 64;
 thread_local std::string g_create_error;
 
 struct TransformTables {
-  float2* tw = nullptr;  // L twiddles exp(-2 pi i q/L)
+  float2* tw = nullptr;  // per-pass Stockham twiddles (L - 8 used entries)
   float* sinw = nullptr; // L weights sin(pi n/L)
 };
 
@@ -46,12 +46,18 @@ cudaError_t get_tables(int device, int log2L, TransformTables* out) {
     return cudaSuccess;
   }
   const int L = 1 << log2L;
-  std::vector<float2> tw(L);
+  std::vector<float2> tw(L, make_float2(0.f, 0.f));
   std::vector<float> sw(L);
-  for (int q = 0; q < L; ++q) {
-    const double ang = 2.0 * M_PI * double(q) / double(L);
-    tw[q] = make_float2(float(std::cos(ang)), float(-std::sin(ang)));
-    sw[q] = float(std::sin(M_PI * double(q) / double(L)));
+  for (int q = 0; q < L; ++q) sw[q] = float(std::sin(M_PI * double(q) / double(L)));
+  // per-pass Stockham twiddles exp(-2 pi i r k/(NS R)) at (NS - 8) + (r - 1) NS + k for the
+  // passes after the first (spans NS = 8, 64, ...; radix R = min(8, L/NS)); L - 8 entries
+  for (int ns = 8; ns < L; ns *= 8) {
+    const int R = std::min(8, L / ns);
+    for (int r = 1; r < R; ++r)
+      for (int k = 0; k < ns; ++k) {
+        const double ang = 2.0 * M_PI * double(r) * double(k) / (double(ns) * double(R));
+        tw[(ns - 8) + (r - 1) * ns + k] = make_float2(float(std::cos(ang)), float(-std::sin(ang)));
+      }
   }
   TransformTables t;
   cudaError_t e = cudaMalloc(&t.tw, sizeof(float2) * L);
