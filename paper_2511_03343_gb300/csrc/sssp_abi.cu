@@ -505,7 +505,7 @@ pe_status pe_set_field(pe_plan* p, const float* u, int on_device, double r) {
   return PE_OK;
 }
 
-static pe_status append_nodes(pe_plan* p, const float* n2, const double* ranges, int count, int on_device) {
+static pe_status append_nodes(pe_plan* p, const double* n2, const double* ranges, int count, int on_device) {
   for (int i = 0; i < count; ++i) {
     const double prev = (p->nodes + i > 0) ? (i > 0 ? ranges[i - 1] : p->node_r.back()) : -1e300;
     if (!std::isfinite(ranges[i]) || ranges[i] < prev) return fail(p, PE_ERR_ARG, "profile ranges must be finite and non-decreasing");
@@ -514,11 +514,11 @@ static pe_status append_nodes(pe_plan* p, const float* n2, const double* ranges,
   if (st != PE_OK) return st;
   // V = n^2 - 1 with V[0] = 0 (boundary); converted on the host in FP64
   std::vector<float> host;
-  std::vector<float> src;
-  const float* s = n2;
+  std::vector<double> src;
+  const double* s = n2;
   if (on_device) {
     src.resize(size_t(count) * p->N);
-    PE_CUDA(p, cudaMemcpyAsync(src.data(), n2, sizeof(float) * src.size(), cudaMemcpyDeviceToHost, p->stream));
+    PE_CUDA(p, cudaMemcpyAsync(src.data(), n2, sizeof(double) * src.size(), cudaMemcpyDeviceToHost, p->stream));
     PE_CUDA(p, cudaStreamSynchronize(p->stream));
     s = src.data();
   }
@@ -526,9 +526,9 @@ static pe_status append_nodes(pe_plan* p, const float* n2, const double* ranges,
   for (int i = 0; i < count; ++i) {
     host[size_t(i) * p->L] = 0.0f;
     for (int n = 0; n < p->N; ++n) {
-      const float v = s[size_t(i) * p->N + n];
+      const double v = s[size_t(i) * p->N + n];
       if (!std::isfinite(v)) return fail(p, PE_ERR_ARG, "n2 must be finite");
-      host[size_t(i) * p->L + n + 1] = float(double(v) - 1.0);
+      host[size_t(i) * p->L + n + 1] = float(v - 1.0);
     }
   }
   PE_CUDA(p, cudaMemcpyAsync(p->dV + size_t(p->nodes) * p->L, host.data(), sizeof(float) * host.size(),
@@ -540,14 +540,14 @@ static pe_status append_nodes(pe_plan* p, const float* n2, const double* ranges,
   return PE_OK;
 }
 
-pe_status pe_set_profile(pe_plan* p, const float* n2, int is_complex, double range, int on_device) {
+pe_status pe_set_profile(pe_plan* p, const double* n2, int is_complex, double range, int on_device) {
   if (!p) return PE_ERR_ARG;
   if (!n2) return fail(p, PE_ERR_ARG, "n2 is NULL");
   if (is_complex) return fail(p, PE_ERR_ARG, "complex n2 is not supported by this build");
   return append_nodes(p, n2, &range, 1, on_device);
 }
 
-pe_status pe_set_profiles(pe_plan* p, const float* n2, const double* ranges, int count, int on_device) {
+pe_status pe_set_profiles(pe_plan* p, const double* n2, const double* ranges, int count, int on_device) {
   if (!p) return PE_ERR_ARG;
   if (!n2 || !ranges || count < 0) return fail(p, PE_ERR_ARG, "n2/ranges NULL or count < 0");
   return append_nodes(p, n2, ranges, count, on_device);

@@ -170,28 +170,32 @@ class Plan:
             self._c(lib().pe_set_field(self._p, h.ctypes.data, 0, float(r)))
 
     def set_profile(self, n2, range_m: float = 0.0):
+        """n^2 at the N depth points (FP64: numpy float64, or a float64 CUDA tensor)."""
         if _is_torch(n2):
-            assert n2.is_cuda and n2.is_contiguous() and n2.numel() == self.N
+            import torch
+            assert n2.is_cuda and n2.is_contiguous() and n2.numel() == self.N and n2.dtype == torch.float64
             self._c(lib().pe_set_profile(self._p, n2.data_ptr(), 0, float(range_m), 1))
         else:
-            h = np.ascontiguousarray(np.asarray(n2, dtype=np.float32))
+            h = np.ascontiguousarray(np.asarray(n2, dtype=np.float64))
             assert h.size == self.N
             self._c(lib().pe_set_profile(self._p, h.ctypes.data, 0, float(range_m), 0))
 
     def set_profiles(self, n2_rows, ranges):
         r = np.ascontiguousarray(np.asarray(ranges, dtype=np.float64))
         if _is_torch(n2_rows):
+            import torch
             assert n2_rows.is_cuda and n2_rows.is_contiguous() and n2_rows.numel() == self.N * r.size
+            assert n2_rows.dtype == torch.float64
             self._c(lib().pe_set_profiles(self._p, n2_rows.data_ptr(), r.ctypes.data, int(r.size), 1))
         else:
-            h = np.ascontiguousarray(np.asarray(n2_rows, dtype=np.float32))
+            h = np.ascontiguousarray(np.asarray(n2_rows, dtype=np.float64))
             assert h.size == self.N * r.size
             self._c(lib().pe_set_profiles(self._p, h.ctypes.data, r.ctypes.data, int(r.size), 0))
 
     def set_profile_nodes(self, nodes: Sequence[Tuple[float, np.ndarray]]):
         """Replace the profile by (range, n2) nodes."""
         self._c(lib().pe_clear_profiles(self._p))
-        rows = np.stack([np.asarray(n2, dtype=np.float32) for _, n2 in nodes])
+        rows = np.stack([np.asarray(n2, dtype=np.float64) for _, n2 in nodes])
         self.set_profiles(rows, [r for r, _ in nodes])
 
     def march(self, steps: int):

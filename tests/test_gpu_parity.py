@@ -240,7 +240,7 @@ def test_state_errors(sssp):
         pl.set_profile(np.ones(255), 50.0)  # decreasing range
     assert e.value.status == sssp.PE_ERR_ARG
     with pytest.raises(sssp.PEError) as e:
-        pl._c(sssp.lib().pe_set_profile(pl.handle, np.ones(255, dtype=np.float32).ctypes.data, 1, 200.0, 0))
+        pl._c(sssp.lib().pe_set_profile(pl.handle, np.ones(255, dtype=np.float64).ctypes.data, 1, 200.0, 0))
     assert e.value.status == sssp.PE_ERR_ARG
     pl.close()
 
