@@ -172,6 +172,24 @@ pe_status pe_get_transform_count(pe_plan* plan, unsigned long long* count);
  */
 pe_status pe_dst1(pe_plan* plan, const float* in, float* out, int on_device);
 
+/*
+ * pe_dst1 for callers that cannot allocate device memory.  (The paper has no counterpart:
+ * this is a deployment variant of the transform, not a step of the method.)
+ *
+ * Same result as pe_dst1 (unnormalised DST-I of N complex64 values, in and out in device
+ * memory, ordered on `cuda_stream`, NULL = legacy default stream) but no plan and no
+ * allocation: the staged input and the length-(N+1) result live in a fixed scratch array
+ * compiled into the library.  It is meant for applications that reserve all GPU memory up
+ * front and forbid later cudaMalloc calls, or that run inside a framework whose allocator
+ * owns every device buffer.
+ *   N  interior points; N + 1 a power of two in [8, 4096] (larger sizes: PE_ERR_ARG).
+ * The first call on a device performs that device's set-up (array addresses, tables);
+ * make it before any stream capture.  All calls share the scratch array, which keeps the
+ * last call's contents: calls that overlap on the GPU race and must be ordered by the
+ * caller.  Errors: PE_ERR_ARG (NULL pointers, unsupported N), PE_ERR_CUDA.
+ */
+pe_status pe_dst1_noalloc(const float* in, float* out, int N, void* cuda_stream);
+
 /* Current range of the field and number of steps marched since pe_set_field. */
 pe_status pe_get_range(const pe_plan* plan, double* r, long long* steps);
 

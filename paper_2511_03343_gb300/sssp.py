@@ -58,6 +58,7 @@ _SIGNATURES = {
     "pe_read_TL": (_i, [_vp, _vp, _sz, _vp, ctypes.POINTER(_sz)]),
     "pe_get_transform_count": (_i, [_vp, ctypes.POINTER(ctypes.c_ulonglong)]),
     "pe_dst1": (_i, [_vp, _vp, _vp, _i]),
+    "pe_dst1_noalloc": (_i, [_vp, _vp, _i, _vp]),
     "pe_get_range": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
     "pe_pade_coefficients": (_i, [_d, _i, _vp, _vp, _vp]),
 }
