@@ -15,7 +15,8 @@
  *
  * Conventions
  *  - Grid: N interior points z_n = n H/(N+1), n = 1..N.  N + 1 must be a power of two
- *    in [8, 4096] for this build.  Fields are N complex64 values stored as interleaved
+ *    in [8, 65536] for this build (up to 4096 the whole march runs in one CTA's shared
+ *    memory; larger grids use a per-plan workspace of 4 (N+1) complex values in HBM).  Fields are N complex64 values stored as interleaved
  *    float pairs (re, im), index n-1 for z_n.
  *  - Every function returns a pe_status; PE_OK is 0.  On failure the plan (if any) keeps
  *    a message readable with pe_last_error().  No C++ exception crosses this boundary.
@@ -56,7 +57,7 @@ int pe_abi_version(void);
  * Create a plan.  Section 2 (Pade [p/p] of exp(i sigma (sqrt(1+X) - 1)), sigma = k0 dr,
  * coefficients by Baker's linear system in FP64 on the host) and Section 3 (tables of
  * the isovelocity inverse 1/(1 + b_j lambda_m)).
- *   N             interior depth points; N + 1 a power of two in [8, 4096]
+ *   N             interior depth points; N + 1 a power of two in [8, 65536]
  *   H             depth of the guide [m], > 0
  *   k0            reference wavenumber omega/c0 [1/m], > 0
  *   dr            range step [m], > 0

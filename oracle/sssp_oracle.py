@@ -166,6 +166,19 @@ def dst1(x: np.ndarray) -> np.ndarray:
     return out
 
 
+def dst1_at(x: np.ndarray, ms) -> np.ndarray:
+    """Selected DST-I outputs X_m = sum_{n=1..N} x_n sin(pi n m/(N+1)), one explicit O(N) sum per
+    requested m (for grids too large for the full matrix)."""
+    x = np.asarray(x)
+    N = x.shape[0]
+    L = N + 1
+    n = np.arange(1, N + 1, dtype=np.int64)
+    out = []
+    for m in ms:
+        out.append(np.sum(x * np.sin(np.pi * ((n * int(m)) % (2 * L)).astype(np.float64) / L)))
+    return np.array(out)
+
+
 def idst1(X: np.ndarray) -> np.ndarray:
     """Inverse DST-I: x = (2/(N+1)) DST-I(X)."""
     return (2.0 / (X.shape[0] + 1)) * dst1(X)

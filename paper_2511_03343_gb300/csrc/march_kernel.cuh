@@ -43,6 +43,7 @@ struct SolveDesc {
   const float* V;        // nodes x L, V = n^2 - 1
   const double* node_r;  // node ranges, non-decreasing
   float2* yhat;          // L  spectral state (DST-I coefficients, unnormalised)
+  float2* work;          // 4 L workspace (grids beyond one CTA's shared memory only)
   float2* field;         // L  physical envelope written at the end of the march
   float* tl;             // TL rows, N floats each
   int* status;           // device status word

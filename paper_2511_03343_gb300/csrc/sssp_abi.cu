@@ -14,6 +14,7 @@
 
 #include "../../include/sssp.h"
 #include "march_kernel.cuh"
+#include "march_large.cuh"
 #include "pade_host.h"
 
 using sssp::Cfg;
@@ -23,7 +24,8 @@ using cd = std::complex<double>;
 namespace {
 
 constexpr int kMinLog2 = 3;
-constexpr int kMaxLog2 = 12;
+constexpr int kMaxSmemLog2 = 12;   // one CTA, everything in shared memory
+constexpr int kMaxLog2 = 16;       // beyond: global-memory workspace (march_large.cuh)
 constexpr int kMaxTerms = 64;
 
 thread_local std::string g_create_error;
@@ -97,6 +99,7 @@ struct pe_plan {
   float2* dYhat = nullptr;
   float2* dField = nullptr;
   float2* dStage = nullptr;  // N-value staging buffer (set / read field)
+  float2* dWork = nullptr;   // 4 L workspace for grids beyond one CTA's shared memory
   float* dV = nullptr;
   double* dNodeR = nullptr;
   int nodes = 0, node_cap = 0;
@@ -164,6 +167,19 @@ cudaError_t launch_dst_t(const float2* in, float2* out, float scale, const Trans
   return cudaGetLastError();
 }
 
+template <int LOG2L>
+cudaError_t launch_march_large_t(const SolveDesc* dDescs, int count, const TransformTables& tabs, cudaStream_t st) {
+  sssp::sssp_march_large_kernel<LOG2L><<<count, sssp::kLargeNT, 0, st>>>(dDescs, tabs.tw, tabs.sinw);
+  return cudaGetLastError();
+}
+
+template <int LOG2L>
+cudaError_t launch_dst_large_t(const float2* in, float2* out, float scale, float2* work, const TransformTables& tabs,
+                               cudaStream_t st) {
+  sssp::sssp_dst_large_kernel<LOG2L><<<1, sssp::kLargeNT, 0, st>>>(in, out, scale, work, tabs.tw, tabs.sinw);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_march(int log2L, const SolveDesc* d, int count, const TransformTables& tabs, cudaStream_t st) {
   switch (log2L) {
     case 3: return launch_march_t<3>(d, count, tabs, st);
@@ -176,13 +192,21 @@ cudaError_t launch_march(int log2L, const SolveDesc* d, int count, const Transfo
     case 10: return launch_march_t<10>(d, count, tabs, st);
     case 11: return launch_march_t<11>(d, count, tabs, st);
     case 12: return launch_march_t<12>(d, count, tabs, st);
+    case 13: return launch_march_large_t<13>(d, count, tabs, st);
+    case 14: return launch_march_large_t<14>(d, count, tabs, st);
+    case 15: return launch_march_large_t<15>(d, count, tabs, st);
+    case 16: return launch_march_large_t<16>(d, count, tabs, st);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_dst(int log2L, const float2* in, float2* out, float scale, const TransformTables& tabs,
-                       cudaStream_t st) {
+                       cudaStream_t st, float2* work = nullptr) {
   switch (log2L) {
+    case 13: return launch_dst_large_t<13>(in, out, scale, work, tabs, st);
+    case 14: return launch_dst_large_t<14>(in, out, scale, work, tabs, st);
+    case 15: return launch_dst_large_t<15>(in, out, scale, work, tabs, st);
+    case 16: return launch_dst_large_t<16>(in, out, scale, work, tabs, st);
     case 3: return launch_dst_t<3>(in, out, scale, tabs, st);
     case 4: return launch_dst_t<4>(in, out, scale, tabs, st);
     case 5: return launch_dst_t<5>(in, out, scale, tabs, st);
@@ -281,6 +305,7 @@ pe_status prepare_desc(pe_plan* p, int steps, SolveDesc* d) {
   d->V = p->dV;
   d->node_r = p->dNodeR;
   d->yhat = p->dYhat;
+  d->work = p->dWork;
   d->field = p->dField;
   d->tl = p->dTL;
   d->status = p->dStatus;
@@ -357,6 +382,7 @@ void pe_plan_destroy(pe_plan* p) {
   cudaFree(p->dYhat);
   cudaFree(p->dField);
   cudaFree(p->dStage);
+  cudaFree(p->dWork);
   cudaFree(p->dV);
   cudaFree(p->dNodeR);
   cudaFree(p->dStatus);
@@ -376,7 +402,7 @@ pe_status pe_plan_create(pe_plan** out, int N, double H, double k0, double dr, i
   *out = nullptr;
   const int log2L = ilog2_exact(N + 1);
   if (N < 1 || log2L < kMinLog2 || log2L > kMaxLog2) {
-    g_create_error = "N + 1 must be a power of two in [8, 4096]";
+    g_create_error = "N + 1 must be a power of two in [8, 65536]";
     return PE_ERR_ARG;
   }
   if (!(H > 0) || !(k0 > 0) || !(dr > 0) || !std::isfinite(H) || !std::isfinite(k0) || !std::isfinite(dr)) {
@@ -462,6 +488,9 @@ pe_status pe_plan_create(pe_plan** out, int N, double H, double k0, double dr, i
   if ((e = cudaMalloc(&p->dField, sizeof(float2) * L)) != cudaSuccess) return bail(e, "cudaMalloc");
   if ((e = cudaMalloc(&p->dStage, sizeof(float2) * L)) != cudaSuccess) return bail(e, "cudaMalloc");
   if ((e = cudaMalloc(&p->dStatus, sizeof(int))) != cudaSuccess) return bail(e, "cudaMalloc");
+  if (log2L > kMaxSmemLog2 &&
+      (e = cudaMalloc(&p->dWork, sizeof(float2) * sssp::large_work_elems(L))) != cudaSuccess)
+    return bail(e, "cudaMalloc(workspace)");
   if ((e = cudaMalloc(&p->dNdst, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMalloc");
   if ((e = cudaMalloc(&p->dDesc, sizeof(SolveDesc))) != cudaSuccess) return bail(e, "cudaMalloc");
   if ((e = cudaMemcpy(p->dR, R.data(), sizeof(float4) * R.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "upload");
@@ -491,7 +520,7 @@ pe_status pe_set_field(pe_plan* p, const float* u, int on_device, double r) {
   if (!std::isfinite(r)) return fail(p, PE_ERR_ARG, "r must be finite");
   PE_CUDA(p, cudaMemcpyAsync(p->dStage, u, sizeof(float2) * p->N,
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
-  PE_CUDA(p, launch_dst(p->log2L, p->dStage, p->dYhat, 1.0f, p->tabs, p->stream));
+  PE_CUDA(p, launch_dst(p->log2L, p->dStage, p->dYhat, 1.0f, p->tabs, p->stream, p->dWork));
   // the physical field as given (index 0 = boundary)
   PE_CUDA(p, cudaMemsetAsync(p->dField, 0, sizeof(float2), p->stream));
   PE_CUDA(p, cudaMemcpyAsync(p->dField + 1, p->dStage, sizeof(float2) * p->N, cudaMemcpyDeviceToDevice, p->stream));
@@ -651,7 +680,7 @@ pe_status pe_dst1(pe_plan* p, const float* in, float* out, int on_device) {
   PE_CUDA(p, cudaMallocAsync(reinterpret_cast<void**>(&res), sizeof(float2) * p->L, p->stream));
   PE_CUDA(p, cudaMemcpyAsync(tmp, in, sizeof(float2) * p->N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                              p->stream));
-  PE_CUDA(p, launch_dst(p->log2L, tmp, res, 1.0f, p->tabs, p->stream));
+  PE_CUDA(p, launch_dst(p->log2L, tmp, res, 1.0f, p->tabs, p->stream, p->dWork));
   PE_CUDA(p, cudaMemcpyAsync(out, res + 1, sizeof(float2) * p->N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                              p->stream));
   PE_CUDA(p, cudaFreeAsync(res, p->stream));

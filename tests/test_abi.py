@@ -79,7 +79,7 @@ def test_host_pade_rejects_bad_order(L):
 @pytest.mark.parametrize("args", [
     dict(N=100, H=100.0, k0=0.4, dr=5.0, pade_order=4),      # N + 1 not a power of two
     dict(N=3, H=100.0, k0=0.4, dr=5.0, pade_order=4),        # too small
-    dict(N=8191, H=100.0, k0=0.4, dr=5.0, pade_order=4),     # too large for this build
+    dict(N=131071, H=100.0, k0=0.4, dr=5.0, pade_order=4),   # too large for this build
     dict(N=255, H=-1.0, k0=0.4, dr=5.0, pade_order=4),
     dict(N=255, H=100.0, k0=0.0, dr=5.0, pade_order=4),
     dict(N=255, H=100.0, k0=0.4, dr=0.0, pade_order=4),

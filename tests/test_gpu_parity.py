@@ -77,6 +77,21 @@ def test_dst1_matches_oracle(sssp, N):
     pl.close()
 
 
+@pytest.mark.parametrize("N", [8191, 16383, 32767, 65535])
+def test_dst1_large_sampled(sssp, N):
+    """Grids beyond one CTA's shared memory: sampled outputs against the oracle's explicit sums."""
+    rng = np.random.default_rng(N)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    pl = sssp.Plan(N, 100.0, 0.4, 5.0, 4)
+    X = pl.dst1(x.astype(np.complex64))
+    pl.close()
+    ms = np.concatenate([[1, 2, 3, N // 2, N // 2 + 1, N - 1, N], rng.integers(1, N + 1, 25)])
+    ref = O.dst1_at(x, ms)
+    scale = np.sqrt(N / 2.0) * np.sqrt(2.0)  # typical |X_m| for unit-variance complex input
+    err = np.max(np.abs(X[ms - 1] - ref)) / scale
+    assert err < 2e-6 * math.log2(N + 1), err
+
+
 def test_dst1_single_mode(sssp):
     """A sampled sine mode transforms to ((N+1)/2) delta (the closed form)."""
     N, m0 = 1023, 37
@@ -145,6 +160,41 @@ def test_range_dependent_eddy(sssp):
     # the oracle run itself is inside the Neumann series' convergence region
     assert abs(np.linalg.norm(ref.u) / np.linalg.norm(s.u0) - 1) < 1e-7
     _compare(u, tl, ref)
+
+
+def test_munk_large_grid_short(sssp):
+    """Munk on N = 8191 (the global-workspace kernel), 100 Hz, [6/6], 12 terms, 8 steps."""
+    s = inputs.munk(N=8191, freq=100.0, dr=25.0, steps=8)
+    u, tl, _, _ = _gpu(sssp, s)
+    ref = _oracle(s)
+    _compare(u, tl, ref)
+
+
+def test_eddy_n16383_short(sssp):
+    """The range-dependent workload's grid and Pade order (N = 16383, 250 Hz, [8/8], dr = 25 m,
+    profile node per step) for its first 3 steps against the oracle."""
+    s = inputs.munk_eddy(steps=3)
+    u, tl, _, _ = _gpu(sssp, s)
+    ref = _oracle(s)
+    _compare(u, tl, ref)
+
+
+def test_isovelocity_mode_n65535(sssp):
+    """N = 65535, isovelocity: a single sine mode is an eigenvector of the step, so after n steps
+    it is (e^{i sigma} R(lambda_m))^n times itself (closed form, any size)."""
+    N, m0, steps = 65535, 40, 30
+    s = inputs.isovelocity(N=N, H=5000.0, freq=200.0, dr=25.0, steps=steps, pade_order=8)
+    z = s.z
+    s.u0 = np.sin(np.pi * m0 * z / s.H).astype(np.complex128)
+    pl = sssp.plan_for(s)
+    pl.march(steps)
+    u = pl.read_field()
+    pl.close()
+    plan = O.pade_plan(s.k0 * s.dr, 8)
+    lam = -(np.pi * m0 / (s.k0 * s.H)) ** 2
+    G = np.exp(1j * s.k0 * s.dr) * plan.rational(lam)
+    ref = G ** steps * s.u0
+    assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < 1e-5
 
 
 @pytest.mark.parametrize("N,p,terms", [(7, 1, 12), (15, 8, 12), (31, 4, 3), (63, 6, 12), (127, 2, 12)])

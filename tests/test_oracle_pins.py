@@ -48,6 +48,13 @@ def pin_dst_single_mode(N=31, m0=5):
     return np.max(np.abs(X - ref))
 
 
+def pin_dst_at(N=127):
+    """The one-output-at-a-time sums agree with the full sine-matrix DST-I."""
+    x = _rng_field(N, 11)
+    ms = [1, 2, 5, 64, 126, 127]
+    return np.max(np.abs(O.dst1_at(x, ms) - O.dst1(x)[np.array(ms) - 1]))
+
+
 def pin_idst_roundtrip(N=63):
     x = _rng_field(N, 2)
     return np.max(np.abs(O.idst1(O.dst1(x)) - x))
@@ -195,6 +202,10 @@ def test_dst_against_scipy():
 
 def test_dst_single_mode():
     assert pin_dst_single_mode() < 1e-12
+
+
+def test_dst_at():
+    assert pin_dst_at() < 1e-11
 
 
 def test_idst_roundtrip():
