@@ -172,6 +172,73 @@ def _golden_check(tl, u):
             "against": "stored FP64 oracle run (tests/golden/munk_n4095_s2000.txt)"}
 
 
+def bench_other(args):
+    """Secondary workloads (not the headline line): 'batch' = 256 Munk solves N = 1023,
+    f ~ U[50, 500] Hz (default_rng(4)), dr = 25 m, 2000 steps, [6/6], Neumann 12 terms, marched
+    together by pe_march_batch (one launch, one CTA per solve); 'eddy' = Munk + Gaussian eddy,
+    N = 16383, 250 Hz, dr = 25 m, [8/8], a profile node per step; 'iso' = isovelocity N = 255."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2511_03343_gb300 import build as B
+    B.build()
+    from paper_2511_03343_gb300 import inputs, sssp
+    stream = torch.cuda.current_stream()
+    steps = args.range_steps
+    if args.workload == "batch":
+        solves = inputs.munk_batch(count=args.batch_count, steps=steps)
+    elif args.workload == "eddy":
+        solves = [inputs.munk_eddy(steps=steps)]
+    else:
+        solves = [inputs.isovelocity(steps=steps)]
+    plans = []
+    for s in solves:
+        pl = sssp.Plan(s.N, s.H, s.k0, s.dr, s.pade_order, s.neumann_terms, s.neumann_tol, stream=stream)
+        pl.set_output(1)
+        if s.neumann_terms > 1:
+            pl.set_profile_nodes(s.profiles)
+        plans.append(pl)
+    u0s = [torch.from_numpy(s.u0.astype(np.complex64)).cuda() for s in solves]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one():
+        for pl, u0 in zip(plans, u0s):
+            pl.set_field(u0, 0.0)
+        if len(plans) == 1:
+            plans[0].march(steps)
+        else:
+            sssp.march_batch(plans, steps)
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    nd0 = sum(pl.transform_count() for pl in plans)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    nd1 = sum(pl.transform_count() for pl in plans)
+    units = sum(s.N * steps for s in solves) * args.steps
+    tot = sum(ms)
+    line = {"metric": METRIC, "value": units / (tot * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": args.workload, "solves": len(solves), "N": [s.N for s in solves][:1],
+                       "range_steps": steps},
+            "dst_per_step": (nd1 - nd0) / args.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    for pl in plans:
+        pl.close()
+
+
 def bench_ours(args):
     import numpy as np
     import torch
@@ -305,9 +372,13 @@ def main():
     ap.add_argument("--range-steps", type=int, default=2000,
                     help="range steps per march (2000 = the workload; fewer only for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="munk", choices=["munk", "batch", "eddy", "iso"])
+    ap.add_argument("--batch-count", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
+    elif args.workload != "munk":
+        bench_other(args)
     else:
         bench_ours(args)
 

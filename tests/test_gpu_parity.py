@@ -318,3 +318,21 @@ def test_norm_conserved_full_munk(sssp):
     u = pl.read_field()
     pl.close()
     assert abs(np.linalg.norm(u) / np.linalg.norm(s.u0) - 1) < 5e-5
+
+
+def test_batch_workload_sampled_solves(sssp):
+    """The 256-solve Munk batch (N = 1023, f ~ U[50, 500] Hz, dr = 25 m, [6/6], 12 terms) marched in
+    one batched launch for 60 steps; three sampled solves (lowest, median and highest frequency)
+    against the oracle."""
+    solves = inputs.munk_batch(steps=60)
+    plans = [sssp.plan_for(s, tl_every=20) for s in solves]
+    sssp.march_batch(plans, 60)
+    freqs = np.array([s.freq for s in solves])
+    for idx in [int(np.argmin(freqs)), int(np.argsort(freqs)[128]), int(np.argmax(freqs))]:
+        s = solves[idx]
+        u = plans[idx].read_field()
+        tl, _ = plans[idx].read_tl()
+        ref = _oracle(s, tl_every=20)
+        _compare(u, tl, ref)
+    for pl in plans:
+        pl.close()
