@@ -30,11 +30,12 @@ def sssp():
     return S
 
 
-def _oracle(s, steps=None, tl_every=1, form="sum"):
-    """The oracle march.  The paper's Algorithm 1 uses the sum form; the GPU marches the
-    product form, which is the same operator once the Neumann series has converged (pin P7).
-    A series cut short after a few terms is a different approximation in each form, so those
-    cases compare against the oracle's product form."""
+def _oracle(s, steps=None, tl_every=1, form="product"):
+    """The oracle march.  The GPU marches the product form; the paper's Algorithm 1 writes the
+    sum form.  The two are the same operator once the Neumann series has converged (pin P7),
+    but a series cut short by the term limit (few terms, or a slowly converging low-frequency
+    case) is a different approximation in each form, so by default the GPU is compared with
+    the oracle's product form; converged workloads are also compared with the sum form."""
     g = O.Grid(N=s.N, H=s.H, k0=s.k0, dr=s.dr)
     return O.march(s.u0, s.profiles, g, s.pade_order, steps or s.steps, s.neumann_terms, s.neumann_tol,
                    r0=s.r0, tl_every=tl_every, form=form)
@@ -109,7 +110,7 @@ def test_isovelocity_full(sssp):
     """Isovelocity Dirichlet guide, N = 255, 1000 steps of 5 m, [4/4], no Neumann terms."""
     s = inputs.isovelocity()
     u, tl, _, nd = _gpu(sssp, s)
-    ref = _oracle(s)
+    ref = _oracle(s, form="sum")
     _compare(u, tl, ref)
     assert nd == s.steps + 1  # one TL transform per step + the final field
 
@@ -118,8 +119,8 @@ def test_munk_short(sssp):
     """Range-independent Munk, N = 1023, f = 50 Hz, [6/6], Neumann 1e-10 / 12 terms, 150 steps."""
     s = inputs.munk(N=1023, steps=150)
     u, tl, _, _ = _gpu(sssp, s)
-    ref = _oracle(s)
-    _compare(u, tl, ref)
+    _compare(u, tl, _oracle(s, form="sum"))   # converged series: Algorithm 1's sum form
+    _compare(u, tl, _oracle(s))
 
 
 def test_munk_full_size_against_stored_oracle(sssp):
@@ -205,7 +206,7 @@ def test_small_grids_and_orders(sssp, N, p, terms):
     n = np.arange(1, N + 1)
     s.u0 = sum(np.sin(np.pi * n * m / (N + 1)) * (1.0 + 0.5j * m) / m for m in range(1, min(N, 5) + 1))
     u, tl, _, _ = _gpu(sssp, s)
-    ref = _oracle(s, form="sum" if terms >= 12 else "product")
+    ref = _oracle(s)
     _compare(u, tl, ref)
 
 
