@@ -139,6 +139,19 @@ pe_status pe_march(pe_plan* plan, int steps);
  */
 pe_status pe_march_batch(pe_plan** plans, int count, int steps);
 
+/*
+ * As pe_march_batch, but plan i advances steps[i] >= 0 steps (0: left untouched).  Plans of
+ * equal size still share one launch; each CTA marches its own count.
+ */
+pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count);
+
+/*
+ * Device bytes a plan of this size will hold (tables, state, `nodes` profile rows, `tl_rows`
+ * TL rows, workspace for N + 1 > 4096): the unit of the serving loop's memory budget.
+ * Host-only; no GPU needed.
+ */
+size_t pe_plan_bytes_estimate(int N, int pade_order, int nodes, long long tl_rows);
+
 /* Wait for the plan's stream; returns a device-side error raised by an earlier march. */
 pe_status pe_sync(pe_plan* plan);
 
@@ -200,6 +213,47 @@ pe_status pe_get_range(const pe_plan* plan, double* r, long long* steps);
  * d[2p + 2] = (d0, d_1..d_p) of the sum form.  Runs without a GPU.
  */
 pe_status pe_pade_coefficients(double sigma, int p, double* b, double* a, double* d);
+
+/* ------------------------------------------------------------------------------------
+ * Serving loop (continuous batching).  The paper marches one solve at a time; this is the
+ * deployment form: many independent marches share the GPU.  Requests queue in arrival order;
+ * each pe_server_step admits queued requests while a slot is free and their device bytes
+ * (pe_plan_bytes_estimate) fit in the remaining budget, advances every live solve by up to
+ * `chunk_steps` range steps in one batched march, and retires finished ones (field and TL
+ * rows copied to host memory, plan freed).  A solve's result is bit-identical to marching it
+ * alone.  The server is not thread-safe.
+ * ------------------------------------------------------------------------------------ */
+typedef struct pe_server pe_server;
+
+typedef struct {
+  int N;                 /* interior depth points (as pe_plan_create) */
+  double H, k0, dr;
+  int pade_order, neumann_terms;
+  double neumann_tol;
+  long long steps;       /* range steps to march */
+  int tl_every;          /* TL row every tl_every steps (0: none) */
+  const float* u0;       /* starter, N interleaved complex64, host; copied at submit */
+  const double* n2;      /* nodes x N FP64 n^2 rows, host (NULL when neumann_terms <= 1) */
+  const double* node_r;  /* node ranges, non-decreasing */
+  int nodes;
+  double r0;             /* range of the starter */
+} pe_request;
+
+/* hbm_budget_bytes > 0, max_live >= 1 concurrent solves, chunk_steps >= 1 steps per launch. */
+pe_status pe_server_create(pe_server** out, size_t hbm_budget_bytes, int max_live, int chunk_steps, void* cuda_stream);
+void pe_server_destroy(pe_server* server);
+const char* pe_server_error(const pe_server* server);
+/* Queue a request (inputs copied); *id identifies it.  PE_ERR_OOM if it can never fit. */
+pe_status pe_server_submit(pe_server* server, const pe_request* request, unsigned long long* id);
+/* Admit, march every live solve one chunk, retire.  Outputs may be NULL.  Synchronises. */
+pe_status pe_server_step(pe_server* server, int* live, int* queued, int* completed);
+/* state: 0 queued, 1 running, 2 done, 3 failed. */
+pe_status pe_server_state(pe_server* server, unsigned long long id, int* state);
+/* Copy a finished request's field (2N floats) and TL rows (rows x N floats, capacity tl_cap)
+ * and release it; with field = tl = NULL only *rows is set. */
+pe_status pe_server_take(pe_server* server, unsigned long long id, float* field, float* tl, size_t tl_cap,
+                         size_t* rows);
+pe_status pe_server_stats(pe_server* server, size_t* bytes_in_use, size_t* peak_bytes, int* peak_live);
 
 #ifdef __cplusplus
 }

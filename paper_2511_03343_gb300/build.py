@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["sssp_abi.cu", "sssp_noalloc.cu"]
-CXX_SOURCES = ["pade_host.cpp"]
+CXX_SOURCES = ["pade_host.cpp", "sssp_server.cpp"]
 
 
 def _nvcc() -> str:

@@ -600,21 +600,23 @@ pe_status pe_march(pe_plan* p, int steps) {
   return PE_OK;
 }
 
-pe_status pe_march_batch(pe_plan** plans, int count, int steps) {
-  if (!plans || count < 0) return PE_ERR_ARG;
+pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
+  if (!plans || !steps || count < 0) return PE_ERR_ARG;
   if (count == 0) return PE_OK;
   pe_plan* p0 = plans[0];
   if (!p0) return PE_ERR_ARG;
   for (int i = 0; i < count; ++i) {
     if (!plans[i]) return fail(p0, PE_ERR_ARG, "NULL plan in batch");
     if (plans[i]->device != p0->device) return fail(p0, PE_ERR_ARG, "plans on different devices");
+    if (steps[i] < 0) return fail(p0, PE_ERR_ARG, "steps must be >= 0");
   }
-  // group by size, one launch per group
+  // group by size, one launch per group; every CTA marches its own plan its own step count
   std::map<int, std::vector<SolveDesc>> groups;
   std::map<int, TransformTables> tabs;
   for (int i = 0; i < count; ++i) {
+    if (steps[i] == 0) continue;
     SolveDesc d;
-    pe_status st = prepare_desc(plans[i], steps, &d);
+    pe_status st = prepare_desc(plans[i], steps[i], &d);
     if (st != PE_OK) {
       p0->err = plans[i]->err;
       return st;
@@ -622,7 +624,6 @@ pe_status pe_march_batch(pe_plan** plans, int count, int steps) {
     groups[plans[i]->log2L].push_back(d);
     tabs[plans[i]->log2L] = plans[i]->tabs;
   }
-  if (steps == 0) return PE_OK;
   for (auto& kv : groups) {
     SolveDesc* dd = nullptr;
     const size_t bytes = sizeof(SolveDesc) * kv.second.size();
@@ -632,6 +633,26 @@ pe_status pe_march_batch(pe_plan** plans, int count, int steps) {
     PE_CUDA(p0, cudaFreeAsync(dd, p0->stream));
   }
   return PE_OK;
+}
+
+pe_status pe_march_batch(pe_plan** plans, int count, int steps) {
+  if (!plans || count < 0) return PE_ERR_ARG;
+  std::vector<int> st(size_t(count), steps);
+  if (steps < 0) {
+    if (count > 0 && plans[0]) return fail(plans[0], PE_ERR_ARG, "steps must be >= 0");
+    return PE_ERR_ARG;
+  }
+  return pe_march_batch_steps(plans, st.data(), count);
+}
+
+size_t pe_plan_bytes_estimate(int N, int pade_order, int nodes, long long tl_rows) {
+  const size_t L = size_t(N) + 1, p = size_t(pade_order > 0 ? pade_order : 0);
+  size_t b = L * p * (sizeof(float4) + 2 * sizeof(float2));      // R, A, B tables
+  b += L * sizeof(float4) + 3 * L * sizeof(float2);               // G, spectral state, field, staging
+  b += size_t(nodes > 0 ? nodes : 0) * (L * sizeof(float) + sizeof(double));
+  b += size_t(tl_rows > 0 ? tl_rows : 0) * size_t(N) * sizeof(float);
+  if (L > (size_t(1) << kMaxSmemLog2)) b += sssp::large_work_elems(int(L)) * sizeof(float2);
+  return b + 1024;
 }
 
 pe_status pe_sync(pe_plan* p) {

@@ -1,0 +1,86 @@
+"""Trace replay for the serving loop (pe_server_*): arrivals in real time, continuous batching on
+the GPU, per-request latency (arrival -> result on the host) and throughput.
+
+The work itself runs in the CUDA library through ``sssp.Server``; this module only turns trace
+entries (``inputs.serving_trace``) into requests and keeps the clock.
+"""
+from __future__ import annotations
+
+import math
+import time
+from typing import Dict, List
+
+import numpy as np
+
+from . import inputs
+from . import sssp
+
+
+def build_solve(req: Dict, range_scale: float = 1.0, node_spacing: float = 5000.0) -> inputs.Solve:
+    """The march of one trace entry: isovelocity (V ignored), Munk, or Munk + Gaussian eddy with
+    a profile node every ``node_spacing`` metres (evaluated at the node's centre)."""
+    steps = max(1, int(math.ceil(req["range_m"] * range_scale / req["dr"])))
+    if req["env"] == "isovelocity":
+        s = inputs.isovelocity(N=req["N"], H=req["H"], freq=req["freq"], dr=req["dr"], steps=steps,
+                               pade_order=req["pade_order"], zs=req["zs"])
+        return s
+    s = inputs.munk(N=req["N"], H=req["H"], freq=req["freq"], dr=req["dr"], steps=steps,
+                    pade_order=req["pade_order"], zs=req["zs"])
+    if req["env"] == "munk_eddy":
+        z = s.z
+        cm = inputs.munk_c(z)
+        rng_total = steps * req["dr"]
+        nodes = []
+        r = 0.0
+        while r < rng_total or not nodes:
+            rc = r + 0.5 * node_spacing
+            nodes.append((r, inputs.n2_from_c(cm + inputs.gaussian_eddy_dc(rc, z, req["eddy_dc"], r0=req["eddy_r0"]),
+                                              s.c0)))
+            r += node_spacing
+        s.profiles = nodes
+    return s
+
+
+def replay(trace: List[Dict], hbm_budget: float, chunk_steps: int = 50, tl_every: int = 10,
+           range_scale: float = 1.0, max_live: int = 1024, stream=None, keep_results: bool = False):
+    """Replay ``trace`` against a fresh server; returns latency / throughput figures."""
+    srv = sssp.Server(int(hbm_budget), max_live=max_live, chunk_steps=chunk_steps, stream=stream)
+    order = sorted(range(len(trace)), key=lambda i: trace[i]["t_arrival"])
+    pending = list(order)
+    running = {}     # id -> (trace index, arrival wall time)
+    lat = {}
+    units = 0
+    results = {}
+    t0 = time.perf_counter()
+    nsteps = 0
+    while pending or running:
+        now = time.perf_counter() - t0
+        while pending and trace[pending[0]]["t_arrival"] <= now:
+            i = pending.pop(0)
+            s = build_solve(trace[i], range_scale)
+            rid = srv.submit(s, tl_every=tl_every)
+            running[rid] = (i, t0 + trace[i]["t_arrival"], s.N * s.steps, s)
+        if not running:
+            time.sleep(max(0.0, trace[pending[0]]["t_arrival"] - (time.perf_counter() - t0)))
+            continue
+        srv.step()
+        nsteps += 1
+        tnow = time.perf_counter()
+        for rid in list(running):
+            if srv.state(rid) >= 2:
+                i, ta, u, s = running.pop(rid)
+                lat[i] = tnow - ta
+                units += u
+                f, tl = srv.take(rid)
+                if keep_results:
+                    results[i] = (f, tl, s)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    L = np.array([lat[i] for i in sorted(lat)])
+    out = {"requests": len(trace), "wall_s": wall, "server_steps": nsteps,
+           "throughput": units / wall, "p50_s": float(np.percentile(L, 50)), "p99_s": float(np.percentile(L, 99)),
+           "mean_s": float(L.mean()), "peak_live": st["peak_live"], "peak_bytes": st["peak_bytes"]}
+    if keep_results:
+        out["results"] = results
+    return out

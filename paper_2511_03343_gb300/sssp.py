@@ -61,7 +61,24 @@ _SIGNATURES = {
     "pe_dst1_noalloc": (_i, [_vp, _vp, _i, _vp]),
     "pe_get_range": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
     "pe_pade_coefficients": (_i, [_d, _i, _vp, _vp, _vp]),
+    "pe_march_batch_steps": (_i, [ctypes.POINTER(_vp), _vp, _i]),
+    "pe_plan_bytes_estimate": (_sz, [_i, _i, _i, ctypes.c_longlong]),
+    "pe_server_create": (_i, [ctypes.POINTER(_vp), _sz, _i, _i, _vp]),
+    "pe_server_destroy": (None, [_vp]),
+    "pe_server_error": (ctypes.c_char_p, [_vp]),
+    "pe_server_submit": (_i, [_vp, _vp, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "pe_server_step": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "pe_server_state": (_i, [_vp, ctypes.c_ulonglong, ctypes.POINTER(_i)]),
+    "pe_server_take": (_i, [_vp, ctypes.c_ulonglong, _vp, _vp, _sz, ctypes.POINTER(_sz)]),
+    "pe_server_stats": (_i, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz), ctypes.POINTER(_i)]),
 }
+
+
+class PERequest(ctypes.Structure):
+    """Mirror of ``pe_request`` (include/sssp.h)."""
+    _fields_ = [("N", _i), ("H", _d), ("k0", _d), ("dr", _d), ("pade_order", _i), ("neumann_terms", _i),
+                ("neumann_tol", _d), ("steps", ctypes.c_longlong), ("tl_every", _i), ("u0", _vp), ("n2", _vp),
+                ("node_r", _vp), ("nodes", _i), ("r0", _d)]
 
 
 def library_path() -> str:
@@ -254,6 +271,88 @@ class Plan:
         out = np.empty_like(h)
         self._c(lib().pe_dst1(self._p, h.ctypes.data, out.ctypes.data, 0))
         return out
+
+
+def plan_bytes_estimate(N: int, pade_order: int, nodes: int, tl_rows: int) -> int:
+    return int(lib().pe_plan_bytes_estimate(int(N), int(pade_order), int(nodes), int(tl_rows)))
+
+
+class Server:
+    """The continuous-batching serving loop (pe_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_live: int = 512, chunk_steps: int = 50, stream=None):
+        ptr = _vp()
+        st = lib().pe_server_create(ctypes.byref(ptr), int(hbm_budget_bytes), int(max_live), int(chunk_steps),
+                                    _stream_ptr(stream))
+        if st != PE_OK:
+            raise PEError(st, "pe_server_create")
+        self._s = ptr
+        self._keep = {}
+
+    def _c(self, st):
+        if st != PE_OK:
+            raise PEError(st, lib().pe_server_error(self._s).decode())
+
+    def close(self):
+        if getattr(self, "_s", None) is not None and self._s.value:
+            lib().pe_server_destroy(self._s)
+            self._s = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, solve, tl_every: int = 0, steps: Optional[int] = None) -> int:
+        """Queue an ``inputs.Solve``; returns the request id."""
+        u0 = _host_c64(solve.u0)
+        req = PERequest(N=solve.N, H=solve.H, k0=solve.k0, dr=solve.dr, pade_order=solve.pade_order,
+                        neumann_terms=solve.neumann_terms, neumann_tol=solve.neumann_tol,
+                        steps=int(steps if steps is not None else solve.steps), tl_every=int(tl_every),
+                        u0=u0.ctypes.data, r0=solve.r0)
+        if solve.neumann_terms > 1:
+            n2 = np.ascontiguousarray(np.stack([np.asarray(v, dtype=np.float64) for _, v in solve.profiles]))
+            nr = np.ascontiguousarray(np.array([r for r, _ in solve.profiles], dtype=np.float64))
+            req.n2, req.node_r, req.nodes = n2.ctypes.data, nr.ctypes.data, nr.size
+        rid = ctypes.c_ulonglong(0)
+        self._c(lib().pe_server_submit(self._s, ctypes.byref(req), ctypes.byref(rid)))
+        self._keep[rid.value] = solve.N
+        return rid.value
+
+    def step(self):
+        live, queued, done = _i(0), _i(0), _i(0)
+        self._c(lib().pe_server_step(self._s, ctypes.byref(live), ctypes.byref(queued), ctypes.byref(done)))
+        return live.value, queued.value, done.value
+
+    def state(self, rid: int) -> int:
+        st = _i(0)
+        self._c(lib().pe_server_state(self._s, ctypes.c_ulonglong(rid), ctypes.byref(st)))
+        return st.value
+
+    def take(self, rid: int):
+        N = self._keep[rid]
+        rows = _sz(0)
+        self._c(lib().pe_server_take(self._s, ctypes.c_ulonglong(rid), None, None, 0, ctypes.byref(rows)))
+        field = np.empty(N, dtype=np.complex64)
+        tl = np.empty((rows.value, N), dtype=np.float32)
+        self._c(lib().pe_server_take(self._s, ctypes.c_ulonglong(rid), field.ctypes.data,
+                                     tl.ctypes.data if tl.size else None, tl.size, ctypes.byref(rows)))
+        del self._keep[rid]
+        return field, tl
+
+    def stats(self):
+        a, b, c = _sz(0), _sz(0), _i(0)
+        self._c(lib().pe_server_stats(self._s, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"bytes_in_use": a.value, "peak_bytes": b.value, "peak_live": c.value}
+
+
+def march_batch_steps(plans: List[Plan], steps: Sequence[int]):
+    arr = (_vp * len(plans))(*[p.handle for p in plans])
+    st_arr = np.ascontiguousarray(np.asarray(steps, dtype=np.int32))
+    st = lib().pe_march_batch_steps(arr, st_arr.ctypes.data, len(plans))
+    if st != PE_OK:
+        raise PEError(st, lib().pe_last_error(plans[0].handle).decode())
 
 
 def march_batch(plans: List[Plan], steps: int):

@@ -110,3 +110,33 @@ def test_product_path_has_no_oracle_import():
 def test_oracle_has_no_product_import():
     txt = open(os.path.join(ROOT, "oracle", "sssp_oracle.py")).read()
     assert "paper_2511_03343_gb300" not in txt
+
+
+def test_plan_bytes_estimate_grows(L):
+    from paper_2511_03343_gb300 import sssp
+    a = sssp.plan_bytes_estimate(1023, 6, 1, 0)
+    assert sssp.plan_bytes_estimate(4095, 6, 1, 0) > a
+    assert sssp.plan_bytes_estimate(1023, 8, 1, 0) > a
+    assert sssp.plan_bytes_estimate(1023, 6, 10, 0) > a
+    assert sssp.plan_bytes_estimate(1023, 6, 1, 100) - a == 100 * 1023 * 4
+    # grids beyond one CTA's shared memory carry the 7 L complex workspace
+    big = sssp.plan_bytes_estimate(8191, 6, 1, 0)
+    assert big - sssp.plan_bytes_estimate(4095, 6, 1, 0) > 7 * 8192 * 8
+
+
+def test_server_submit_host_checks(L):
+    """Request validation and the budget check happen on the host at submit (no GPU work)."""
+    from paper_2511_03343_gb300 import inputs, sssp
+    srv = sssp.Server(hbm_budget_bytes=10_000_000, max_live=4, chunk_steps=10)
+    s = inputs.munk(N=255, steps=5)
+    rid = srv.submit(s, tl_every=1)
+    assert srv.state(rid) == 0                     # queued until a step admits it
+    big = inputs.munk(N=65535, steps=5)
+    with pytest.raises(sssp.PEError) as e:         # can never fit in a 10 MB budget
+        srv.submit(big)
+    assert e.value.status == sssp.PE_ERR_OOM
+    bad = inputs.munk(N=255, steps=5)
+    bad.profiles = []
+    with pytest.raises(sssp.PEError):
+        srv.submit(bad)
+    srv.close()

@@ -337,3 +337,49 @@ def test_batch_workload_sampled_solves(sssp):
         _compare(u, tl, ref)
     for pl in plans:
         pl.close()
+
+
+# ----------------------------------------------------------------------------- serving loop
+def _mixed_trace(seed=7, count=14):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        env = ["isovelocity", "munk", "munk_eddy"][i % 3]
+        N = [255, 1023, 4095, 8191][int(rng.integers(0, 4))]
+        H = 100.0 if env == "isovelocity" else 5000.0
+        out.append(dict(id=i, t_arrival=0.002 * i, N=N, env=env, H=H, freq=float(rng.uniform(25, 60 if H > 1000 else 300)),
+                        range_m=float(rng.uniform(300, 1500)), dr=25.0, pade_order=int(rng.integers(4, 9)),
+                        zs=0.4 * H, eddy_dc=-20.0, eddy_r0=500.0))
+    return out
+
+
+def test_server_alone_vs_mix_bitwise(sssp):
+    """Continuous batching: requests arriving while others run are admitted and share launches;
+    every result is bit-identical to marching that request alone."""
+    from paper_2511_03343_gb300 import serving
+    trace = _mixed_trace()
+    res = serving.replay(trace, hbm_budget=64e6, chunk_steps=7, tl_every=5, keep_results=True)
+    assert len(res["results"]) == len(trace)
+    assert res["peak_live"] > 1
+    for i, (field, tl, s) in res["results"].items():
+        pl = sssp.plan_for(s, tl_every=5)
+        pl.march(s.steps)
+        assert np.array_equal(pl.read_field(), field), i
+        assert np.array_equal(pl.read_tl()[0], tl), i
+        pl.close()
+
+
+def test_server_budget_and_parity(sssp):
+    """A budget that fits only a few plans at a time: the peak stays within it, everything
+    completes, and a served result matches the oracle."""
+    from paper_2511_03343_gb300 import serving
+    trace = _mixed_trace(seed=8, count=9)
+    one = max(sssp.plan_bytes_estimate(t["N"], t["pade_order"], 1, 100) for t in trace)
+    budget = 3 * one
+    res = serving.replay(trace, hbm_budget=budget, chunk_steps=11, tl_every=0, keep_results=True)
+    assert res["peak_bytes"] <= budget
+    assert len(res["results"]) == len(trace)
+    i = next(i for i, t in enumerate(trace) if t["env"] == "munk" and t["N"] <= 1023)
+    field, _, s = res["results"][i]
+    ref = _oracle(s, tl_every=0)
+    assert np.linalg.norm(field - ref.u) / np.linalg.norm(ref.u) <= FIELD_TOL
