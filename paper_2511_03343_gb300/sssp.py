@@ -311,7 +311,7 @@ class Server:
                         neumann_terms=solve.neumann_terms, neumann_tol=solve.neumann_tol,
                         steps=int(steps if steps is not None else solve.steps), tl_every=int(tl_every),
                         u0=u0.ctypes.data, r0=solve.r0)
-        if solve.neumann_terms > 1:
+        if solve.neumann_terms > 1 and len(solve.profiles) > 0:
             n2 = np.ascontiguousarray(np.stack([np.asarray(v, dtype=np.float64) for _, v in solve.profiles]))
             nr = np.ascontiguousarray(np.array([r for r, _ in solve.profiles], dtype=np.float64))
             req.n2, req.node_r, req.nodes = n2.ctypes.data, nr.ctypes.data, nr.size
