@@ -239,6 +239,63 @@ def bench_other(args):
         pl.close()
 
 
+def bench_serve(args):
+    """Serving mix: Poisson arrivals (200 req/s, default_rng(5)) of solves with N in
+    {255, 1023, 4095, 16383, 65535}, f in [25, 1000] Hz, environment in {isovelocity, Munk,
+    Munk + eddy}, Pade order 4..8, under a 120 GB budget, continuous batching (pe_server_*).
+    Ranges are scaled by --range-scale (10-200 km x scale).  Compared with the one-at-a-time
+    plain marcher: the same requests marched alone, FIFO in arrival order."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2511_03343_gb300 import build as B
+    B.build()
+    from paper_2511_03343_gb300 import inputs, serving, sssp
+    trace = inputs.serving_trace(count=args.serve_requests)
+    stream = torch.cuda.current_stream()
+    # warm the kernels of every size
+    for N in (255, 1023, 4095, 16383, 65535):
+        pl = sssp.Plan(N, 100.0, 0.4, 5.0, 4, stream=stream)
+        pl.set_field(np.ones(N, dtype=np.complex64))
+        pl.march(1)
+        pl.read_field()
+        pl.close()
+    clocks = ClockSampler(0)
+    clocks.start()
+    res = serving.replay(trace, hbm_budget=120e9, chunk_steps=args.chunk_steps, tl_every=10,
+                         range_scale=args.range_scale, stream=stream)
+    clk = clocks.stop()
+    line = {"metric": METRIC, "value": res["throughput"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": 1e3 * res["wall_s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "serving_mix", "requests": len(trace), "rate_per_s": 200,
+                       "range_scale": args.range_scale, "budget_bytes": 120e9, "chunk_steps": args.chunk_steps},
+            "served": {k: v for k, v in res.items() if k != "results"}, "clocks": clk}
+    if args.serve_baseline:
+        # one-at-a-time: every request marched alone (its service time), FIFO queue in arrival order
+        svc = []
+        units = 0
+        for t in trace:
+            s = serving.build_solve(t, args.range_scale)
+            pl = sssp.plan_for(s, stream=stream, tl_every=10)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pl.march(s.steps)
+            pl.read_field()
+            pl.read_tl()
+            svc.append(time.perf_counter() - t0)
+            units += s.N * s.steps
+            pl.close()
+        free_at, lat = 0.0, []
+        for t, sv in sorted(zip(trace, svc), key=lambda x: x[0]["t_arrival"]):
+            start = max(free_at, t["t_arrival"])
+            free_at = start + sv
+            lat.append(free_at - t["t_arrival"])
+        line["one_at_a_time"] = {"throughput": units / sum(svc), "busy_s": sum(svc),
+                                 "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99))}
+    print(json.dumps(line), flush=True)
+
+
 def bench_ours(args):
     import numpy as np
     import torch
@@ -372,11 +429,17 @@ def main():
     ap.add_argument("--range-steps", type=int, default=2000,
                     help="range steps per march (2000 = the workload; fewer only for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="munk", choices=["munk", "batch", "eddy", "iso"])
+    ap.add_argument("--workload", default="munk", choices=["munk", "batch", "eddy", "iso", "serve"])
+    ap.add_argument("--serve-requests", type=int, default=100)
+    ap.add_argument("--range-scale", type=float, default=0.05)
+    ap.add_argument("--chunk-steps", type=int, default=50)
+    ap.add_argument("--serve-baseline", action="store_true")
     ap.add_argument("--batch-count", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
+    elif args.workload == "serve":
+        bench_serve(args)
     elif args.workload != "munk":
         bench_other(args)
     else:
