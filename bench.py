@@ -275,6 +275,8 @@ def bench_serve(args):
         # one-at-a-time: every request marched alone (its service time), FIFO queue in arrival order
         svc = []
         units = 0
+        skip = set(res["failed_ids"])
+        trace = [t for i, t in enumerate(trace) if i not in skip]  # the same completed requests
         for t in trace:
             s = serving.build_solve(t, args.range_scale)
             pl = sssp.plan_for(s, stream=stream, tl_every=10)

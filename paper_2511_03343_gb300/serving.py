@@ -51,6 +51,7 @@ def replay(trace: List[Dict], hbm_budget: float, chunk_steps: int = 50, tl_every
     lat = {}
     units = 0
     results = {}
+    failed = {}
     t0 = time.perf_counter()
     nsteps = 0
     while pending or running:
@@ -67,7 +68,15 @@ def replay(trace: List[Dict], hbm_budget: float, chunk_steps: int = 50, tl_every
         nsteps += 1
         tnow = time.perf_counter()
         for rid in list(running):
-            if srv.state(rid) >= 2:
+            state = srv.state(rid)
+            if state == 3:  # the march failed on the device (e.g. a diverging Neumann series)
+                i, ta, u, s = running.pop(rid)
+                try:
+                    srv.take(rid)
+                except sssp.PEError as e:
+                    failed[i] = str(e)
+                continue
+            if state == 2:
                 i, ta, u, s = running.pop(rid)
                 lat[i] = tnow - ta
                 units += u
@@ -78,7 +87,8 @@ def replay(trace: List[Dict], hbm_budget: float, chunk_steps: int = 50, tl_every
     st = srv.stats()
     srv.close()
     L = np.array([lat[i] for i in sorted(lat)])
-    out = {"requests": len(trace), "wall_s": wall, "server_steps": nsteps,
+    out = {"requests": len(trace), "completed": len(lat), "failed": len(failed),
+           "failed_ids": sorted(failed), "wall_s": wall, "server_steps": nsteps,
            "throughput": units / wall, "p50_s": float(np.percentile(L, 50)), "p99_s": float(np.percentile(L, 99)),
            "mean_s": float(L.mean()), "peak_live": st["peak_live"], "peak_bytes": st["peak_bytes"]}
     if keep_results:
