@@ -298,6 +298,38 @@ def bench_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_gemm(args):
+    """The 256-solve Munk batch (N = 1023) with the DST-I as a dense tensor-core GEMM, per
+    precision: throughput of the lockstep march (one captured graph per range step)."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2511_03343_gb300 import build as B
+    B.build()
+    from paper_2511_03343_gb300 import inputs, sssp
+    stream = torch.cuda.current_stream()
+    steps = args.range_steps
+    solves = inputs.munk_batch(count=args.batch_count, steps=steps)
+    out = {}
+    for mode in ["fp32", "tf32", "3xtf32", "bf16x3"]:
+        plans = [sssp.plan_for(s, stream=stream) for s in solves]
+        gb = sssp.GemmBatch(plans, mode)
+        gb.march(2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gb.march(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[mode] = {"ms": ms, "throughput": sum(s.N for s in solves) * steps / (ms * 1e-3)}
+        gb.close()
+        for pl in plans:
+            pl.close()
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "config": {"workload": "batch_gemm_dst", "solves": len(solves),
+                      "N": 1023, "range_steps": steps}, "modes": out}), flush=True)
+
+
 def bench_ours(args):
     import numpy as np
     import torch
@@ -431,7 +463,7 @@ def main():
     ap.add_argument("--range-steps", type=int, default=2000,
                     help="range steps per march (2000 = the workload; fewer only for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="munk", choices=["munk", "batch", "eddy", "iso", "serve"])
+    ap.add_argument("--workload", default="munk", choices=["munk", "batch", "eddy", "iso", "serve", "gemm"])
     ap.add_argument("--serve-requests", type=int, default=100)
     ap.add_argument("--range-scale", type=float, default=0.05)
     ap.add_argument("--chunk-steps", type=int, default=50)
@@ -442,6 +474,8 @@ def main():
         bench_reference(args)
     elif args.workload == "serve":
         bench_serve(args)
+    elif args.workload == "gemm":
+        bench_gemm(args)
     elif args.workload != "munk":
         bench_other(args)
     else:

@@ -215,6 +215,25 @@ pe_status pe_get_range(const pe_plan* plan, double* r, long long* steps);
 pe_status pe_pade_coefficients(double sigma, int p, double* b, double* a, double* d);
 
 /* ------------------------------------------------------------------------------------
+ * Tensor-core GEMM-DST (a precision variant for batches of one small grid size).  Every
+ * transform of the march (Section 3's DST-I, applied to all fields of the batch at once) is
+ * the dense product S X with S[m][n] = sin(pi n m/(N+1)), computed by a library GEMM in the
+ * given precision with FP32 accumulation; the rest of the step is the FFT marcher's arithmetic.
+ * All plans must share N, Pade order, neumann_terms (>= 2; a fixed count of terms is taken)
+ * and dr, have a field set and exactly one profile node.  The batch copies the plans' spectral
+ * states at creation and marches its own copy (the plans are not advanced).
+ * ------------------------------------------------------------------------------------ */
+enum { PE_GEMM_FP32 = 0, PE_GEMM_TF32 = 1, PE_GEMM_3XTF32 = 2, PE_GEMM_BF16X3 = 3 };
+typedef struct pe_gemm_batch pe_gemm_batch;
+pe_status pe_gemm_batch_create(pe_gemm_batch** out, pe_plan** plans, int count, int mode);
+/* Enqueue `steps` range steps (one captured CUDA graph per step) on plans[0]'s stream. */
+pe_status pe_gemm_batch_march(pe_gemm_batch* batch, int steps);
+/* Field of member `index` (N interleaved complex64, host; carrier included).  Synchronises. */
+pe_status pe_gemm_batch_read_field(pe_gemm_batch* batch, int index, float* out);
+const char* pe_gemm_batch_error(const pe_gemm_batch* batch);
+void pe_gemm_batch_destroy(pe_gemm_batch* batch);
+
+/* ------------------------------------------------------------------------------------
  * Serving loop (continuous batching).  The paper marches one solve at a time; this is the
  * deployment form: many independent marches share the GPU.  Requests queue in arrival order;
  * each pe_server_step admits queued requests while a slot is free and their device bytes

@@ -20,7 +20,7 @@ LIB = os.path.join(BUILD, "libsssp.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["sssp_abi.cu", "sssp_noalloc.cu"]
+CUDA_SOURCES = ["sssp_abi.cu", "sssp_noalloc.cu", "sssp_gemm.cu"]
 CXX_SOURCES = ["pade_host.cpp", "sssp_server.cpp"]
 
 
@@ -77,7 +77,9 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         logs = list(ex.map(_run, jobs))
     tmp = LIB + ".tmp"
-    logs.append(_run([nvcc, *ARCH, "-shared", "-o", tmp, *objs]))
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
+    logs.append(_run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcublas",
+                      "-Xlinker", "-rpath", "-Xlinker", cuda_lib]))
     os.replace(tmp, LIB)
     if verbose:
         sys.stdout.write("".join(logs))

@@ -16,6 +16,7 @@
 #include "march_kernel.cuh"
 #include "march_large.cuh"
 #include "pade_host.h"
+#include "plan_internal.h"
 
 using sssp::Cfg;
 using sssp::SolveDesc;
@@ -29,11 +30,6 @@ constexpr int kMaxLog2 = 16;       // beyond: global-memory workspace (march_lar
 constexpr int kMaxTerms = 64;
 
 thread_local std::string g_create_error;
-
-struct TransformTables {
-  float2* tw = nullptr;  // per-pass Stockham twiddles (L - 8 used entries)
-  float* sinw = nullptr; // L weights sin(pi n/L)
-};
 
 std::mutex g_tab_mu;
 std::map<std::pair<int, int>, TransformTables> g_tabs;  // (device, log2L)
@@ -85,37 +81,6 @@ int ilog2_exact(int v) {
 
 }  // namespace
 
-struct pe_plan {
-  int N = 0, L = 0, log2L = 0, p = 0, terms = 0, device = 0;
-  double H = 0, k0 = 0, dr = 0, tol = 0;
-  cudaStream_t stream = nullptr;
-  sssp::PadeData pade;
-  TransformTables tabs;
-  float4* dR = nullptr;
-  float2* dA = nullptr;
-  float2* dB = nullptr;
-  float4* dG = nullptr;
-  float2 beta[sssp::kMaxStages];
-  float2* dYhat = nullptr;
-  float2* dField = nullptr;
-  float2* dStage = nullptr;  // N-value staging buffer (set / read field)
-  float2* dWork = nullptr;   // 4 L workspace for grids beyond one CTA's shared memory
-  float* dV = nullptr;
-  double* dNodeR = nullptr;
-  int nodes = 0, node_cap = 0;
-  std::vector<double> node_r;
-  int* dStatus = nullptr;
-  unsigned long long* dNdst = nullptr;
-  float* dTL = nullptr;
-  long long tl_cap_rows = 0, tl_rows = 0;
-  std::vector<double> tl_ranges;
-  int tl_every = 0;
-  SolveDesc* dDesc = nullptr;
-  double r_set = 0.0;
-  long long steps_done = 0;
-  bool field_set = false;
-  std::string err;
-};
 
 namespace {
 

@@ -62,6 +62,11 @@ _SIGNATURES = {
     "pe_get_range": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
     "pe_pade_coefficients": (_i, [_d, _i, _vp, _vp, _vp]),
     "pe_march_batch_steps": (_i, [ctypes.POINTER(_vp), _vp, _i]),
+    "pe_gemm_batch_create": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i]),
+    "pe_gemm_batch_march": (_i, [_vp, _i]),
+    "pe_gemm_batch_read_field": (_i, [_vp, _i, _vp]),
+    "pe_gemm_batch_error": (ctypes.c_char_p, [_vp]),
+    "pe_gemm_batch_destroy": (None, [_vp]),
     "pe_plan_bytes_estimate": (_sz, [_i, _i, _i, ctypes.c_longlong]),
     "pe_server_create": (_i, [ctypes.POINTER(_vp), _sz, _i, _i, _vp]),
     "pe_server_destroy": (None, [_vp]),
@@ -345,6 +350,45 @@ class Server:
         a, b, c = _sz(0), _sz(0), _i(0)
         self._c(lib().pe_server_stats(self._s, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return {"bytes_in_use": a.value, "peak_bytes": b.value, "peak_live": c.value}
+
+
+GEMM_MODES = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3}
+
+
+class GemmBatch:
+    """Lockstep batched march with the DST-I as a dense GEMM (pe_gemm_batch_*)."""
+
+    def __init__(self, plans: List[Plan], mode: str = "3xtf32"):
+        arr = (_vp * len(plans))(*[p.handle for p in plans])
+        ptr = _vp()
+        st = lib().pe_gemm_batch_create(ctypes.byref(ptr), arr, len(plans), GEMM_MODES[mode])
+        if st != PE_OK:
+            raise PEError(st, lib().pe_last_error(plans[0].handle).decode())
+        self._g = ptr
+        self.N = plans[0].N
+
+    def march(self, steps: int):
+        st = lib().pe_gemm_batch_march(self._g, int(steps))
+        if st != PE_OK:
+            raise PEError(st, lib().pe_gemm_batch_error(self._g).decode())
+
+    def read_field(self, index: int) -> np.ndarray:
+        out = np.empty(self.N, dtype=np.complex64)
+        st = lib().pe_gemm_batch_read_field(self._g, int(index), out.ctypes.data)
+        if st != PE_OK:
+            raise PEError(st, lib().pe_gemm_batch_error(self._g).decode())
+        return out
+
+    def close(self):
+        if getattr(self, "_g", None) is not None and self._g.value:
+            lib().pe_gemm_batch_destroy(self._g)
+            self._g = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def march_batch_steps(plans: List[Plan], steps: Sequence[int]):

@@ -383,3 +383,31 @@ def test_server_budget_and_parity(sssp):
     field, _, s = res["results"][i]
     ref = _oracle(s, tl_every=0)
     assert np.linalg.norm(field - ref.u) / np.linalg.norm(ref.u) <= FIELD_TOL
+
+
+# ----------------------------------------------------------------------------- tensor-core GEMM-DST
+def test_gemm_dst_precisions(sssp):
+    """The batched march with the DST-I as a dense GEMM, per precision, against the FP64 oracle
+    (6 Munk solves, N = 1023, 60-200 Hz, dr = 25 m, [6/6], 12 terms, 40 steps).  FP32 and the
+    3xTF32 split meet the field tolerance; plain TF32 (10-bit mantissa) cannot; BF16x3 lies
+    between.  The errors are printed for the record."""
+    freqs = [60.0, 80.0, 100.0, 130.0, 160.0, 200.0]
+    solves = [inputs.munk(N=1023, freq=f, dr=25.0, steps=40) for f in freqs]
+    refs = [_oracle(s, tl_every=0).u for s in solves]
+    errs = {}
+    for mode in ["fp32", "3xtf32", "bf16x3", "tf32"]:
+        plans = [sssp.plan_for(s) for s in solves]
+        gb = sssp.GemmBatch(plans, mode)
+        gb.march(40)
+        e = []
+        for i, ref in enumerate(refs):
+            u = gb.read_field(i)
+            e.append(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+        gb.close()
+        for pl in plans:
+            pl.close()
+        errs[mode] = max(e)
+    print("GEMM-DST max field rel-L2 after 40 steps:", errs)
+    assert errs["fp32"] <= FIELD_TOL and errs["3xtf32"] <= FIELD_TOL
+    assert errs["tf32"] > errs["3xtf32"]
+    assert errs["bf16x3"] >= errs["3xtf32"] * 0.5
