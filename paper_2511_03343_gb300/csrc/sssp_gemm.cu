@@ -170,7 +170,7 @@ __global__ void k_gather(const float2* const* yhats, float2* Y, int N, int B) {
 
 struct pe_gemm_batch {
   int N = 0, B = 0, p = 0, terms = 0, mode = 0;
-  double sigma = 0;
+  std::vector<double> sigma;  // k0 dr of every member (the carrier phase per step)
   long long steps_done = 0;
   cudaStream_t stream = nullptr;
   cublasHandle_t h = nullptr;
@@ -356,7 +356,7 @@ pe_status pe_gemm_batch_create(pe_gemm_batch** out, pe_plan** plans, int count, 
   cudaStreamSynchronize(g->stream);
   cudaFree(dyh);
   if (cudaGetLastError() != cudaSuccess) return bail("gather");
-  g->sigma = p0->k0 * p0->dr;
+  for (int i = 0; i < count; ++i) g->sigma.push_back(plans[i]->k0 * plans[i]->dr);
   // one range step as a CUDA graph (cuBLAS runs on the user workspace, so it can be captured)
   cudaStream_t cap = nullptr;
   if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return bail("stream");
@@ -395,7 +395,7 @@ pe_status pe_gemm_batch_read_field(pe_gemm_batch* g, int index, float* out) {
   cudaMemcpyAsync(im.data(), g->G + size_t(g->B + index) * g->N, sizeof(float) * g->N, cudaMemcpyDeviceToHost,
                   g->stream);
   if (cudaStreamSynchronize(g->stream) != cudaSuccess) return gfail(g, PE_ERR_CUDA, "sync");
-  const double ph = std::fmod(g->sigma * double(g->steps_done), 2.0 * M_PI);
+  const double ph = std::fmod(g->sigma[index] * double(g->steps_done), 2.0 * M_PI);
   const double c = std::cos(ph), s = std::sin(ph);
   for (int n = 0; n < g->N; ++n) {
     out[2 * n] = float(c * re[n] - s * im[n]);
