@@ -330,6 +330,59 @@ def bench_gemm(args):
                       "N": 1023, "range_steps": steps}, "modes": out}), flush=True)
 
 
+def bench_dst(args):
+    """Transform-level comparison: the library's batched DST-I kernels against a cuFFT DST-I
+    (odd extension to length 2(N+1), complex64 C2C through torch.fft; comparison baseline only).
+    Inputs larger than L2 where the batch allows; per-transform device time with CUDA events."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2511_03343_gb300 import build as B
+    B.build()
+    from paper_2511_03343_gb300 import sssp
+    stream = torch.cuda.current_stream()
+    rows = []
+    for N, count in [(1023, 256), (1023, 16384), (4095, 1), (4095, 4096), (16383, 512), (65535, 128)]:
+        L = N + 1
+        x = torch.randn(count, N, dtype=torch.complex64, device="cuda")
+        out = torch.empty_like(x)
+        pl = sssp.Plan(N, 100.0, 0.4, 5.0, 4, stream=stream)
+
+        def ours():
+            pl.dst1_batch(x, out)
+
+        ext = torch.zeros(count, 2 * L, dtype=torch.complex64, device="cuda")
+
+        def cufft():
+            ext[:, 1:L] = x
+            ext[:, L + 1:] = -torch.flip(x, dims=[1])
+            return 0.5j * torch.fft.fft(ext, dim=1)[:, 1:L]
+
+        res = {}
+        for name, fn in [("ours", ours), ("cufft", cufft)]:
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 5
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[name] = e0.elapsed_time(e1) / reps / count * 1e3  # us per transform
+        ref = cufft()
+        ours()
+        err = float((out - ref).abs().max() / ref.abs().max())
+        io = 16.0 * N  # read + write one complex64 vector
+        rows.append({"N": N, "batch": count, "us_per_dst_ours": res["ours"], "us_per_dst_cufft": res["cufft"],
+                     "speedup_vs_cufft": res["cufft"] / res["ours"],
+                     "io_GBps_ours": io / (res["ours"] * 1e-6) / 1e9, "max_rel_diff": err})
+        pl.close()
+        del x, out, ext
+    print(json.dumps({"metric": "DST-I time per transform", "unit": "us", "rows": rows}), flush=True)
+
+
 def bench_ours(args):
     import numpy as np
     import torch
@@ -463,7 +516,7 @@ def main():
     ap.add_argument("--range-steps", type=int, default=2000,
                     help="range steps per march (2000 = the workload; fewer only for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="munk", choices=["munk", "batch", "eddy", "iso", "serve", "gemm"])
+    ap.add_argument("--workload", default="munk", choices=["munk", "batch", "eddy", "iso", "serve", "gemm", "dst"])
     ap.add_argument("--serve-requests", type=int, default=100)
     ap.add_argument("--range-scale", type=float, default=0.05)
     ap.add_argument("--chunk-steps", type=int, default=50)
@@ -476,6 +529,8 @@ def main():
         bench_serve(args)
     elif args.workload == "gemm":
         bench_gemm(args)
+    elif args.workload == "dst":
+        bench_dst(args)
     elif args.workload != "munk":
         bench_other(args)
     else:

@@ -187,6 +187,13 @@ pe_status pe_get_transform_count(pe_plan* plan, unsigned long long* count);
 pe_status pe_dst1(pe_plan* plan, const float* in, float* out, int on_device);
 
 /*
+ * `count` DST-I of length N at once (one CTA per field), in and out device memory holding
+ * count x N interleaved complex64 values (row b = field b).  Asynchronous on the plan's
+ * stream.  Section 3.1's transform, batched.
+ */
+pe_status pe_dst1_batch(pe_plan* plan, const float* in, float* out, int count);
+
+/*
  * pe_dst1 for callers that cannot allocate device memory.  (The paper has no counterpart:
  * this is a deployment variant of the transform, not a step of the method.)
  *

@@ -483,15 +483,19 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
   }
 }
 
-// DST-I of one field: out = scale * DST(in), in holds N values (n = 1..N), out L values.
+// DST-I of one field per CTA: out = scale * DST(in); field b = blockIdx.x reads N values at
+// in + b * in_stride (n = 1..N) and writes L values at out + b * out_stride.
 template <int LOG2L>
 __global__ void __launch_bounds__(Cfg<LOG2L>::NT)
     sssp_dst_kernel(const float2* __restrict__ in, float2* __restrict__ out, float scale,
-                    const float2* __restrict__ tw_g, const float* __restrict__ sin_g) {
+                    const float2* __restrict__ tw_g, const float* __restrict__ sin_g, long long in_stride = 0,
+                    long long out_stride = 0) {
   using C = Cfg<LOG2L>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<LOG2L> sm(smem_raw);
   const int t = threadIdx.x;
+  in += blockIdx.x * in_stride;
+  out += blockIdx.x * out_stride;
   load_tables<LOG2L>(sm.tw, sm.sinw, tw_g, sin_g);
   for (int n = t; n < C::L; n += C::NT) sm.bufA[pidx(n)] = (n == 0) ? make_float2(0.f, 0.f) : in[n - 1];
   __syncthreads();

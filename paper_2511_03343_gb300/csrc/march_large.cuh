@@ -278,8 +278,12 @@ __global__ void __launch_bounds__(kLargeNT, 1)
 template <int LOG2L>
 __global__ void __launch_bounds__(kLargeNT, 1)
     sssp_dst_large_kernel(const float2* __restrict__ in, float2* __restrict__ out, float scale, float2* work,
-                          const float2* __restrict__ tw_g, const float* __restrict__ sin_g) {
+                          const float2* __restrict__ tw_g, const float* __restrict__ sin_g, long long in_stride = 0,
+                          long long out_stride = 0) {
   constexpr int L = 1 << LOG2L;
+  in += blockIdx.x * in_stride;
+  out += blockIdx.x * out_stride;
+  work += blockIdx.x * (long long)large_work_elems(L);
   float2* X = work;
   for (int n = threadIdx.x; n < L; n += kLargeNT) X[n] = (n == 0) ? make_float2(0.f, 0.f) : in[n - 1];
   __syncthreads();

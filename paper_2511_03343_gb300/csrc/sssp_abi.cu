@@ -125,10 +125,12 @@ cudaError_t launch_march_t(const SolveDesc* dDescs, int count, const TransformTa
 }
 
 template <int LOG2L>
-cudaError_t launch_dst_t(const float2* in, float2* out, float scale, const TransformTables& tabs, cudaStream_t st) {
+cudaError_t launch_dst_t(const float2* in, float2* out, float scale, const TransformTables& tabs, cudaStream_t st,
+                         int count = 1, long long in_stride = 0, long long out_stride = 0) {
   cudaError_t e = set_smem_attr<LOG2L>();
   if (e != cudaSuccess) return e;
-  sssp::sssp_dst_kernel<LOG2L><<<1, Cfg<LOG2L>::NT, Cfg<LOG2L>::SMEM, st>>>(in, out, scale, tabs.tw, tabs.sinw);
+  sssp::sssp_dst_kernel<LOG2L><<<count, Cfg<LOG2L>::NT, Cfg<LOG2L>::SMEM, st>>>(in, out, scale, tabs.tw, tabs.sinw,
+                                                                                in_stride, out_stride);
   return cudaGetLastError();
 }
 
@@ -140,8 +142,9 @@ cudaError_t launch_march_large_t(const SolveDesc* dDescs, int count, const Trans
 
 template <int LOG2L>
 cudaError_t launch_dst_large_t(const float2* in, float2* out, float scale, float2* work, const TransformTables& tabs,
-                               cudaStream_t st) {
-  sssp::sssp_dst_large_kernel<LOG2L><<<1, sssp::kLargeNT, 0, st>>>(in, out, scale, work, tabs.tw, tabs.sinw);
+                               cudaStream_t st, int count = 1, long long in_stride = 0, long long out_stride = 0) {
+  sssp::sssp_dst_large_kernel<LOG2L><<<count, sssp::kLargeNT, 0, st>>>(in, out, scale, work, tabs.tw, tabs.sinw,
+                                                                        in_stride, out_stride);
   return cudaGetLastError();
 }
 
@@ -182,6 +185,27 @@ cudaError_t launch_dst(int log2L, const float2* in, float2* out, float scale, co
     case 10: return launch_dst_t<10>(in, out, scale, tabs, st);
     case 11: return launch_dst_t<11>(in, out, scale, tabs, st);
     case 12: return launch_dst_t<12>(in, out, scale, tabs, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_dst_batch(int log2L, const float2* in, float2* out, const TransformTables& tabs, cudaStream_t st,
+                             float2* work, int count, long long in_stride, long long out_stride) {
+  switch (log2L) {
+    case 3: return launch_dst_t<3>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
+    case 4: return launch_dst_t<4>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
+    case 5: return launch_dst_t<5>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
+    case 6: return launch_dst_t<6>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
+    case 7: return launch_dst_t<7>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
+    case 8: return launch_dst_t<8>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
+    case 9: return launch_dst_t<9>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
+    case 10: return launch_dst_t<10>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
+    case 11: return launch_dst_t<11>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
+    case 12: return launch_dst_t<12>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
+    case 13: return launch_dst_large_t<13>(in, out, 1.f, work, tabs, st, count, in_stride, out_stride);
+    case 14: return launch_dst_large_t<14>(in, out, 1.f, work, tabs, st, count, in_stride, out_stride);
+    case 15: return launch_dst_large_t<15>(in, out, 1.f, work, tabs, st, count, in_stride, out_stride);
+    case 16: return launch_dst_large_t<16>(in, out, 1.f, work, tabs, st, count, in_stride, out_stride);
   }
   return cudaErrorInvalidValue;
 }
@@ -671,6 +695,26 @@ pe_status pe_dst1(pe_plan* p, const float* in, float* out, int on_device) {
                              p->stream));
   PE_CUDA(p, cudaFreeAsync(res, p->stream));
   if (!on_device) PE_CUDA(p, cudaStreamSynchronize(p->stream));
+  return PE_OK;
+}
+
+pe_status pe_dst1_batch(pe_plan* p, const float* in, float* out, int count) {
+  if (!p) return PE_ERR_ARG;
+  if (!in || !out || count < 0) return fail(p, PE_ERR_ARG, "in/out NULL or count < 0");
+  if (count == 0) return PE_OK;
+  // every field gets an L-long result row (index 0 is the zero mode), then rows 1..N are packed
+  float2* res = nullptr;
+  float2* work = nullptr;
+  PE_CUDA(p, cudaMallocAsync(reinterpret_cast<void**>(&res), sizeof(float2) * size_t(p->L) * count, p->stream));
+  if (p->log2L > kMaxSmemLog2)
+    PE_CUDA(p, cudaMallocAsync(reinterpret_cast<void**>(&work),
+                               sizeof(float2) * sssp::large_work_elems(p->L) * size_t(count), p->stream));
+  PE_CUDA(p, launch_dst_batch(p->log2L, reinterpret_cast<const float2*>(in), res, p->tabs, p->stream, work, count,
+                              p->N, p->L));
+  PE_CUDA(p, cudaMemcpy2DAsync(out, sizeof(float2) * p->N, res + 1, sizeof(float2) * p->L, sizeof(float2) * p->N,
+                               count, cudaMemcpyDeviceToDevice, p->stream));
+  PE_CUDA(p, cudaFreeAsync(res, p->stream));
+  if (work) PE_CUDA(p, cudaFreeAsync(work, p->stream));
   return PE_OK;
 }
 

@@ -59,6 +59,7 @@ _SIGNATURES = {
     "pe_get_transform_count": (_i, [_vp, ctypes.POINTER(ctypes.c_ulonglong)]),
     "pe_dst1": (_i, [_vp, _vp, _vp, _i]),
     "pe_dst1_noalloc": (_i, [_vp, _vp, _i, _vp]),
+    "pe_dst1_batch": (_i, [_vp, _vp, _vp, _i]),
     "pe_get_range": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
     "pe_pade_coefficients": (_i, [_d, _i, _vp, _vp, _vp]),
     "pe_march_batch_steps": (_i, [ctypes.POINTER(_vp), _vp, _i]),
@@ -264,6 +265,12 @@ class Plan:
         s = ctypes.c_longlong(0)
         self._c(lib().pe_get_range(self._p, ctypes.byref(r), ctypes.byref(s)))
         return r.value, s.value
+
+    def dst1_batch(self, x, out):
+        """count DST-I on device tensors x, out of shape (count, N), complex64."""
+        assert x.is_cuda and out.is_cuda and x.shape == out.shape and x.shape[-1] == self.N
+        self._c(lib().pe_dst1_batch(self._p, x.data_ptr(), out.data_ptr(), int(x.shape[0])))
+        return out
 
     def dst1(self, x):
         """Unnormalised DST-I of N complex values on the GPU (host numpy in/out)."""

@@ -411,3 +411,19 @@ def test_gemm_dst_precisions(sssp):
     assert errs["fp32"] <= FIELD_TOL and errs["3xtf32"] <= FIELD_TOL
     assert errs["tf32"] > errs["3xtf32"]
     assert errs["bf16x3"] >= errs["3xtf32"] * 0.5
+
+
+@pytest.mark.parametrize("N,count", [(255, 7), (4095, 3), (16383, 2)])
+def test_dst1_batch_equals_single(sssp, N, count):
+    """The batched DST entry gives every field the same bits as the single-field one."""
+    import torch
+    rng = np.random.default_rng(N + count)
+    x = (rng.standard_normal((count, N)) + 1j * rng.standard_normal((count, N))).astype(np.complex64)
+    pl = sssp.Plan(N, 100.0, 0.4, 5.0, 4)
+    d_in = torch.from_numpy(x).cuda()
+    d_out = torch.empty_like(d_in)
+    pl.dst1_batch(d_in, d_out)
+    got = d_out.cpu().numpy()
+    for b in range(count):
+        assert np.array_equal(got[b], pl.dst1(x[b]))
+    pl.close()
