@@ -95,6 +95,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate_over_ranks(local_ms: float, local_units: float, device=None):
+    """Whole-job figures of a replica run: the slowest rank's time (max over ranks, after a
+    barrier) and the units all ranks processed.  Works with any torch.distributed backend
+    (NCCL on GPUs, gloo on CPU); without a process group it returns the local figures."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return local_ms, local_units
+    dist.barrier()
+    t = torch.tensor([local_ms, local_units], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0].item()), float(sm[1].item())
+
+
 def _dst_flops(N):
     L = N + 1
     return 5.0 * L * math.log2(L)
@@ -438,13 +455,7 @@ def bench_ours(args):
     clk = clocks.stop()
     nd1 = pl.transform_count()
     dst_per_launch = (nd1 - nd0) / args.steps
-    tot_ms = sum(step_ms)
-    # max over ranks
-    if world > 1:
-        t = torch.tensor([tot_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    units = s.N * s.steps * args.steps * world
+    tot_ms, units = aggregate_over_ranks(sum(step_ms), float(s.N * s.steps * args.steps), device="cuda")
     value = units / (tot_ms * 1e-3)
     # parity of the bench's own output
     tl, _ = pl.read_tl()
@@ -468,10 +479,7 @@ def bench_ours(args):
         if i >= args.warmup:
             e2e_ms.append(el * 1e3)
     e2e_tot = sum(e2e_ms) if e2e_ms else float("nan")
-    if world > 1:
-        t = torch.tensor([e2e_tot], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_tot = float(t.item())
+    e2e_tot, _ = aggregate_over_ranks(e2e_tot, 0.0, device="cuda")
 
     # roofline of the dominant kernel (the fused march kernel, FP32 ALU bound)
     kern_avg = sum(kern_ms) / len(kern_ms)
