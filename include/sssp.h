@@ -102,14 +102,14 @@ pe_status pe_set_field(pe_plan* plan, const float* u, int on_device, double r);
  * step [r, r + dr] uses V = n^2 - 1 of the last node whose range is <= r + dr/2, or the
  * first node if there is none (the step-midpoint reading of Section 4.2's range
  * dependence).  Node ranges must be non-decreasing.
- *   n2         N doubles (is_complex = 0).  is_complex = 1 (the complex absorbing
- *              potential of Section 3.1) is rejected with PE_ERR_ARG by this build.
+ *   n2         N doubles (is_complex = 0), or N interleaved (re, im) pairs (is_complex = 1:
+ *              the complex absorbing potential of Section 3.1; Im n^2 > 0 absorbs).
  *              n^2 is taken in FP64 because n^2 ~ 1: rounded to FP32 it would carry an
  *              absolute error ~6e-8, a fixed perturbation of the medium whose phase error
  *              grows with range; V = n^2 - 1 is formed in FP64 and only then rounded.
  *   on_device  0: host memory, 1: device memory
- * Errors: PE_ERR_ARG (NULL, decreasing range, mixing real and complex nodes),
- * PE_ERR_OOM, PE_ERR_CUDA.
+ * Real and complex nodes may be mixed (real nodes have Im n^2 = 0).
+ * Errors: PE_ERR_ARG (NULL, decreasing range, non-finite values), PE_ERR_OOM, PE_ERR_CUDA.
  */
 pe_status pe_set_profile(pe_plan* plan, const double* n2, int is_complex, double range, int on_device);
 

@@ -40,7 +40,8 @@ struct SolveDesc {
   const float2* A;       // p x L  (2/L) / (1 + b_j lam_m)
   const float2* B;       // p x L  (2/L) (-b_j) / (1 + b_j lam_m)
   const float4* G;       // L      hi/lo of prod_j R_j (isovelocity step)
-  const float* V;        // nodes x L, V = n^2 - 1
+  const float* V;        // nodes x L, V = n^2 - 1 (real part)
+  const float* Vi;       // nodes x L imaginary part of n^2 (absorbing layers), or null
   const double* node_r;  // node ranges, non-decreasing
   float2* yhat;          // L  spectral state (DST-I coefficients, unnormalised)
   float2* work;          // 4 L workspace (grids beyond one CTA's shared memory only)
@@ -72,9 +73,10 @@ struct Cfg {
   static constexpr int NW = (NT + 31) / 32;
   static constexpr unsigned MASK = NT >= 32 ? 0xffffffffu : ((1u << NT) - 1u);
   static constexpr int MIN_BLOCKS = NT >= 512 ? 1 : (512 / NT > 16 ? 16 : 512 / NT);
-  // dynamic shared memory: 2 padded buffers, twiddles, t_0 and B_j areas, sin weights, V row,
+  // dynamic shared memory: 2 padded buffers, twiddles, t_0 and B_j areas, sin weights, V row
+  // (real and imaginary parts),
   // scan + reduce
-  static constexpr size_t SMEM = sizeof(float2) * (2 * PADL + 3 * L) + sizeof(float) * (2 * L) +
+  static constexpr size_t SMEM = sizeof(float2) * (2 * PADL + 3 * L) + sizeof(float) * (3 * L) +
                                  sizeof(float2) * NW + sizeof(float) * 2 * NW;
 };
 
@@ -254,6 +256,7 @@ struct Smem {
   float2* Bs;    // per-thread B_j multipliers, same layout
   float* sinw;
   float* Vs;
+  float* Vis;
   float2* scan_s;
   float* red;
   __device__ __forceinline__ explicit Smem(unsigned char* base) {
@@ -265,7 +268,8 @@ struct Smem {
     Bs = t0s + C::L;
     sinw = reinterpret_cast<float*>(Bs + C::L);
     Vs = sinw + C::L;
-    scan_s = reinterpret_cast<float2*>(Vs + C::L);
+    Vis = Vs + C::L;
+    scan_s = reinterpret_cast<float2*>(Vis + C::L);
     red = reinterpret_cast<float*>(scan_s + C::NW);
   }
 };
@@ -339,9 +343,14 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
   int nrec = 0;
   int node = d.node0;
   double next_r = (node + 1 < d.nodes) ? d.node_r[node + 1] : 1e300;
+  const bool cplx = d.Vi != nullptr;
   if (!iso) {
     const float* Vg = d.V + (size_t)node * L;
     for (int i = t; i < L; i += C::NT) sm.Vs[i] = Vg[i];
+    if (cplx) {
+      const float* Vig = d.Vi + (size_t)node * L;
+      for (int i = t; i < L; i += C::NT) sm.Vis[i] = Vig[i];
+    }
   }
   __syncthreads();
 
@@ -371,6 +380,10 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
         next_r = (node + 1 < d.nodes) ? d.node_r[node + 1] : 1e300;
         const float* Vg = d.V + (size_t)node * L;
         for (int i = t; i < L; i += C::NT) sm.Vs[i] = Vg[i];
+        if (cplx) {
+          const float* Vig = d.Vi + (size_t)node * L;
+          for (int i = t; i < L; i += C::NT) sm.Vis[i] = Vig[i];
+        }
         // first read of Vs is after the syncs of the stage's first transform
       }
       for (int j = 0; j < d.p && status == kStatusOk; ++j) {
@@ -398,7 +411,9 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
         float first = 0.f;
         for (int m = 1; m < d.terms; ++m) {
 #pragma unroll
-          for (int i = 0; i < 8; ++i) sm.bufA[pidx(8 * t + i)] = sm.Vs[8 * t + i] * tp[i];
+          for (int i = 0; i < 8; ++i)
+            sm.bufA[pidx(8 * t + i)] = cplx ? cmul(make_float2(sm.Vs[8 * t + i], sm.Vis[8 * t + i]), tp[i])
+                                            : sm.Vs[8 * t + i] * tp[i];
           __syncthreads();
           dst_block<LOG2L>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // DST(V t_{m-1})
           ++ndst;

@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(kLargeNT, 1)
   int node = d.node0;
   double next_r = (node + 1 < d.nodes) ? d.node_r[node + 1] : 1e300;
   const float* V = iso ? nullptr : d.V + (size_t)node * L;
+  const float* Vi = (iso || d.Vi == nullptr) ? nullptr : d.Vi + (size_t)node * L;
 
   for (int s = 0; s < d.steps && status == kStatusOk; ++s) {
     if (iso) {
@@ -175,6 +176,7 @@ __global__ void __launch_bounds__(kLargeNT, 1)
         while (node + 1 < d.nodes && d.node_r[node + 1] <= rmid) ++node;
         next_r = (node + 1 < d.nodes) ? d.node_r[node + 1] : 1e300;
         V = d.V + (size_t)node * L;
+        if (d.Vi != nullptr) Vi = d.Vi + (size_t)node * L;
       }
       for (int j = 0; j < d.p && status == kStatusOk; ++j) {
         const float2* Aj = d.A + (size_t)j * L;
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(kLargeNT, 1)
         for (int m = 1; m < d.terms; ++m) {
           for (int q = 0; q < C::PER; ++q) {
             const int i = t + q * kLargeNT;
-            X[i] = __ldg(V + i) * X[i];
+            X[i] = Vi ? cmul(make_float2(__ldg(V + i), __ldg(Vi + i)), X[i]) : __ldg(V + i) * X[i];
           }
           __syncthreads();
           dst_global<LOG2L>(X, W1, W2, tw_g, sin_g);  // DST(V t_{m-1})

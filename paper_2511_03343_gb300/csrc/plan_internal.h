@@ -30,6 +30,8 @@ struct pe_plan {
   float2* dStage = nullptr;  // N-value staging buffer (set / read field)
   float2* dWork = nullptr;   // 4 L workspace for grids beyond one CTA's shared memory
   float* dV = nullptr;
+  float* dVi = nullptr;      // imaginary parts of n^2, allocated with the first complex node
+  bool complex_profile = false;
   double* dNodeR = nullptr;
   int nodes = 0, node_cap = 0;
   std::vector<double> node_r;

@@ -241,10 +241,19 @@ pe_status ensure_node_cap(pe_plan* p, int need) {
     PE_CUDA(p, cudaMemcpyAsync(nV, p->dV, sizeof(float) * size_t(p->nodes) * p->L, cudaMemcpyDeviceToDevice, p->stream));
     PE_CUDA(p, cudaMemcpyAsync(nR, p->dNodeR, sizeof(double) * p->nodes, cudaMemcpyDeviceToDevice, p->stream));
   }
+  float* nVi = nullptr;
+  if (p->complex_profile) {
+    PE_CUDA(p, cudaMalloc(&nVi, sizeof(float) * size_t(cap) * p->L));
+    if (p->nodes > 0)
+      PE_CUDA(p, cudaMemcpyAsync(nVi, p->dVi, sizeof(float) * size_t(p->nodes) * p->L, cudaMemcpyDeviceToDevice,
+                                 p->stream));
+  }
   PE_CUDA(p, cudaStreamSynchronize(p->stream));
   cudaFree(p->dV);
+  cudaFree(p->dVi);
   cudaFree(p->dNodeR);
   p->dV = nV;
+  p->dVi = nVi;
   p->dNodeR = nR;
   p->node_cap = cap;
   return PE_OK;
@@ -292,6 +301,7 @@ pe_status prepare_desc(pe_plan* p, int steps, SolveDesc* d) {
   d->B = p->dB;
   d->G = p->dG;
   d->V = p->dV;
+  d->Vi = p->complex_profile ? p->dVi : nullptr;
   d->node_r = p->dNodeR;
   d->yhat = p->dYhat;
   d->work = p->dWork;
@@ -373,6 +383,7 @@ void pe_plan_destroy(pe_plan* p) {
   cudaFree(p->dStage);
   cudaFree(p->dWork);
   cudaFree(p->dV);
+  cudaFree(p->dVi);
   cudaFree(p->dNodeR);
   cudaFree(p->dStatus);
   cudaFree(p->dNdst);
@@ -523,34 +534,49 @@ pe_status pe_set_field(pe_plan* p, const float* u, int on_device, double r) {
   return PE_OK;
 }
 
-static pe_status append_nodes(pe_plan* p, const double* n2, const double* ranges, int count, int on_device) {
+static pe_status append_nodes(pe_plan* p, const double* n2, const double* ranges, int count, int on_device,
+                              int is_complex = 0) {
   for (int i = 0; i < count; ++i) {
     const double prev = (p->nodes + i > 0) ? (i > 0 ? ranges[i - 1] : p->node_r.back()) : -1e300;
     if (!std::isfinite(ranges[i]) || ranges[i] < prev) return fail(p, PE_ERR_ARG, "profile ranges must be finite and non-decreasing");
   }
+  if (is_complex && !p->complex_profile) {
+    // first complex node: imaginary rows for every node (zeros for the real ones so far)
+    if (p->node_cap > 0) {
+      PE_CUDA(p, cudaMalloc(&p->dVi, sizeof(float) * size_t(p->node_cap) * p->L));
+      PE_CUDA(p, cudaMemsetAsync(p->dVi, 0, sizeof(float) * size_t(p->node_cap) * p->L, p->stream));
+    }
+    p->complex_profile = true;
+  }
   pe_status st = ensure_node_cap(p, p->nodes + count);
   if (st != PE_OK) return st;
-  // V = n^2 - 1 with V[0] = 0 (boundary); converted on the host in FP64
-  std::vector<float> host;
+  const size_t per = size_t(p->N) * (is_complex ? 2 : 1);
   std::vector<double> src;
   const double* s = n2;
   if (on_device) {
-    src.resize(size_t(count) * p->N);
+    src.resize(size_t(count) * per);
     PE_CUDA(p, cudaMemcpyAsync(src.data(), n2, sizeof(double) * src.size(), cudaMemcpyDeviceToHost, p->stream));
     PE_CUDA(p, cudaStreamSynchronize(p->stream));
     s = src.data();
   }
-  host.resize(size_t(count) * p->L);
+  // V = n^2 - 1 formed in FP64, then rounded; index 0 is the boundary (0)
+  std::vector<float> host(size_t(count) * p->L), hosti;
+  if (p->complex_profile) hosti.assign(size_t(count) * p->L, 0.f);
   for (int i = 0; i < count; ++i) {
     host[size_t(i) * p->L] = 0.0f;
     for (int n = 0; n < p->N; ++n) {
-      const double v = s[size_t(i) * p->N + n];
-      if (!std::isfinite(v)) return fail(p, PE_ERR_ARG, "n2 must be finite");
-      host[size_t(i) * p->L + n + 1] = float(v - 1.0);
+      const double re = is_complex ? s[size_t(i) * per + 2 * n] : s[size_t(i) * per + n];
+      const double im = is_complex ? s[size_t(i) * per + 2 * n + 1] : 0.0;
+      if (!std::isfinite(re) || !std::isfinite(im)) return fail(p, PE_ERR_ARG, "n2 must be finite");
+      host[size_t(i) * p->L + n + 1] = float(re - 1.0);
+      if (p->complex_profile) hosti[size_t(i) * p->L + n + 1] = float(im);
     }
   }
   PE_CUDA(p, cudaMemcpyAsync(p->dV + size_t(p->nodes) * p->L, host.data(), sizeof(float) * host.size(),
                              cudaMemcpyHostToDevice, p->stream));
+  if (p->complex_profile)
+    PE_CUDA(p, cudaMemcpyAsync(p->dVi + size_t(p->nodes) * p->L, hosti.data(), sizeof(float) * hosti.size(),
+                               cudaMemcpyHostToDevice, p->stream));
   PE_CUDA(p, cudaMemcpyAsync(p->dNodeR + p->nodes, ranges, sizeof(double) * count, cudaMemcpyHostToDevice, p->stream));
   PE_CUDA(p, cudaStreamSynchronize(p->stream));
   for (int i = 0; i < count; ++i) p->node_r.push_back(ranges[i]);
@@ -561,8 +587,7 @@ static pe_status append_nodes(pe_plan* p, const double* n2, const double* ranges
 pe_status pe_set_profile(pe_plan* p, const double* n2, int is_complex, double range, int on_device) {
   if (!p) return PE_ERR_ARG;
   if (!n2) return fail(p, PE_ERR_ARG, "n2 is NULL");
-  if (is_complex) return fail(p, PE_ERR_ARG, "complex n2 is not supported by this build");
-  return append_nodes(p, n2, &range, 1, on_device);
+  return append_nodes(p, n2, &range, 1, on_device, is_complex ? 1 : 0);
 }
 
 pe_status pe_set_profiles(pe_plan* p, const double* n2, const double* ranges, int count, int on_device) {
@@ -574,6 +599,9 @@ pe_status pe_set_profiles(pe_plan* p, const double* n2, const double* ranges, in
 pe_status pe_clear_profiles(pe_plan* p) {
   if (!p) return PE_ERR_ARG;
   p->nodes = 0;
+  p->complex_profile = false;
+  cudaFree(p->dVi);
+  p->dVi = nullptr;
   p->node_r.clear();
   return PE_OK;
 }

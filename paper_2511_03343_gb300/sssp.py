@@ -199,6 +199,11 @@ class Plan:
             import torch
             assert n2.is_cuda and n2.is_contiguous() and n2.numel() == self.N and n2.dtype == torch.float64
             self._c(lib().pe_set_profile(self._p, n2.data_ptr(), 0, float(range_m), 1))
+        elif np.iscomplexobj(n2):
+            # complex n^2 (absorbing layer): interleaved (re, im) doubles
+            h = np.ascontiguousarray(np.asarray(n2, dtype=np.complex128))
+            assert h.size == self.N
+            self._c(lib().pe_set_profile(self._p, h.ctypes.data, 1, float(range_m), 0))
         else:
             h = np.ascontiguousarray(np.asarray(n2, dtype=np.float64))
             assert h.size == self.N
@@ -219,6 +224,10 @@ class Plan:
     def set_profile_nodes(self, nodes: Sequence[Tuple[float, np.ndarray]]):
         """Replace the profile by (range, n2) nodes."""
         self._c(lib().pe_clear_profiles(self._p))
+        if any(np.iscomplexobj(n2) for _, n2 in nodes):
+            for r, n2 in nodes:
+                self.set_profile(np.asarray(n2, dtype=np.complex128), r)
+            return
         rows = np.stack([np.asarray(n2, dtype=np.float64) for _, n2 in nodes])
         self.set_profiles(rows, [r for r, _ in nodes])
 

@@ -291,7 +291,7 @@ def test_state_errors(sssp):
         pl.set_profile(np.ones(255), 50.0)  # decreasing range
     assert e.value.status == sssp.PE_ERR_ARG
     with pytest.raises(sssp.PEError) as e:
-        pl._c(sssp.lib().pe_set_profile(pl.handle, np.ones(255, dtype=np.float64).ctypes.data, 1, 200.0, 0))
+        pl._c(sssp.lib().pe_set_profile(pl.handle, np.full(255, np.nan).ctypes.data, 0, 200.0, 0))
     assert e.value.status == sssp.PE_ERR_ARG
     pl.close()
 
@@ -427,3 +427,19 @@ def test_dst1_batch_equals_single(sssp, N, count):
     for b in range(count):
         assert np.array_equal(got[b], pl.dst1(x[b]))
     pl.close()
+
+
+@pytest.mark.parametrize("N", [511, 8191])
+def test_absorbing_layer(sssp, N):
+    """Complex n^2 (Section 3.1's complex absorbing potential) in the bottom 20 % of a Munk guide:
+    the march matches the oracle and the field's norm decreases (energy leaves through the layer)."""
+    s = inputs.munk(N=N, freq=60.0 if N < 4096 else 100.0, dr=25.0, steps=40 if N < 4096 else 6)
+    z = s.z
+    za = 0.8 * s.H
+    n2 = s.profiles[0][1].astype(np.complex128) + 1j * 0.02 * np.clip((z - za) / (s.H - za), 0.0, None) ** 2
+    s.profiles = [(0.0, n2)]
+    s.u0 = s.u0 + inputs.gaussian_starter(z, s.k0, 0.9 * s.H)  # energy that reaches the layer
+    u, tl, _, _ = _gpu(sssp, s)
+    ref = _oracle(s)
+    _compare(u, tl, ref)
+    assert np.linalg.norm(u) < 0.999 * np.linalg.norm(s.u0)
