@@ -73,11 +73,11 @@ struct Cfg {
   static constexpr int NW = (NT + 31) / 32;
   static constexpr unsigned MASK = NT >= 32 ? 0xffffffffu : ((1u << NT) - 1u);
   static constexpr int MIN_BLOCKS = NT >= 512 ? 1 : (512 / NT > 16 ? 16 : 512 / NT);
-  // dynamic shared memory: 2 padded buffers, twiddles, t_0 and B_j areas, sin weights, V row
-  // (real and imaginary parts),
+  // dynamic shared memory: 2 padded buffers, twiddles, t_0 and B_j areas, sin weights, V row,
   // scan + reduce
-  static constexpr size_t SMEM = sizeof(float2) * (2 * PADL + 3 * L) + sizeof(float) * (3 * L) +
+  static constexpr size_t SMEM = sizeof(float2) * (2 * PADL + 3 * L) + sizeof(float) * (2 * L) +
                                  sizeof(float2) * NW + sizeof(float) * 2 * NW;
+  static constexpr size_t SMEM_CPLX = SMEM + sizeof(float) * L;  // + imaginary V row
 };
 
 // padded shared-memory index: one pad element per 16 (128 B), so contiguous half-warp
@@ -268,9 +268,9 @@ struct Smem {
     Bs = t0s + C::L;
     sinw = reinterpret_cast<float*>(Bs + C::L);
     Vs = sinw + C::L;
-    Vis = Vs + C::L;
-    scan_s = reinterpret_cast<float2*>(Vis + C::L);
+    scan_s = reinterpret_cast<float2*>(Vs + C::L);
     red = reinterpret_cast<float*>(scan_s + C::NW);
+    Vis = red + 2 * C::NW;  // only present in the complex-profile kernel (SMEM_CPLX)
   }
 };
 
@@ -314,7 +314,7 @@ __device__ __forceinline__ void record_tl(Smem<LOG2L>& sm, const SolveDesc& d, c
 // ---------------------------------------------------------------------------------------
 // The persistent march: blockIdx.x selects the solve.
 // ---------------------------------------------------------------------------------------
-template <int LOG2L>
+template <int LOG2L, bool CPLX>
 __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
     sssp_march_kernel(const SolveDesc* __restrict__ descs, const float2* __restrict__ tw_g,
                       const float* __restrict__ sin_g) {
@@ -343,11 +343,11 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
   int nrec = 0;
   int node = d.node0;
   double next_r = (node + 1 < d.nodes) ? d.node_r[node + 1] : 1e300;
-  const bool cplx = d.Vi != nullptr;
+  constexpr bool cplx = CPLX;  // complex n^2: launched only for solves with an imaginary profile
   if (!iso) {
     const float* Vg = d.V + (size_t)node * L;
     for (int i = t; i < L; i += C::NT) sm.Vs[i] = Vg[i];
-    if (cplx) {
+    if constexpr (cplx) {
       const float* Vig = d.Vi + (size_t)node * L;
       for (int i = t; i < L; i += C::NT) sm.Vis[i] = Vig[i];
     }
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
         next_r = (node + 1 < d.nodes) ? d.node_r[node + 1] : 1e300;
         const float* Vg = d.V + (size_t)node * L;
         for (int i = t; i < L; i += C::NT) sm.Vs[i] = Vg[i];
-        if (cplx) {
+        if constexpr (cplx) {
           const float* Vig = d.Vi + (size_t)node * L;
           for (int i = t; i < L; i += C::NT) sm.Vis[i] = Vig[i];
         }
@@ -411,9 +411,12 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
         float first = 0.f;
         for (int m = 1; m < d.terms; ++m) {
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            sm.bufA[pidx(8 * t + i)] = cplx ? cmul(make_float2(sm.Vs[8 * t + i], sm.Vis[8 * t + i]), tp[i])
-                                            : sm.Vs[8 * t + i] * tp[i];
+          for (int i = 0; i < 8; ++i) {
+            if constexpr (cplx)
+              sm.bufA[pidx(8 * t + i)] = cmul(make_float2(sm.Vs[8 * t + i], sm.Vis[8 * t + i]), tp[i]);
+            else
+              sm.bufA[pidx(8 * t + i)] = sm.Vs[8 * t + i] * tp[i];
+          }
           __syncthreads();
           dst_block<LOG2L>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // DST(V t_{m-1})
           ++ndst;

@@ -107,8 +107,11 @@ cudaError_t set_smem_attr() {
   int dev = 0;
   cudaGetDevice(&dev);
   if (done_dev == dev) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(sssp::sssp_march_kernel<LOG2L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(Cfg<LOG2L>::SMEM));
+  cudaError_t e = cudaFuncSetAttribute(sssp::sssp_march_kernel<LOG2L, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg<LOG2L>::SMEM));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sssp::sssp_march_kernel<LOG2L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(Cfg<LOG2L>::SMEM_CPLX));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(sssp::sssp_dst_kernel<LOG2L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(Cfg<LOG2L>::SMEM));
@@ -117,10 +120,15 @@ cudaError_t set_smem_attr() {
 }
 
 template <int LOG2L>
-cudaError_t launch_march_t(const SolveDesc* dDescs, int count, const TransformTables& tabs, cudaStream_t st) {
+cudaError_t launch_march_t(const SolveDesc* dDescs, int count, const TransformTables& tabs, cudaStream_t st,
+                           bool cplx) {
   cudaError_t e = set_smem_attr<LOG2L>();
   if (e != cudaSuccess) return e;
-  sssp::sssp_march_kernel<LOG2L><<<count, Cfg<LOG2L>::NT, Cfg<LOG2L>::SMEM, st>>>(dDescs, tabs.tw, tabs.sinw);
+  if (cplx)
+    sssp::sssp_march_kernel<LOG2L, true><<<count, Cfg<LOG2L>::NT, Cfg<LOG2L>::SMEM_CPLX, st>>>(dDescs, tabs.tw,
+                                                                                              tabs.sinw);
+  else
+    sssp::sssp_march_kernel<LOG2L, false><<<count, Cfg<LOG2L>::NT, Cfg<LOG2L>::SMEM, st>>>(dDescs, tabs.tw, tabs.sinw);
   return cudaGetLastError();
 }
 
@@ -148,18 +156,19 @@ cudaError_t launch_dst_large_t(const float2* in, float2* out, float scale, float
   return cudaGetLastError();
 }
 
-cudaError_t launch_march(int log2L, const SolveDesc* d, int count, const TransformTables& tabs, cudaStream_t st) {
+cudaError_t launch_march(int log2L, const SolveDesc* d, int count, const TransformTables& tabs, cudaStream_t st,
+                         bool cplx) {
   switch (log2L) {
-    case 3: return launch_march_t<3>(d, count, tabs, st);
-    case 4: return launch_march_t<4>(d, count, tabs, st);
-    case 5: return launch_march_t<5>(d, count, tabs, st);
-    case 6: return launch_march_t<6>(d, count, tabs, st);
-    case 7: return launch_march_t<7>(d, count, tabs, st);
-    case 8: return launch_march_t<8>(d, count, tabs, st);
-    case 9: return launch_march_t<9>(d, count, tabs, st);
-    case 10: return launch_march_t<10>(d, count, tabs, st);
-    case 11: return launch_march_t<11>(d, count, tabs, st);
-    case 12: return launch_march_t<12>(d, count, tabs, st);
+    case 3: return launch_march_t<3>(d, count, tabs, st, cplx);
+    case 4: return launch_march_t<4>(d, count, tabs, st, cplx);
+    case 5: return launch_march_t<5>(d, count, tabs, st, cplx);
+    case 6: return launch_march_t<6>(d, count, tabs, st, cplx);
+    case 7: return launch_march_t<7>(d, count, tabs, st, cplx);
+    case 8: return launch_march_t<8>(d, count, tabs, st, cplx);
+    case 9: return launch_march_t<9>(d, count, tabs, st, cplx);
+    case 10: return launch_march_t<10>(d, count, tabs, st, cplx);
+    case 11: return launch_march_t<11>(d, count, tabs, st, cplx);
+    case 12: return launch_march_t<12>(d, count, tabs, st, cplx);
     case 13: return launch_march_large_t<13>(d, count, tabs, st);
     case 14: return launch_march_large_t<14>(d, count, tabs, st);
     case 15: return launch_march_large_t<15>(d, count, tabs, st);
@@ -613,7 +622,7 @@ pe_status pe_march(pe_plan* p, int steps) {
   if (st != PE_OK) return st;
   if (steps == 0) return PE_OK;
   PE_CUDA(p, cudaMemcpyAsync(p->dDesc, &d, sizeof(d), cudaMemcpyHostToDevice, p->stream));
-  PE_CUDA(p, launch_march(p->log2L, p->dDesc, 1, p->tabs, p->stream));
+  PE_CUDA(p, launch_march(p->log2L, p->dDesc, 1, p->tabs, p->stream, d.Vi != nullptr));
   return PE_OK;
 }
 
@@ -627,9 +636,10 @@ pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
     if (plans[i]->device != p0->device) return fail(p0, PE_ERR_ARG, "plans on different devices");
     if (steps[i] < 0) return fail(p0, PE_ERR_ARG, "steps must be >= 0");
   }
-  // group by size, one launch per group; every CTA marches its own plan its own step count
-  std::map<int, std::vector<SolveDesc>> groups;
-  std::map<int, TransformTables> tabs;
+  // group by (size, complex profile), one launch per group; every CTA marches its own plan its
+  // own step count
+  std::map<std::pair<int, bool>, std::vector<SolveDesc>> groups;
+  std::map<std::pair<int, bool>, TransformTables> tabs;
   for (int i = 0; i < count; ++i) {
     if (steps[i] == 0) continue;
     SolveDesc d;
@@ -638,15 +648,16 @@ pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
       p0->err = plans[i]->err;
       return st;
     }
-    groups[plans[i]->log2L].push_back(d);
-    tabs[plans[i]->log2L] = plans[i]->tabs;
+    const auto key = std::make_pair(plans[i]->log2L, d.Vi != nullptr);
+    groups[key].push_back(d);
+    tabs[key] = plans[i]->tabs;
   }
   for (auto& kv : groups) {
     SolveDesc* dd = nullptr;
     const size_t bytes = sizeof(SolveDesc) * kv.second.size();
     PE_CUDA(p0, cudaMallocAsync(reinterpret_cast<void**>(&dd), bytes, p0->stream));
     PE_CUDA(p0, cudaMemcpyAsync(dd, kv.second.data(), bytes, cudaMemcpyHostToDevice, p0->stream));
-    PE_CUDA(p0, launch_march(kv.first, dd, int(kv.second.size()), tabs[kv.first], p0->stream));
+    PE_CUDA(p0, launch_march(kv.first.first, dd, int(kv.second.size()), tabs[kv.first], p0->stream, kv.first.second));
     PE_CUDA(p0, cudaFreeAsync(dd, p0->stream));
   }
   return PE_OK;
