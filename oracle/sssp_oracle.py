@@ -14,9 +14,10 @@ Propagation"), in complex128:
   X = (k^2 - k0^2 + d_z^2)/k0^2 = V + d_z^2/k0^2, V = n^2 - 1; Eq. (1dhelmholtz)
   defines w_j by (1 + b_j X) w_j = u.
 * Section 3: the isovelocity inverse L_j^{-1} applied diagonally after a
-  discrete trigonometric transform (Eq. inverse_isovel; here the DST-I of the
-  Dirichlet case of Section 3.1), and the Neumann series Eq. (Neumann) for the
-  depth-dependent perturbation.
+  discrete trigonometric transform (Eq. inverse_isovel): the DST-I for the
+  Dirichlet case of Section 3.1 (the workloads), the DFT for periodic and the
+  DCT-I for homogeneous Neumann boundaries; and the Neumann series Eq. (Neumann)
+  for the depth-dependent perturbation.
 * Algorithm 1 (SSSP): per range step, w_j for every Pade term, then
   u_n = e^{ihk0}(d0 u_{n-1} + sum_j d_j w_j).
 
@@ -184,27 +185,80 @@ def idst1(X: np.ndarray) -> np.ndarray:
     return (2.0 / (X.shape[0] + 1)) * dst1(X)
 
 
+def dft(x: np.ndarray) -> np.ndarray:
+    """DFT along axis 0 (periodic boundaries, Section 3): X_m = sum_{n=0..N-1} x_n e^{-2 pi i n m/N},
+    by the explicit sum (argument reduced exactly mod N)."""
+    x = np.asarray(x)
+    N = x.shape[0]
+    idx = np.arange(N, dtype=np.int64)
+    F = np.exp(-2j * np.pi * (np.outer(idx, idx) % N).astype(np.float64) / N)
+    return F @ x
+
+
+def idft(X: np.ndarray) -> np.ndarray:
+    """Inverse DFT: x_n = (1/N) sum_m X_m e^{+2 pi i n m/N}."""
+    return np.conj(dft(np.conj(X))) / X.shape[0]
+
+
+def dct1(x: np.ndarray) -> np.ndarray:
+    """DCT-I along axis 0 (homogeneous Neumann boundaries, Section 3.1), points n = 0..N-1 with
+    z_0 = 0 and z_{N-1} = H: C_m = x_0/2 + (-1)^m x_{N-1}/2 + sum_{n=1..N-2} x_n cos(pi n m/(N-1))."""
+    x = np.asarray(x)
+    N = x.shape[0]
+    K = N - 1
+    idx = np.arange(N, dtype=np.int64)
+    C = np.cos(np.pi * (np.outer(idx, idx) % (2 * K)).astype(np.float64) / K)
+    C[:, 0] *= 0.5
+    C[:, -1] *= 0.5
+    return C @ x
+
+
+def idct1(C: np.ndarray) -> np.ndarray:
+    """Inverse DCT-I: x = (2/(N-1)) DCT-I(C)."""
+    return (2.0 / (C.shape[0] - 1)) * dct1(C)
+
+
 def lambdas(N: int, H: float, k0: float) -> np.ndarray:
     """Eigenvalues of d_z^2/k0^2 on sin(pi m z/H): lambda_m = -(pi m/(k0 H))^2, m = 1..N."""
     m = np.arange(1, N + 1, dtype=np.float64)
     return -(np.pi * m / (k0 * H)) ** 2
 
 
-def apply_Linv(x: np.ndarray, bj, lam: np.ndarray) -> np.ndarray:
-    """L_j^{-1} x = IDST[ DST[x] / (1 + b_j lambda) ]   (Eq. inverse_isovel, DST-I version).
+def lambdas_bc(N: int, H: float, k0: float, bc: str) -> np.ndarray:
+    """Eigenvalues of d_z^2/k0^2 for each boundary condition of Section 3.1:
+    Dirichlet sin(pi m z/H), m = 1..N; periodic e^{2 pi i l z/H} with the signed frequency
+    l = m (m <= N/2) or m - N, lambda = -(2 pi l/(k0 H))^2; Neumann cos(pi m z/H), m = 0..N-1."""
+    if bc == "dirichlet":
+        return lambdas(N, H, k0)
+    m = np.arange(N, dtype=np.float64)
+    if bc == "periodic":
+        l = np.where(m <= N // 2, m, m - N)
+        return -(2.0 * np.pi * l / (k0 * H)) ** 2
+    if bc == "neumann":
+        return -(np.pi * m / (k0 * H)) ** 2
+    raise ValueError(bc)
+
+
+_FWD = {"dirichlet": lambda x: dst1(x), "periodic": lambda x: dft(x), "neumann": lambda x: dct1(x)}
+_INV = {"dirichlet": lambda X: idst1(X), "periodic": lambda X: idft(X), "neumann": lambda X: idct1(X)}
+
+
+def apply_Linv(x: np.ndarray, bj, lam: np.ndarray, bc: str = "dirichlet") -> np.ndarray:
+    """L_j^{-1} x = T^{-1}[ T[x] / (1 + b_j lambda) ]   (Eq. inverse_isovel) with the transform T
+    of the boundary condition (DST-I Dirichlet, DFT periodic, DCT-I Neumann).
 
     ``bj`` may be a scalar or a row of p values (x then has p columns)."""
-    X = dst1(x)
+    X = _FWD[bc](x)
     if X.ndim == 1:
-        return idst1(X / (1.0 + bj * lam))
-    return idst1(X / (1.0 + np.asarray(bj)[None, :] * lam[:, None]))
+        return _INV[bc](X / (1.0 + bj * lam))
+    return _INV[bc](X / (1.0 + np.asarray(bj)[None, :] * lam[:, None]))
 
 
 # ----------------------------------------------------------------------------
 # Neumann series and the SSSP step                     (Eq. Neumann, Algorithm 1)
 # ----------------------------------------------------------------------------
 def neumann_w(u: np.ndarray, V: np.ndarray, b: np.ndarray, lam: np.ndarray, terms: int, tol: float,
-              return_counts: bool = False):
+              return_counts: bool = False, bc: str = "dirichlet"):
     """w_j = sum_{m=0..M} (-b_j L_j^{-1} V)^m L_j^{-1} u for every j (columns), Eq. (Neumann).
 
     ``u`` is one field (N,) used by every j (sum form) or a matrix (N, p) of per-j inputs.
@@ -214,14 +268,14 @@ def neumann_w(u: np.ndarray, V: np.ndarray, b: np.ndarray, lam: np.ndarray, term
     b = np.asarray(b, dtype=np.complex128)
     p = b.shape[0]
     U = np.repeat(u[:, None], p, axis=1) if u.ndim == 1 else u
-    t = apply_Linv(U, b, lam)
+    t = apply_Linv(U, b, lam, bc)
     w = t.copy()
     counts = np.ones(p, dtype=np.int64)
     active = np.ones(p, dtype=bool)
     for m in range(1, max(terms, 1)):
         if not active.any():
             break
-        t = -b[None, :] * apply_Linv(V[:, None] * t, b, lam)
+        t = -b[None, :] * apply_Linv(V[:, None] * t, b, lam, bc)
         t[:, ~active] = 0.0
         w = w + t
         counts[active] += 1
@@ -233,10 +287,13 @@ def neumann_w(u: np.ndarray, V: np.ndarray, b: np.ndarray, lam: np.ndarray, term
 
 @dataclasses.dataclass
 class Grid:
+    """Depth grid: 'dirichlet' N interior points z_n = n H/(N+1), n = 1..N; 'periodic' N points
+    z_n = n H/N, n = 0..N-1; 'neumann' N points z_n = n H/(N-1), n = 0..N-1 (both boundaries)."""
     N: int
     H: float
     k0: float
     dr: float
+    bc: str = "dirichlet"
 
     @property
     def sigma(self) -> float:
@@ -244,13 +301,15 @@ class Grid:
 
     @property
     def lam(self) -> np.ndarray:
-        return lambdas(self.N, self.H, self.k0)
+        if self.bc == "dirichlet":
+            return lambdas(self.N, self.H, self.k0)
+        return lambdas_bc(self.N, self.H, self.k0, self.bc)
 
 
 def step_sum(u: np.ndarray, V: np.ndarray, grid: Grid, plan: PadePlan, terms: int, tol: float) -> np.ndarray:
     """One SSSP range step in the paper's sum form (Algorithm 1):
     u_n = e^{i k0 dr} (d0 u + sum_j d_j w_j)."""
-    w = neumann_w(u, V, plan.b, grid.lam, terms, tol)
+    w = neumann_w(u, V, plan.b, grid.lam, terms, tol, bc=grid.bc)
     return np.exp(1j * grid.sigma) * (plan.d0 * u + w @ plan.d)
 
 
@@ -259,7 +318,7 @@ def step_product(u: np.ndarray, V: np.ndarray, grid: Grid, plan: PadePlan, terms
     y -> (a_j/b_j) y + (1 - a_j/b_j) w_j with (1 + b_j X) w_j = y; then u_n = e^{i k0 dr} P(0) y."""
     y = u.astype(np.complex128)
     for aj, bj in zip(plan.a, plan.b):
-        w = neumann_w(y, V, np.array([bj]), grid.lam, terms, tol)[:, 0]
+        w = neumann_w(y, V, np.array([bj]), grid.lam, terms, tol, bc=grid.bc)[:, 0]
         y = (aj / bj) * y + (1.0 - aj / bj) * w
     return np.exp(1j * grid.sigma) * plan.pc[0] * y
 
@@ -320,10 +379,16 @@ def march(u0: np.ndarray, profiles, grid: Grid, pade_order: int, steps: int, ter
 # dense brute force (tiny N only)
 # ----------------------------------------------------------------------------
 def dense_X(grid: Grid, V: np.ndarray) -> np.ndarray:
-    """X = S^{-1} diag(lambda) S + diag(V) as a dense N x N matrix (S the DST-I matrix)."""
-    S = sine_matrix(grid.N)
-    Sinv = (2.0 / (grid.N + 1)) * S
-    return Sinv @ np.diag(grid.lam) @ S + np.diag(np.asarray(V, dtype=np.complex128))
+    """X = T^{-1} diag(lambda) T + diag(V) as a dense N x N matrix (T the transform of the
+    boundary condition, built by transforming the identity)."""
+    if grid.bc == "dirichlet":
+        S = sine_matrix(grid.N)
+        Sinv = (2.0 / (grid.N + 1)) * S
+        return Sinv @ np.diag(grid.lam) @ S + np.diag(np.asarray(V, dtype=np.complex128))
+    I = np.eye(grid.N, dtype=np.complex128)
+    T = _FWD[grid.bc](I)
+    Tinv = _INV[grid.bc](I)
+    return Tinv @ np.diag(grid.lam) @ T + np.diag(np.asarray(V, dtype=np.complex128))
 
 
 def dense_pade_step(X: np.ndarray, plan: PadePlan, form: str = "product") -> np.ndarray:

@@ -28,8 +28,13 @@ C0_DEFAULT = 1500.0  # reference sound speed [m/s] used for k0 = omega / c0
 # ----------------------------------------------------------------------------
 # grid
 # ----------------------------------------------------------------------------
-def depth_grid(N: int, H: float) -> np.ndarray:
-    """Interior depth points z_n = n*dz, n = 1..N, dz = H/(N+1) (Dirichlet at 0 and H)."""
+def depth_grid(N: int, H: float, bc: str = "dirichlet") -> np.ndarray:
+    """Depth points of the grid: Dirichlet N interior points z_n = n H/(N+1), n = 1..N;
+    periodic N points z_n = n H/N, n = 0..N-1; Neumann N points z_n = n H/(N-1), n = 0..N-1."""
+    if bc == "periodic":
+        return (H / N) * np.arange(N, dtype=np.float64)
+    if bc == "neumann":
+        return (H / (N - 1)) * np.arange(N, dtype=np.float64)
     dz = H / (N + 1)
     return dz * np.arange(1, N + 1, dtype=np.float64)
 

@@ -441,3 +441,86 @@ def test_planted_mistakes_are_caught(monkeypatch, mutation):
     finally:
         O._SINE_CACHE.clear()
     assert failed, f"no pin caught {mutation.__name__}"
+
+
+# ----------------------------------------------------------------------------- other boundary conditions
+def test_dft_and_dct_against_library():
+    """DFT vs numpy.fft.fft; DCT-I vs scipy.fft.dct(type=1), whose definition carries a factor 2;
+    both inverses round-trip."""
+    import scipy.fft
+    x = _rng_field(64, 21)
+    assert np.max(np.abs(O.dft(x) - np.fft.fft(x))) < 1e-11
+    ref = scipy.fft.dct(x.real, type=1) / 2 + 1j * scipy.fft.dct(x.imag, type=1) / 2
+    assert np.max(np.abs(O.dct1(x) - ref)) < 1e-11
+    assert np.max(np.abs(O.idft(O.dft(x)) - x)) < 1e-12
+    assert np.max(np.abs(O.idct1(O.dct1(x)) - x)) < 1e-12
+
+
+@pytest.mark.parametrize("bc,N,mode", [("periodic", 32, 3), ("periodic", 32, -5), ("neumann", 33, 4), ("neumann", 33, 0)])
+def test_single_mode_other_bc(bc, N, mode):
+    """A single eigenmode of d_z^2 under the boundary condition (e^{2 pi i l z/H} periodic,
+    cos(pi m z/H) Neumann) marched in isovelocity is (e^{i sigma} R(lambda))^n times itself,
+    with lambda from calculus and R from mpmath's Pade."""
+    g = O.Grid(N=N, H=100.0, k0=2 * math.pi * 100 / 1500.0, dr=5.0, bc=bc)
+    mpmath, P, Q = _mp_pade(g.sigma, 4)
+    z = inputs.depth_grid(N, g.H, bc)
+    if bc == "periodic":
+        u0 = np.exp(2j * np.pi * mode * z / g.H)
+        lam = -(2 * np.pi * mode / (g.k0 * g.H)) ** 2
+    else:
+        u0 = np.cos(np.pi * mode * z / g.H).astype(np.complex128)
+        lam = -(np.pi * mode / (g.k0 * g.H)) ** 2
+    G = complex(mpmath.exp(1j * g.sigma) * mpmath.polyval(P[::-1], lam) / mpmath.polyval(Q[::-1], lam))
+    res = O.march(u0, [(0.0, np.ones(N))], g, 4, 15, 1, 1e-10, tl_every=0)
+    assert np.max(np.abs(res.u - G ** 15 * u0)) < 1e-11
+
+
+@pytest.mark.parametrize("bc,N", [("periodic", 16), ("neumann", 17)])
+@pytest.mark.parametrize("form", ["sum", "product"])
+def test_bruteforce_step_other_bc(bc, N, form):
+    """P1 for the periodic and Neumann transforms: one step (converged Neumann series) equals
+    the dense LU operator built on the dense X of that boundary condition."""
+    g = O.Grid(N=N, H=100.0, k0=2 * math.pi * 100 / 1500.0, dr=5.0, bc=bc)
+    rng = np.random.default_rng(31)
+    V = 0.05 * rng.standard_normal(N)
+    u = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    plan = O.pade_plan(g.sigma, 4)
+    stepper = O.step_sum if form == "sum" else O.step_product
+    got = stepper(u, V, g, plan, 200, 1e-16)
+    ref = O.dense_pade_step(O.dense_X(g, V), plan, form) @ u
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-11
+
+
+def test_spectral_second_derivative_other_bc():
+    """The spectral d_z^2 of each transform on a band-limited function equals calculus:
+    periodic cos(2 pi z/H) + sin(6 pi z/H); Neumann cos(pi z/H) + cos(3 pi z/H)."""
+    H, k0 = 100.0, 0.4
+    for bc, N, f, d2 in [
+        ("periodic", 64, lambda z: np.cos(2 * np.pi * z / H) + np.sin(6 * np.pi * z / H),
+         lambda z: -(2 * np.pi / H) ** 2 * np.cos(2 * np.pi * z / H) - (6 * np.pi / H) ** 2 * np.sin(6 * np.pi * z / H)),
+        ("neumann", 65, lambda z: np.cos(np.pi * z / H) + np.cos(3 * np.pi * z / H),
+         lambda z: -(np.pi / H) ** 2 * np.cos(np.pi * z / H) - (3 * np.pi / H) ** 2 * np.cos(3 * np.pi * z / H)),
+    ]:
+        g = O.Grid(N=N, H=H, k0=k0, dr=1.0, bc=bc)
+        z = inputs.depth_grid(N, H, bc)
+        fwd = O.dft if bc == "periodic" else O.dct1
+        inv = O.idft if bc == "periodic" else O.idct1
+        Xu = inv(g.lam * fwd(f(z).astype(np.complex128)))
+        assert np.max(np.abs(Xu - d2(z) / k0 ** 2)) / np.max(np.abs(d2(z) / k0 ** 2)) < 1e-11
+
+
+@pytest.mark.parametrize("bc,N", [("periodic", 64), ("neumann", 65)])
+def test_norm_conservation_other_bc(bc, N):
+    """P5: the step is unitary for real n^2 — in the plain 2-norm (periodic) and in the
+    trapezoid-weighted norm (Neumann: end points weighted 1/2, the DCT-I's inner product)."""
+    g = O.Grid(N=N, H=5000.0, k0=2 * math.pi * 50 / 1500, dr=50.0, bc=bc)
+    z = inputs.depth_grid(N, g.H, bc)
+    n2 = inputs.n2_from_c(inputs.munk_c(z))
+    rng = np.random.default_rng(41)
+    u0 = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    res = O.march(u0, [(0.0, n2)], g, 6, 30, 40, 1e-14, tl_every=0)
+    w = np.ones(N)
+    if bc == "neumann":
+        w[0] = w[-1] = 0.5
+    nrm = lambda u: math.sqrt(np.sum(w * np.abs(u) ** 2))
+    assert abs(nrm(res.u) / nrm(u0) - 1) < 1e-9
