@@ -71,6 +71,16 @@ int pe_abi_version(void);
 pe_status pe_plan_create(pe_plan** out, int N, double H, double k0, double dr, int pade_order,
                          int neumann_terms, double neumann_tol, void* cuda_stream);
 
+/*
+ * Boundary conditions of Section 3.1: homogeneous Dirichlet (the DST-I, pe_plan_create's
+ * default) or periodic (the DFT; N grid points z_n = n H/N, n = 0..N-1, N a power of two in
+ * [8, 4096]; eigenvalues -(2 pi l/(k0 H))^2 for the signed frequency l).  For a periodic plan
+ * every "DST-I" of this header is the DFT, N values in and out.
+ */
+enum { PE_BC_DIRICHLET = 0, PE_BC_PERIODIC = 1 };
+pe_status pe_plan_create_bc(pe_plan** out, int N, double H, double k0, double dr, int pade_order, int neumann_terms,
+                            double neumann_tol, int bc, void* cuda_stream);
+
 /* Release every device and host resource of the plan (NULL is ignored). */
 void pe_plan_destroy(pe_plan* plan);
 

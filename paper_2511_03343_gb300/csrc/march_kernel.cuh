@@ -151,8 +151,10 @@ __device__ __forceinline__ void fft_pass(const float2* __restrict__ src, float2*
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[pidx(j + r * NB)];
     const int k = j & (NS - 1);
+    if constexpr (NS > 1) {
 #pragma unroll
-    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[OFF + (r - 1) * NS + k]);
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[OFF + (r - 1) * NS + k]);
+    }
     dftR<R>(v);
     const int base = (j - k) * R + k;
 #pragma unroll
@@ -237,6 +239,53 @@ __device__ __forceinline__ void dst_block(float2* a, float2* b, const float2* __
   }
 }
 
+// Boundary conditions of Section 3.1: homogeneous Dirichlet (DST-I, the workloads) and
+// periodic (DFT).
+constexpr int kBcDirichlet = 0;
+constexpr int kBcPeriodic = 1;
+
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+// Unnormalised DFT of the L values in `a` (natural order, padded) into out[0..8) = X_{8t..8t+8)
+// of thread t; INV uses e^{+2 pi i n m/L} (by conjugating input and output).  On return every
+// thread has finished reading both buffers.
+template <int LOG2L, bool INV>
+__device__ __forceinline__ void dft_block(float2* a, float2* b, const float2* __restrict__ tw, float2 (&out)[8]) {
+  constexpr int L = 1 << LOG2L;
+  const int t = threadIdx.x;
+  {
+    float2 v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const float2 x = a[pidx(t + r * (L / 8))];
+      v[r] = INV ? conjf2(x) : x;
+    }
+    dft8(v);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) b[pidx(8 * t + r)] = v[r];
+  }
+  __syncthreads();
+  const float2* F = fft_rest<LOG2L, 8>(b, a, tw);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float2 x = F[pidx(8 * t + i)];
+    out[i] = INV ? conjf2(x) : x;
+  }
+  __syncthreads();
+}
+
+// The transform of the boundary condition: TO_DEPTH maps spectral coefficients to depth values
+// (the inverse transform up to the scale folded into the tables), otherwise depth -> spectral.
+template <int LOG2L, int BC, bool TO_DEPTH>
+__device__ __forceinline__ void xform(float2* a, float2* b, const float2* __restrict__ tw,
+                                      const float* __restrict__ sinw, float2* scan_s, float2 (&out)[8]) {
+  if constexpr (BC == kBcPeriodic) {
+    dft_block<LOG2L, TO_DEPTH>(a, b, tw, out);
+  } else {
+    dst_block<LOG2L>(a, b, tw, sinw, scan_s, out);  // DST-I is its own inverse
+  }
+}
+
 template <int LOG2L>
 __device__ __forceinline__ void load_tables(float2* tw, float* sinw, const float2* __restrict__ tw_g,
                                             const float* __restrict__ sin_g) {
@@ -293,7 +342,7 @@ __device__ __forceinline__ void store8(float2* p, const float2 (&v)[8]) {
 }
 
 // TL row after a step: physical envelope u = (2/L) DST(y), TL = -20 log10|u| + 10 log10 r.
-template <int LOG2L>
+template <int LOG2L, int BC>
 __device__ __forceinline__ void record_tl(Smem<LOG2L>& sm, const SolveDesc& d, const float2 (&y)[8], float out_scale,
                                           int s, int nrec) {
   const int t = threadIdx.x;
@@ -301,20 +350,21 @@ __device__ __forceinline__ void record_tl(Smem<LOG2L>& sm, const SolveDesc& d, c
   for (int i = 0; i < 8; ++i) sm.bufA[pidx(8 * t + i)] = out_scale * y[i];
   __syncthreads();
   float2 u[8];
-  dst_block<LOG2L>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, u);
+  xform<LOG2L, BC, true>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, u);
   const float lr = float(10.0 * log10(d.r0 + double(s + 1) * d.dr));
   float* row = d.tl + (size_t)(d.rec0 + nrec) * d.N;
+  constexpr int off = (BC == kBcPeriodic) ? 0 : 1;  // Dirichlet: depth index 0 is the boundary
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int n = 8 * t + i;
-    if (n >= 1) row[n - 1] = fmaf(-10.f, log10f(cabs2(u[i])), lr);
+    if (n >= off) row[n - off] = fmaf(-10.f, log10f(cabs2(u[i])), lr);
   }
 }
 
 // ---------------------------------------------------------------------------------------
 // The persistent march: blockIdx.x selects the solve.
 // ---------------------------------------------------------------------------------------
-template <int LOG2L, bool CPLX>
+template <int LOG2L, bool CPLX, int BC>
 __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
     sssp_march_kernel(const SolveDesc* __restrict__ descs, const float2* __restrict__ tw_g,
                       const float* __restrict__ sin_g) {
@@ -335,7 +385,7 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
 
   float2 y[8];
   load8<LOG2L>(d.yhat + 8 * t, y);
-  const float out_scale = 2.0f / float(L);
+  const float out_scale = (BC == kBcPeriodic ? 1.0f : 2.0f) / float(L);
   const bool iso = d.terms <= 1;
   const float tol2f = float(d.tol2);
   int status = kStatusOk;
@@ -367,7 +417,7 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
       for (int i = 0; i < 8; ++i) y[i] = ffmul(G[i], y[i]);
       const long long gs = d.step0 + s + 1;
       if (d.tl_every > 0 && gs % d.tl_every == 0) {
-        record_tl<LOG2L>(sm, d, y, out_scale, s, nrec);
+        record_tl<LOG2L, BC>(sm, d, y, out_scale, s, nrec);
         ++ndst;
         ++nrec;
       }
@@ -406,7 +456,7 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
           }
         }
         __syncthreads();
-        dst_block<LOG2L>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // t_0 in depth space
+        xform<LOG2L, BC, true>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // t_0 in depth space
         ++ndst;
         float first = 0.f;
         for (int m = 1; m < d.terms; ++m) {
@@ -418,7 +468,7 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
               sm.bufA[pidx(8 * t + i)] = sm.Vs[8 * t + i] * tp[i];
           }
           __syncthreads();
-          dst_block<LOG2L>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // DST(V t_{m-1})
+          xform<LOG2L, BC, false>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // T(V t_{m-1})
           ++ndst;
           float nt = 0.f, nw = 0.f;
 #pragma unroll
@@ -467,7 +517,7 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
             break;
           }
           if (snt <= tol2f * snw) break;
-          dst_block<LOG2L>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // t_m in depth space
+          xform<LOG2L, BC, true>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // t_m in depth space
           ++ndst;
         }
         {
@@ -480,7 +530,7 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
       if (status != kStatusOk) break;
       const long long gs = d.step0 + s + 1;
       if (d.tl_every > 0 && gs % d.tl_every == 0) {
-        record_tl<LOG2L>(sm, d, y, out_scale, s, nrec);
+        record_tl<LOG2L, BC>(sm, d, y, out_scale, s, nrec);
         ++ndst;
         ++nrec;
       }
@@ -492,7 +542,7 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
   for (int i = 0; i < 8; ++i) sm.bufA[pidx(8 * t + i)] = out_scale * y[i];
   __syncthreads();
   float2 u[8];
-  dst_block<LOG2L>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, u);
+  xform<LOG2L, BC, true>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, u);
   ++ndst;
   store8<LOG2L>(d.field + 8 * t, u);
   if (t == 0) {
@@ -503,7 +553,7 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
 
 // DST-I of one field per CTA: out = scale * DST(in); field b = blockIdx.x reads N values at
 // in + b * in_stride (n = 1..N) and writes L values at out + b * out_stride.
-template <int LOG2L>
+template <int LOG2L, int BC = kBcDirichlet>
 __global__ void __launch_bounds__(Cfg<LOG2L>::NT)
     sssp_dst_kernel(const float2* __restrict__ in, float2* __restrict__ out, float scale,
                     const float2* __restrict__ tw_g, const float* __restrict__ sin_g, long long in_stride = 0,
@@ -515,10 +565,11 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT)
   in += blockIdx.x * in_stride;
   out += blockIdx.x * out_stride;
   load_tables<LOG2L>(sm.tw, sm.sinw, tw_g, sin_g);
-  for (int n = t; n < C::L; n += C::NT) sm.bufA[pidx(n)] = (n == 0) ? make_float2(0.f, 0.f) : in[n - 1];
+  for (int n = t; n < C::L; n += C::NT)
+    sm.bufA[pidx(n)] = (BC == kBcPeriodic) ? in[n] : ((n == 0) ? make_float2(0.f, 0.f) : in[n - 1]);
   __syncthreads();
   float2 o[8];
-  dst_block<LOG2L>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, o);
+  xform<LOG2L, BC, false>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, o);
 #pragma unroll
   for (int i = 0; i < 8; ++i) o[i] = scale * o[i];
   store8<LOG2L>(out + 8 * t, o);

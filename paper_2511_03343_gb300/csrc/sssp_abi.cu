@@ -10,6 +10,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/sssp.h"
@@ -107,38 +108,50 @@ cudaError_t set_smem_attr() {
   int dev = 0;
   cudaGetDevice(&dev);
   if (done_dev == dev) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(sssp::sssp_march_kernel<LOG2L, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg<LOG2L>::SMEM));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(sssp::sssp_march_kernel<LOG2L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(Cfg<LOG2L>::SMEM_CPLX));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(sssp::sssp_dst_kernel<LOG2L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(Cfg<LOG2L>::SMEM));
+  const int sm = int(Cfg<LOG2L>::SMEM), smc = int(Cfg<LOG2L>::SMEM_CPLX);
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(sssp::sssp_march_kernel<LOG2L, false, sssp::kBcDirichlet>, a, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(sssp::sssp_march_kernel<LOG2L, true, sssp::kBcDirichlet>, a, smc);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(sssp::sssp_march_kernel<LOG2L, false, sssp::kBcPeriodic>, a, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(sssp::sssp_march_kernel<LOG2L, true, sssp::kBcPeriodic>, a, smc);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(sssp::sssp_dst_kernel<LOG2L, sssp::kBcDirichlet>, a, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(sssp::sssp_dst_kernel<LOG2L, sssp::kBcPeriodic>, a, sm);
   if (e == cudaSuccess) done_dev = dev;
   return e;
 }
 
 template <int LOG2L>
 cudaError_t launch_march_t(const SolveDesc* dDescs, int count, const TransformTables& tabs, cudaStream_t st,
-                           bool cplx) {
+                           bool cplx, int bc) {
   cudaError_t e = set_smem_attr<LOG2L>();
   if (e != cudaSuccess) return e;
-  if (cplx)
-    sssp::sssp_march_kernel<LOG2L, true><<<count, Cfg<LOG2L>::NT, Cfg<LOG2L>::SMEM_CPLX, st>>>(dDescs, tabs.tw,
-                                                                                              tabs.sinw);
-  else
-    sssp::sssp_march_kernel<LOG2L, false><<<count, Cfg<LOG2L>::NT, Cfg<LOG2L>::SMEM, st>>>(dDescs, tabs.tw, tabs.sinw);
+  const int nt = Cfg<LOG2L>::NT;
+  const size_t sm = Cfg<LOG2L>::SMEM, smc = Cfg<LOG2L>::SMEM_CPLX;
+  if (bc == sssp::kBcPeriodic) {
+    if (cplx)
+      sssp::sssp_march_kernel<LOG2L, true, sssp::kBcPeriodic><<<count, nt, smc, st>>>(dDescs, tabs.tw, tabs.sinw);
+    else
+      sssp::sssp_march_kernel<LOG2L, false, sssp::kBcPeriodic><<<count, nt, sm, st>>>(dDescs, tabs.tw, tabs.sinw);
+  } else {
+    if (cplx)
+      sssp::sssp_march_kernel<LOG2L, true, sssp::kBcDirichlet><<<count, nt, smc, st>>>(dDescs, tabs.tw, tabs.sinw);
+    else
+      sssp::sssp_march_kernel<LOG2L, false, sssp::kBcDirichlet><<<count, nt, sm, st>>>(dDescs, tabs.tw, tabs.sinw);
+  }
   return cudaGetLastError();
 }
 
 template <int LOG2L>
 cudaError_t launch_dst_t(const float2* in, float2* out, float scale, const TransformTables& tabs, cudaStream_t st,
-                         int count = 1, long long in_stride = 0, long long out_stride = 0) {
+                         int count = 1, long long in_stride = 0, long long out_stride = 0, int bc = 0) {
   cudaError_t e = set_smem_attr<LOG2L>();
   if (e != cudaSuccess) return e;
-  sssp::sssp_dst_kernel<LOG2L><<<count, Cfg<LOG2L>::NT, Cfg<LOG2L>::SMEM, st>>>(in, out, scale, tabs.tw, tabs.sinw,
-                                                                                in_stride, out_stride);
+  if (bc == sssp::kBcPeriodic)
+    sssp::sssp_dst_kernel<LOG2L, sssp::kBcPeriodic><<<count, Cfg<LOG2L>::NT, Cfg<LOG2L>::SMEM, st>>>(
+        in, out, scale, tabs.tw, tabs.sinw, in_stride, out_stride);
+  else
+    sssp::sssp_dst_kernel<LOG2L, sssp::kBcDirichlet><<<count, Cfg<LOG2L>::NT, Cfg<LOG2L>::SMEM, st>>>(
+        in, out, scale, tabs.tw, tabs.sinw, in_stride, out_stride);
   return cudaGetLastError();
 }
 
@@ -157,18 +170,18 @@ cudaError_t launch_dst_large_t(const float2* in, float2* out, float scale, float
 }
 
 cudaError_t launch_march(int log2L, const SolveDesc* d, int count, const TransformTables& tabs, cudaStream_t st,
-                         bool cplx) {
+                         bool cplx, int bc) {
   switch (log2L) {
-    case 3: return launch_march_t<3>(d, count, tabs, st, cplx);
-    case 4: return launch_march_t<4>(d, count, tabs, st, cplx);
-    case 5: return launch_march_t<5>(d, count, tabs, st, cplx);
-    case 6: return launch_march_t<6>(d, count, tabs, st, cplx);
-    case 7: return launch_march_t<7>(d, count, tabs, st, cplx);
-    case 8: return launch_march_t<8>(d, count, tabs, st, cplx);
-    case 9: return launch_march_t<9>(d, count, tabs, st, cplx);
-    case 10: return launch_march_t<10>(d, count, tabs, st, cplx);
-    case 11: return launch_march_t<11>(d, count, tabs, st, cplx);
-    case 12: return launch_march_t<12>(d, count, tabs, st, cplx);
+    case 3: return launch_march_t<3>(d, count, tabs, st, cplx, bc);
+    case 4: return launch_march_t<4>(d, count, tabs, st, cplx, bc);
+    case 5: return launch_march_t<5>(d, count, tabs, st, cplx, bc);
+    case 6: return launch_march_t<6>(d, count, tabs, st, cplx, bc);
+    case 7: return launch_march_t<7>(d, count, tabs, st, cplx, bc);
+    case 8: return launch_march_t<8>(d, count, tabs, st, cplx, bc);
+    case 9: return launch_march_t<9>(d, count, tabs, st, cplx, bc);
+    case 10: return launch_march_t<10>(d, count, tabs, st, cplx, bc);
+    case 11: return launch_march_t<11>(d, count, tabs, st, cplx, bc);
+    case 12: return launch_march_t<12>(d, count, tabs, st, cplx, bc);
     case 13: return launch_march_large_t<13>(d, count, tabs, st);
     case 14: return launch_march_large_t<14>(d, count, tabs, st);
     case 15: return launch_march_large_t<15>(d, count, tabs, st);
@@ -178,39 +191,39 @@ cudaError_t launch_march(int log2L, const SolveDesc* d, int count, const Transfo
 }
 
 cudaError_t launch_dst(int log2L, const float2* in, float2* out, float scale, const TransformTables& tabs,
-                       cudaStream_t st, float2* work = nullptr) {
+                       cudaStream_t st, float2* work = nullptr, int bc = 0) {
   switch (log2L) {
     case 13: return launch_dst_large_t<13>(in, out, scale, work, tabs, st);
     case 14: return launch_dst_large_t<14>(in, out, scale, work, tabs, st);
     case 15: return launch_dst_large_t<15>(in, out, scale, work, tabs, st);
     case 16: return launch_dst_large_t<16>(in, out, scale, work, tabs, st);
-    case 3: return launch_dst_t<3>(in, out, scale, tabs, st);
-    case 4: return launch_dst_t<4>(in, out, scale, tabs, st);
-    case 5: return launch_dst_t<5>(in, out, scale, tabs, st);
-    case 6: return launch_dst_t<6>(in, out, scale, tabs, st);
-    case 7: return launch_dst_t<7>(in, out, scale, tabs, st);
-    case 8: return launch_dst_t<8>(in, out, scale, tabs, st);
-    case 9: return launch_dst_t<9>(in, out, scale, tabs, st);
-    case 10: return launch_dst_t<10>(in, out, scale, tabs, st);
-    case 11: return launch_dst_t<11>(in, out, scale, tabs, st);
-    case 12: return launch_dst_t<12>(in, out, scale, tabs, st);
+    case 3: return launch_dst_t<3>(in, out, scale, tabs, st, 1, 0, 0, bc);
+    case 4: return launch_dst_t<4>(in, out, scale, tabs, st, 1, 0, 0, bc);
+    case 5: return launch_dst_t<5>(in, out, scale, tabs, st, 1, 0, 0, bc);
+    case 6: return launch_dst_t<6>(in, out, scale, tabs, st, 1, 0, 0, bc);
+    case 7: return launch_dst_t<7>(in, out, scale, tabs, st, 1, 0, 0, bc);
+    case 8: return launch_dst_t<8>(in, out, scale, tabs, st, 1, 0, 0, bc);
+    case 9: return launch_dst_t<9>(in, out, scale, tabs, st, 1, 0, 0, bc);
+    case 10: return launch_dst_t<10>(in, out, scale, tabs, st, 1, 0, 0, bc);
+    case 11: return launch_dst_t<11>(in, out, scale, tabs, st, 1, 0, 0, bc);
+    case 12: return launch_dst_t<12>(in, out, scale, tabs, st, 1, 0, 0, bc);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_dst_batch(int log2L, const float2* in, float2* out, const TransformTables& tabs, cudaStream_t st,
-                             float2* work, int count, long long in_stride, long long out_stride) {
+                             float2* work, int count, long long in_stride, long long out_stride, int bc = 0) {
   switch (log2L) {
-    case 3: return launch_dst_t<3>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
-    case 4: return launch_dst_t<4>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
-    case 5: return launch_dst_t<5>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
-    case 6: return launch_dst_t<6>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
-    case 7: return launch_dst_t<7>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
-    case 8: return launch_dst_t<8>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
-    case 9: return launch_dst_t<9>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
-    case 10: return launch_dst_t<10>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
-    case 11: return launch_dst_t<11>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
-    case 12: return launch_dst_t<12>(in, out, 1.f, tabs, st, count, in_stride, out_stride);
+    case 3: return launch_dst_t<3>(in, out, 1.f, tabs, st, count, in_stride, out_stride, bc);
+    case 4: return launch_dst_t<4>(in, out, 1.f, tabs, st, count, in_stride, out_stride, bc);
+    case 5: return launch_dst_t<5>(in, out, 1.f, tabs, st, count, in_stride, out_stride, bc);
+    case 6: return launch_dst_t<6>(in, out, 1.f, tabs, st, count, in_stride, out_stride, bc);
+    case 7: return launch_dst_t<7>(in, out, 1.f, tabs, st, count, in_stride, out_stride, bc);
+    case 8: return launch_dst_t<8>(in, out, 1.f, tabs, st, count, in_stride, out_stride, bc);
+    case 9: return launch_dst_t<9>(in, out, 1.f, tabs, st, count, in_stride, out_stride, bc);
+    case 10: return launch_dst_t<10>(in, out, 1.f, tabs, st, count, in_stride, out_stride, bc);
+    case 11: return launch_dst_t<11>(in, out, 1.f, tabs, st, count, in_stride, out_stride, bc);
+    case 12: return launch_dst_t<12>(in, out, 1.f, tabs, st, count, in_stride, out_stride, bc);
     case 13: return launch_dst_large_t<13>(in, out, 1.f, work, tabs, st, count, in_stride, out_stride);
     case 14: return launch_dst_large_t<14>(in, out, 1.f, work, tabs, st, count, in_stride, out_stride);
     case 15: return launch_dst_large_t<15>(in, out, 1.f, work, tabs, st, count, in_stride, out_stride);
@@ -219,10 +232,11 @@ cudaError_t launch_dst_batch(int log2L, const float2* in, float2* out, const Tra
   return cudaErrorInvalidValue;
 }
 
-__global__ void carrier_kernel(const float2* __restrict__ field, float2* __restrict__ out, float c, float s, int N) {
+__global__ void carrier_kernel(const float2* __restrict__ field, float2* __restrict__ out, float c, float s, int N,
+                               int off) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n < N) {
-    const float2 v = field[n + 1];
+    const float2 v = field[n + off];
     out[n] = make_float2(c * v.x - s * v.y, c * v.y + s * v.x);
   }
 }
@@ -403,15 +417,28 @@ void pe_plan_destroy(pe_plan* p) {
 
 pe_status pe_plan_create(pe_plan** out, int N, double H, double k0, double dr, int pade_order, int neumann_terms,
                          double neumann_tol, void* cuda_stream) {
+  return pe_plan_create_bc(out, N, H, k0, dr, pade_order, neumann_terms, neumann_tol, PE_BC_DIRICHLET, cuda_stream);
+}
+
+pe_status pe_plan_create_bc(pe_plan** out, int N, double H, double k0, double dr, int pade_order, int neumann_terms,
+                            double neumann_tol, int bc, void* cuda_stream) {
   g_create_error.clear();
   if (!out) {
     g_create_error = "out is NULL";
     return PE_ERR_ARG;
   }
   *out = nullptr;
-  const int log2L = ilog2_exact(N + 1);
-  if (N < 1 || log2L < kMinLog2 || log2L > kMaxLog2) {
+  if (bc != PE_BC_DIRICHLET && bc != PE_BC_PERIODIC) {
+    g_create_error = "bc must be PE_BC_DIRICHLET or PE_BC_PERIODIC";
+    return PE_ERR_ARG;
+  }
+  const int log2L = ilog2_exact(bc == PE_BC_PERIODIC ? N : N + 1);
+  if (bc == PE_BC_DIRICHLET && (N < 1 || log2L < kMinLog2 || log2L > kMaxLog2)) {
     g_create_error = "N + 1 must be a power of two in [8, 65536]";
+    return PE_ERR_ARG;
+  }
+  if (bc == PE_BC_PERIODIC && (N < 1 || log2L < kMinLog2 || log2L > kMaxSmemLog2)) {
+    g_create_error = "periodic grids: N must be a power of two in [8, 4096]";
     return PE_ERR_ARG;
   }
   if (!(H > 0) || !(k0 > 0) || !(dr > 0) || !std::isfinite(H) || !std::isfinite(k0) || !std::isfinite(dr)) {
@@ -428,8 +455,10 @@ pe_status pe_plan_create(pe_plan** out, int N, double H, double k0, double dr, i
   }
   pe_plan* p = new pe_plan();
   p->N = N;
-  p->L = N + 1;
+  p->L = 1 << log2L;
   p->log2L = log2L;
+  p->bc = bc;
+  p->off = (bc == PE_BC_PERIODIC) ? 0 : 1;
   p->p = pade_order;
   p->terms = neumann_terms;
   p->H = H;
@@ -456,9 +485,13 @@ pe_status pe_plan_create(pe_plan** out, int N, double H, double k0, double dr, i
   const int L = p->L, P = pade_order;
   std::vector<float4> R(size_t(P) * L), G(L);
   std::vector<float2> A(size_t(P) * L), B(size_t(P) * L);
-  const double scale = 2.0 / double(L);
+  // Dirichlet: sin(pi m z/H), m = 1..N (m = 0 a zero pad), unnormalised DST-I pair with 2/L;
+  // periodic: e^{2 pi i l z/H} with the signed frequency l, DFT pair with 1/L
+  const bool periodic = (bc == PE_BC_PERIODIC);
+  const double scale = (periodic ? 1.0 : 2.0) / double(L);
   for (int m = 0; m < L; ++m) {
-    const double x = M_PI * double(m) / (k0 * H);
+    const double l = periodic ? double(m <= L / 2 ? m : m - L) : double(m);
+    const double x = (periodic ? 2.0 : 1.0) * M_PI * l / (k0 * H);
     const double lam = -x * x;
     cd g(1.0, 0.0);
     for (int j = 0; j < P; ++j) {
@@ -467,7 +500,7 @@ pe_status pe_plan_create(pe_plan** out, int N, double H, double k0, double dr, i
       const cd r = (1.0 + a * lam) / q;
       g *= r;
       const size_t ix = size_t(j) * L + m;
-      if (m == 0) {
+      if (m == 0 && !periodic) {
         R[ix] = make_float4(0, 0, 0, 0);
         A[ix] = make_float2(0, 0);
         B[ix] = make_float2(0, 0);
@@ -478,12 +511,12 @@ pe_status pe_plan_create(pe_plan** out, int N, double H, double k0, double dr, i
       A[ix] = make_float2(float(av.real()), float(av.imag()));
       B[ix] = make_float2(float(bv.real()), float(bv.imag()));
     }
-    if (m == 0) G[m] = make_float4(0, 0, 0, 0);
+    if (m == 0 && !periodic) G[m] = make_float4(0, 0, 0, 0);
     else split_ff(g, &G[m]);
   }
   for (int j = 0; j < sssp::kMaxStages; ++j) {
     if (j < P) {
-      const cd bb = (double(L) / 2.0) * (1.0 - p->pade.a[j] / p->pade.b[j]);
+      const cd bb = (1.0 / scale) * (1.0 - p->pade.a[j] / p->pade.b[j]);
       p->beta[j] = make_float2(float(bb.real()), float(bb.imag()));
     } else {
       p->beta[j] = make_float2(0, 0);
@@ -529,10 +562,11 @@ pe_status pe_set_field(pe_plan* p, const float* u, int on_device, double r) {
   if (!std::isfinite(r)) return fail(p, PE_ERR_ARG, "r must be finite");
   PE_CUDA(p, cudaMemcpyAsync(p->dStage, u, sizeof(float2) * p->N,
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
-  PE_CUDA(p, launch_dst(p->log2L, p->dStage, p->dYhat, 1.0f, p->tabs, p->stream, p->dWork));
-  // the physical field as given (index 0 = boundary)
-  PE_CUDA(p, cudaMemsetAsync(p->dField, 0, sizeof(float2), p->stream));
-  PE_CUDA(p, cudaMemcpyAsync(p->dField + 1, p->dStage, sizeof(float2) * p->N, cudaMemcpyDeviceToDevice, p->stream));
+  PE_CUDA(p, launch_dst(p->log2L, p->dStage, p->dYhat, 1.0f, p->tabs, p->stream, p->dWork, p->bc));
+  // the physical field as given (Dirichlet: index 0 = boundary)
+  if (p->off) PE_CUDA(p, cudaMemsetAsync(p->dField, 0, sizeof(float2), p->stream));
+  PE_CUDA(p, cudaMemcpyAsync(p->dField + p->off, p->dStage, sizeof(float2) * p->N, cudaMemcpyDeviceToDevice,
+                             p->stream));
   PE_CUDA(p, cudaMemsetAsync(p->dStatus, 0, sizeof(int), p->stream));
   if (!on_device) PE_CUDA(p, cudaStreamSynchronize(p->stream));
   p->r_set = r;
@@ -572,13 +606,13 @@ static pe_status append_nodes(pe_plan* p, const double* n2, const double* ranges
   std::vector<float> host(size_t(count) * p->L), hosti;
   if (p->complex_profile) hosti.assign(size_t(count) * p->L, 0.f);
   for (int i = 0; i < count; ++i) {
-    host[size_t(i) * p->L] = 0.0f;
+    host[size_t(i) * p->L] = 0.0f;  // Dirichlet boundary (overwritten by data on periodic grids)
     for (int n = 0; n < p->N; ++n) {
       const double re = is_complex ? s[size_t(i) * per + 2 * n] : s[size_t(i) * per + n];
       const double im = is_complex ? s[size_t(i) * per + 2 * n + 1] : 0.0;
       if (!std::isfinite(re) || !std::isfinite(im)) return fail(p, PE_ERR_ARG, "n2 must be finite");
-      host[size_t(i) * p->L + n + 1] = float(re - 1.0);
-      if (p->complex_profile) hosti[size_t(i) * p->L + n + 1] = float(im);
+      host[size_t(i) * p->L + n + p->off] = float(re - 1.0);
+      if (p->complex_profile) hosti[size_t(i) * p->L + n + p->off] = float(im);
     }
   }
   PE_CUDA(p, cudaMemcpyAsync(p->dV + size_t(p->nodes) * p->L, host.data(), sizeof(float) * host.size(),
@@ -622,7 +656,7 @@ pe_status pe_march(pe_plan* p, int steps) {
   if (st != PE_OK) return st;
   if (steps == 0) return PE_OK;
   PE_CUDA(p, cudaMemcpyAsync(p->dDesc, &d, sizeof(d), cudaMemcpyHostToDevice, p->stream));
-  PE_CUDA(p, launch_march(p->log2L, p->dDesc, 1, p->tabs, p->stream, d.Vi != nullptr));
+  PE_CUDA(p, launch_march(p->log2L, p->dDesc, 1, p->tabs, p->stream, d.Vi != nullptr, p->bc));
   return PE_OK;
 }
 
@@ -638,8 +672,8 @@ pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
   }
   // group by (size, complex profile), one launch per group; every CTA marches its own plan its
   // own step count
-  std::map<std::pair<int, bool>, std::vector<SolveDesc>> groups;
-  std::map<std::pair<int, bool>, TransformTables> tabs;
+  std::map<std::tuple<int, bool, int>, std::vector<SolveDesc>> groups;
+  std::map<std::tuple<int, bool, int>, TransformTables> tabs;
   for (int i = 0; i < count; ++i) {
     if (steps[i] == 0) continue;
     SolveDesc d;
@@ -648,7 +682,7 @@ pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
       p0->err = plans[i]->err;
       return st;
     }
-    const auto key = std::make_pair(plans[i]->log2L, d.Vi != nullptr);
+    const auto key = std::make_tuple(plans[i]->log2L, d.Vi != nullptr, plans[i]->bc);
     groups[key].push_back(d);
     tabs[key] = plans[i]->tabs;
   }
@@ -657,7 +691,8 @@ pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
     const size_t bytes = sizeof(SolveDesc) * kv.second.size();
     PE_CUDA(p0, cudaMallocAsync(reinterpret_cast<void**>(&dd), bytes, p0->stream));
     PE_CUDA(p0, cudaMemcpyAsync(dd, kv.second.data(), bytes, cudaMemcpyHostToDevice, p0->stream));
-    PE_CUDA(p0, launch_march(kv.first.first, dd, int(kv.second.size()), tabs[kv.first], p0->stream, kv.first.second));
+    PE_CUDA(p0, launch_march(std::get<0>(kv.first), dd, int(kv.second.size()), tabs[kv.first], p0->stream,
+                             std::get<1>(kv.first), std::get<2>(kv.first)));
     PE_CUDA(p0, cudaFreeAsync(dd, p0->stream));
   }
   return PE_OK;
@@ -695,7 +730,7 @@ pe_status pe_read_field(pe_plan* p, float* out, int to_device) {
   const double phase = std::fmod(p->k0 * p->dr * double(p->steps_done), 2.0 * M_PI);
   const float c = float(std::cos(phase)), s = float(std::sin(phase));
   float2* dst = to_device ? reinterpret_cast<float2*>(out) : p->dStage;
-  carrier_kernel<<<(p->N + 255) / 256, 256, 0, p->stream>>>(p->dField, dst, c, s, p->N);
+  carrier_kernel<<<(p->N + 255) / 256, 256, 0, p->stream>>>(p->dField, dst, c, s, p->N, p->off);
   PE_CUDA(p, cudaGetLastError());
   if (!to_device)
     PE_CUDA(p, cudaMemcpyAsync(out, p->dStage, sizeof(float2) * p->N, cudaMemcpyDeviceToHost, p->stream));
@@ -729,8 +764,8 @@ pe_status pe_dst1(pe_plan* p, const float* in, float* out, int on_device) {
   PE_CUDA(p, cudaMallocAsync(reinterpret_cast<void**>(&res), sizeof(float2) * p->L, p->stream));
   PE_CUDA(p, cudaMemcpyAsync(tmp, in, sizeof(float2) * p->N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                              p->stream));
-  PE_CUDA(p, launch_dst(p->log2L, tmp, res, 1.0f, p->tabs, p->stream, p->dWork));
-  PE_CUDA(p, cudaMemcpyAsync(out, res + 1, sizeof(float2) * p->N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+  PE_CUDA(p, launch_dst(p->log2L, tmp, res, 1.0f, p->tabs, p->stream, p->dWork, p->bc));
+  PE_CUDA(p, cudaMemcpyAsync(out, res + p->off, sizeof(float2) * p->N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                              p->stream));
   PE_CUDA(p, cudaFreeAsync(res, p->stream));
   if (!on_device) PE_CUDA(p, cudaStreamSynchronize(p->stream));
@@ -749,8 +784,8 @@ pe_status pe_dst1_batch(pe_plan* p, const float* in, float* out, int count) {
     PE_CUDA(p, cudaMallocAsync(reinterpret_cast<void**>(&work),
                                sizeof(float2) * sssp::large_work_elems(p->L) * size_t(count), p->stream));
   PE_CUDA(p, launch_dst_batch(p->log2L, reinterpret_cast<const float2*>(in), res, p->tabs, p->stream, work, count,
-                              p->N, p->L));
-  PE_CUDA(p, cudaMemcpy2DAsync(out, sizeof(float2) * p->N, res + 1, sizeof(float2) * p->L, sizeof(float2) * p->N,
+                              p->N, p->L, p->bc));
+  PE_CUDA(p, cudaMemcpy2DAsync(out, sizeof(float2) * p->N, res + p->off, sizeof(float2) * p->L, sizeof(float2) * p->N,
                                count, cudaMemcpyDeviceToDevice, p->stream));
   PE_CUDA(p, cudaFreeAsync(res, p->stream));
   if (work) PE_CUDA(p, cudaFreeAsync(work, p->stream));

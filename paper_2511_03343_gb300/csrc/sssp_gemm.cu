@@ -286,7 +286,7 @@ pe_status pe_gemm_batch_create(pe_gemm_batch** out, pe_plan** plans, int count, 
       if (p0) p0->err = "GEMM batch: plans must share N, Pade order, term count and dr";
       return PE_ERR_ARG;
     }
-    if (!p->field_set || p->terms < 2 || p->nodes != 1 || p->complex_profile) {
+    if (!p->field_set || p->terms < 2 || p->nodes != 1 || p->complex_profile || p->bc != PE_BC_DIRICHLET) {
       p0->err = "GEMM batch: every plan needs a field, one real profile node and neumann_terms >= 2";
       return PE_ERR_STATE;
     }

@@ -113,6 +113,7 @@ class Solve:
     u0: Optional[np.ndarray] = None
     profiles: List = dataclasses.field(default_factory=list)
     r0: float = 0.0
+    bc: str = "dirichlet"
 
     @property
     def k0(self) -> float:
@@ -120,7 +121,7 @@ class Solve:
 
     @property
     def z(self) -> np.ndarray:
-        return depth_grid(self.N, self.H)
+        return depth_grid(self.N, self.H, self.bc)
 
 
 def _with_starter(s: Solve) -> Solve:
@@ -129,17 +130,18 @@ def _with_starter(s: Solve) -> Solve:
 
 
 def isovelocity(N: int = 255, H: float = 100.0, freq: float = 100.0, dr: float = 5.0, steps: int = 1000,
-                pade_order: int = 4, zs: float = 50.0) -> Solve:
-    """Isovelocity Dirichlet waveguide, n^2 = 1 (V = 0), no Neumann terms."""
-    s = Solve("isovelocity", N, H, freq, dr, steps, pade_order, 0, 1e-10, zs)
+                pade_order: int = 4, zs: float = 50.0, bc: str = "dirichlet") -> Solve:
+    """Isovelocity waveguide, n^2 = 1 (V = 0), no Neumann terms (Dirichlet unless ``bc``)."""
+    s = Solve("isovelocity", N, H, freq, dr, steps, pade_order, 0, 1e-10, zs, bc=bc)
     s.profiles = [(0.0, np.ones(N))]
     return _with_starter(s)
 
 
 def munk(N: int = 4095, H: float = 5000.0, freq: float = 50.0, dr: float = 50.0, steps: int = 2000,
-         pade_order: int = 6, neumann_terms: int = 12, neumann_tol: float = 1e-10, zs: float = 1000.0) -> Solve:
-    """Range-independent Munk deep-ocean guide."""
-    s = Solve("munk", N, H, freq, dr, steps, pade_order, neumann_terms, neumann_tol, zs)
+         pade_order: int = 6, neumann_terms: int = 12, neumann_tol: float = 1e-10, zs: float = 1000.0,
+         bc: str = "dirichlet") -> Solve:
+    """Range-independent Munk deep-ocean guide (grid of the boundary condition ``bc``)."""
+    s = Solve("munk", N, H, freq, dr, steps, pade_order, neumann_terms, neumann_tol, zs, bc=bc)
     s.profiles = [(0.0, n2_from_c(munk_c(s.z), s.c0))]
     return _with_starter(s)
 

@@ -45,6 +45,7 @@ _SIGNATURES = {
     "pe_create_error": (ctypes.c_char_p, []),
     "pe_last_error": (ctypes.c_char_p, [_vp]),
     "pe_plan_create": (_i, [ctypes.POINTER(_vp), _i, _d, _d, _d, _i, _i, _d, _vp]),
+    "pe_plan_create_bc": (_i, [ctypes.POINTER(_vp), _i, _d, _d, _d, _i, _i, _d, _i, _vp]),
     "pe_plan_destroy": (None, [_vp]),
     "pe_set_output": (_i, [_vp, _i]),
     "pe_set_field": (_i, [_vp, _vp, _i, _d]),
@@ -148,13 +149,16 @@ def pade_coefficients(sigma: float, p: int):
 class Plan:
     """One range-march problem on the GPU (pe_plan)."""
 
+    BCS = {"dirichlet": 0, "periodic": 1}
+
     def __init__(self, N: int, H: float, k0: float, dr: float, pade_order: int, neumann_terms: int = 0,
-                 neumann_tol: float = 1e-10, stream=None):
+                 neumann_tol: float = 1e-10, stream=None, bc: str = "dirichlet"):
         L = lib()
         ptr = _vp()
         s = _stream_ptr(stream)
-        _check(L.pe_plan_create(ctypes.byref(ptr), int(N), float(H), float(k0), float(dr), int(pade_order),
-                                int(neumann_terms), float(neumann_tol), s))
+        _check(L.pe_plan_create_bc(ctypes.byref(ptr), int(N), float(H), float(k0), float(dr), int(pade_order),
+                                   int(neumann_terms), float(neumann_tol), self.BCS[bc], s))
+        self.bc = bc
         self._p = ptr
         self.N = int(N)
         self.H, self.k0, self.dr = float(H), float(k0), float(dr)
@@ -426,7 +430,7 @@ def march_batch(plans: List[Plan], steps: int):
 def plan_for(solve, stream=None, tl_every: int = 0) -> Plan:
     """Plan, starter field and profile nodes for an ``inputs.Solve`` description."""
     pl = Plan(solve.N, solve.H, solve.k0, solve.dr, solve.pade_order, solve.neumann_terms, solve.neumann_tol,
-              stream=stream)
+              stream=stream, bc=getattr(solve, "bc", "dirichlet"))
     pl.set_output(tl_every)
     if solve.neumann_terms > 1:
         pl.set_profile_nodes(solve.profiles)

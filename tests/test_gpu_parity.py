@@ -36,7 +36,7 @@ def _oracle(s, steps=None, tl_every=1, form="product"):
     but a series cut short by the term limit (few terms, or a slowly converging low-frequency
     case) is a different approximation in each form, so by default the GPU is compared with
     the oracle's product form; converged workloads are also compared with the sum form."""
-    g = O.Grid(N=s.N, H=s.H, k0=s.k0, dr=s.dr)
+    g = O.Grid(N=s.N, H=s.H, k0=s.k0, dr=s.dr, bc=getattr(s, "bc", "dirichlet"))
     return O.march(s.u0, s.profiles, g, s.pade_order, steps or s.steps, s.neumann_terms, s.neumann_tol,
                    r0=s.r0, tl_every=tl_every, form=form)
 
@@ -443,3 +443,41 @@ def test_absorbing_layer(sssp, N):
     ref = _oracle(s)
     _compare(u, tl, ref)
     assert np.linalg.norm(u) < 0.999 * np.linalg.norm(s.u0)
+
+
+# ----------------------------------------------------------------------------- periodic boundaries
+@pytest.mark.parametrize("N", [8, 64, 256, 4096])
+def test_dft_periodic_plan(sssp, N):
+    """A periodic plan's transform is the DFT (Section 3's Fourier inversion)."""
+    rng = np.random.default_rng(N + 5)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    pl = sssp.Plan(N, 100.0, 0.4, 5.0, 4, bc="periodic")
+    X = pl.dst1(x.astype(np.complex64))
+    ref = O.dft(x)
+    assert np.max(np.abs(X - ref)) / np.max(np.abs(ref)) < 2e-6 * math.log2(N)
+    pl.close()
+
+
+def test_periodic_isovelocity_and_mode(sssp):
+    """Periodic isovelocity march (N = 256, 1000 steps) vs the oracle, and a single Fourier mode
+    e^{2 pi i 7 z/H} at N = 4096 against its closed form."""
+    s = inputs.isovelocity(N=256, bc="periodic")
+    u, tl, _, _ = _gpu(sssp, s)
+    _compare(u, tl, _oracle(s))
+    s = inputs.isovelocity(N=4096, H=1000.0, freq=150.0, dr=10.0, steps=200, pade_order=6, bc="periodic")
+    s.u0 = np.exp(2j * np.pi * 7 * s.z / s.H)
+    pl = sssp.plan_for(s)
+    pl.march(s.steps)
+    u = pl.read_field()
+    pl.close()
+    plan = O.pade_plan(s.k0 * s.dr, 6)
+    G = np.exp(1j * s.k0 * s.dr) * plan.rational(-(2 * np.pi * 7 / (s.k0 * s.H)) ** 2)
+    assert np.linalg.norm(u - G ** s.steps * s.u0) / np.linalg.norm(s.u0) < 1e-5
+
+
+@pytest.mark.parametrize("N", [512, 4096])
+def test_periodic_munk(sssp, N):
+    """Munk profile on a periodic grid with the Neumann series, vs the oracle's periodic march."""
+    s = inputs.munk(N=N, freq=50.0 if N > 1000 else 30.0, dr=50.0, steps=60 if N < 4096 else 20, bc="periodic")
+    u, tl, _, _ = _gpu(sssp, s)
+    _compare(u, tl, _oracle(s))
