@@ -185,14 +185,20 @@ def idst1(X: np.ndarray) -> np.ndarray:
     return (2.0 / (X.shape[0] + 1)) * dst1(X)
 
 
+_DFT_CACHE = {}
+_DCT_CACHE = {}
+
+
 def dft(x: np.ndarray) -> np.ndarray:
     """DFT along axis 0 (periodic boundaries, Section 3): X_m = sum_{n=0..N-1} x_n e^{-2 pi i n m/N},
-    by the explicit sum (argument reduced exactly mod N)."""
+    by the explicit sum (argument reduced exactly mod N; the matrix is kept for the last N)."""
     x = np.asarray(x)
     N = x.shape[0]
-    idx = np.arange(N, dtype=np.int64)
-    F = np.exp(-2j * np.pi * (np.outer(idx, idx) % N).astype(np.float64) / N)
-    return F @ x
+    if N not in _DFT_CACHE:
+        idx = np.arange(N, dtype=np.int64)
+        _DFT_CACHE.clear()
+        _DFT_CACHE[N] = np.exp(-2j * np.pi * (np.outer(idx, idx) % N).astype(np.float64) / N)
+    return _DFT_CACHE[N] @ x
 
 
 def idft(X: np.ndarray) -> np.ndarray:
@@ -205,12 +211,15 @@ def dct1(x: np.ndarray) -> np.ndarray:
     z_0 = 0 and z_{N-1} = H: C_m = x_0/2 + (-1)^m x_{N-1}/2 + sum_{n=1..N-2} x_n cos(pi n m/(N-1))."""
     x = np.asarray(x)
     N = x.shape[0]
-    K = N - 1
-    idx = np.arange(N, dtype=np.int64)
-    C = np.cos(np.pi * (np.outer(idx, idx) % (2 * K)).astype(np.float64) / K)
-    C[:, 0] *= 0.5
-    C[:, -1] *= 0.5
-    return C @ x
+    if N not in _DCT_CACHE:
+        K = N - 1
+        idx = np.arange(N, dtype=np.int64)
+        C = np.cos(np.pi * (np.outer(idx, idx) % (2 * K)).astype(np.float64) / K)
+        C[:, 0] *= 0.5
+        C[:, -1] *= 0.5
+        _DCT_CACHE.clear()
+        _DCT_CACHE[N] = C
+    return _DCT_CACHE[N] @ x
 
 
 def idct1(C: np.ndarray) -> np.ndarray:
