@@ -421,3 +421,13 @@ def exact_propagator(X: np.ndarray, sigma: float) -> np.ndarray:
     ev, Q = np.linalg.eigh(X)
     root = np.sqrt((1.0 + ev).astype(np.complex128))
     return (Q * np.exp(1j * sigma * root)[None, :]) @ Q.conj().T
+
+
+def modal_field(u0: np.ndarray, grid: Grid, n2: np.ndarray, r: float) -> np.ndarray:
+    """Normal-mode (exact one-way) field at range r for a range-independent n^2 (the reference of
+    Section 4.1, Figs. 1-2): with the eigenpairs (mu_m, Psi_m) of the Hermitian X, the modes of
+    d_z^2 + k^2 have kappa_m = k0 sqrt(1 + mu_m), and u(r) = sum_m <Psi_m, u0> e^{i kappa_m r} Psi_m."""
+    X = dense_X(grid, np.asarray(n2) - 1.0)
+    mu, Q = np.linalg.eigh(X)
+    kappa = grid.k0 * np.sqrt((1.0 + mu).astype(np.complex128))
+    return Q @ (np.exp(1j * kappa * r) * (Q.conj().T @ u0))

@@ -89,6 +89,38 @@ def greene_starter(z: np.ndarray, k0: float, zs: float) -> np.ndarray:
     return (math.sqrt(k0) * (1.4467 - 0.4201 * s2) * np.exp(-s2 / 3.0512)).astype(np.complex128)
 
 
+def modal_starter(z: np.ndarray, H: float, c: np.ndarray, freq: float, zs: float, c0: float = C0_DEFAULT,
+                  max_angle_deg: float = 90.0) -> np.ndarray:
+    """Normal-mode starter of Section 3.2: u(r0, z) = sqrt(2 pi) sum_m Psi_m(zs) Psi_m(z) / sqrt(kappa_m)
+    over the propagating modes of the Sturm-Liouville problem Psi'' + (k^2(z) - kappa^2) Psi = 0 with
+    Psi(0) = Psi(H) = 0 (the printed "+ kappa^2" read as "- kappa^2"), k = 2 pi f / c(z).
+
+    The modes come from a second-order finite-difference discretisation on the interior grid ``z``
+    (a starter generator of its own, independent of the marcher's spectral operator), normalised so
+    that sum_n Psi_m(z_n)^2 dz = 1; Psi_m(zs) is linearly interpolated.  Only modes whose grazing
+    angle acos(kappa_m / k0) is below ``max_angle_deg`` are kept (k0 = 2 pi f / c0).
+    """
+    from scipy.linalg import eigh_tridiagonal
+    z = np.asarray(z, dtype=np.float64)
+    N = z.size
+    dz = H / (N + 1)
+    k2 = (2.0 * math.pi * freq / np.asarray(c, dtype=np.float64)) ** 2
+    k0 = 2.0 * math.pi * freq / c0
+    diag = -2.0 / dz ** 2 + k2
+    off = np.full(N - 1, 1.0 / dz ** 2)
+    kap2, psi = eigh_tridiagonal(diag, off)
+    psi = psi / math.sqrt(dz)
+    cos_max = math.cos(math.radians(max_angle_deg))
+    keep = kap2 > (k0 * cos_max) ** 2 if max_angle_deg < 90.0 else kap2 > 0
+    u = np.zeros(N, dtype=np.complex128)
+    zz = np.concatenate([[0.0], z, [H]])
+    for m in np.nonzero(keep)[0]:
+        col = np.concatenate([[0.0], psi[:, m], [0.0]])
+        psi_s = np.interp(zs, zz, col)
+        u += psi_s * psi[:, m] / math.sqrt(math.sqrt(kap2[m]))
+    return math.sqrt(2.0 * math.pi) * u
+
+
 # ----------------------------------------------------------------------------
 # workload descriptions
 # ----------------------------------------------------------------------------

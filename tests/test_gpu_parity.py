@@ -481,3 +481,20 @@ def test_periodic_munk(sssp, N):
     s = inputs.munk(N=N, freq=50.0 if N > 1000 else 30.0, dr=50.0, steps=60 if N < 4096 else 20, bc="periodic")
     u, tl, _, _ = _gpu(sssp, s)
     _compare(u, tl, _oracle(s))
+
+
+# ----------------------------------------------------------------------------- physics beyond parity
+def test_modal_starter_against_normal_modes(sssp):
+    """Range-independent Munk (N = 1023, 50 Hz, [6/6], dr = 50 m, 100 steps) from the paper's
+    normal-mode starter (modes within 30 degrees of horizontal): the GPU march agrees with the
+    normal-mode (exact one-way) field, the reference of Section 4.1, within the Pade and FP32
+    errors, and with the oracle march."""
+    s = inputs.munk(N=1023, freq=50.0, dr=50.0, steps=100)
+    z = s.z
+    s.u0 = inputs.modal_starter(z, s.H, inputs.munk_c(z), s.freq, s.zs, max_angle_deg=30.0)
+    u, tl, _, _ = _gpu(sssp, s)
+    ref = _oracle(s)
+    _compare(u, tl, ref)
+    g = O.Grid(N=s.N, H=s.H, k0=s.k0, dr=s.dr)
+    modes = O.modal_field(s.u0, g, s.profiles[0][1], s.steps * s.dr)
+    assert np.linalg.norm(u - modes) / np.linalg.norm(modes) < 2e-5

@@ -524,3 +524,36 @@ def test_norm_conservation_other_bc(bc, N):
         w[0] = w[-1] = 0.5
     nrm = lambda u: math.sqrt(np.sum(w * np.abs(u) ** 2))
     assert abs(nrm(res.u) / nrm(u0) - 1) < 1e-9
+
+
+def test_modal_field_is_exact_propagator():
+    """The normal-mode field after n steps equals the n-th power of exp(i sigma sqrt(I + X))."""
+    g = O.Grid(N=31, H=100.0, k0=2 * math.pi * 100 / 1500.0, dr=5.0)
+    z = inputs.depth_grid(31, g.H)
+    n2 = 1.0 + 0.01 * np.cos(2 * np.pi * z / g.H)
+    u0 = _rng_field(31, 51)
+    P = O.exact_propagator(O.dense_X(g, n2 - 1.0), g.sigma)
+    ref = np.linalg.matrix_power(P, 7) @ u0
+    assert np.max(np.abs(O.modal_field(u0, g, n2, 7 * g.dr) - ref)) < 1e-12
+
+
+def test_modal_starter_isovelocity_closed_form():
+    """Isovelocity guide: the finite-difference modes are sin(pi m z/H) with
+    kappa_m^2 = k^2 - (2/dz)^2 sin^2(pi m dz/(2H)); the starter is sqrt(2 pi) sum over them."""
+    N, H, f, zs = 127, 100.0, 100.0, 37.0
+    z = inputs.depth_grid(N, H)
+    c = np.full(N, 1500.0)
+    u = inputs.modal_starter(z, H, c, f, zs)
+    dz = H / (N + 1)
+    k = 2 * math.pi * f / 1500.0
+    ref = np.zeros(N)
+    zz = np.concatenate([[0.0], z, [H]])
+    for m in range(1, N + 1):
+        kap2 = k * k - (2 / dz) ** 2 * math.sin(math.pi * m * dz / (2 * H)) ** 2
+        if kap2 <= 0:
+            continue
+        psi = np.sin(np.pi * m * z / H) * math.sqrt(2.0 / H)
+        psi_s = np.interp(zs, zz, np.concatenate([[0.0], psi, [0.0]]))
+        ref += psi_s * psi / kap2 ** 0.25
+    ref *= math.sqrt(2 * math.pi)
+    assert np.max(np.abs(u - ref)) / np.max(np.abs(ref)) < 1e-9
