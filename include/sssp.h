@@ -73,11 +73,17 @@ pe_status pe_plan_create(pe_plan** out, int N, double H, double k0, double dr, i
 
 /*
  * Boundary conditions of Section 3.1: homogeneous Dirichlet (the DST-I, pe_plan_create's
- * default) or periodic (the DFT; N grid points z_n = n H/N, n = 0..N-1, N a power of two in
- * [8, 4096]; eigenvalues -(2 pi l/(k0 H))^2 for the signed frequency l).  For a periodic plan
- * every "DST-I" of this header is the DFT, N values in and out.
+ * default); periodic (the DFT; N grid points z_n = n H/N, n = 0..N-1, N a power of two in
+ * [8, 4096]; eigenvalues -(2 pi l/(k0 H))^2 for the signed frequency l); homogeneous Neumann
+ * (the DCT-I; N points z_n = n H/(N-1), n = 0..N-1 including both boundaries, N - 1 a power of
+ * two in [4, 2048]; eigenvalues -(pi m/(k0 H))^2).  A Neumann plan marches the periodic
+ * problem on [0, 2H] of the even extension of the field (an exact equivalence: d_z^2 + V
+ * commutes with the reflection) and returns the N points of [0, H].  For a periodic plan
+ * every "DST-I" of this header is the DFT; for a Neumann plan it is the DCT-I
+ * C_m = x_0/2 + (-1)^m x_{N-1}/2 + sum_{n=1..N-2} x_n cos(pi n m/(N-1)); N values in and out.
+ * pe_dst1_batch and the GEMM batch take Dirichlet plans only.
  */
-enum { PE_BC_DIRICHLET = 0, PE_BC_PERIODIC = 1 };
+enum { PE_BC_DIRICHLET = 0, PE_BC_PERIODIC = 1, PE_BC_NEUMANN = 2 };
 pe_status pe_plan_create_bc(pe_plan** out, int N, double H, double k0, double dr, int pade_order, int neumann_terms,
                             double neumann_tol, int bc, void* cuda_stream);
 

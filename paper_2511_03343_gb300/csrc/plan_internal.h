@@ -16,7 +16,10 @@ struct TransformTables {
 
 struct pe_plan {
   int N = 0, L = 0, log2L = 0, p = 0, terms = 0, device = 0;
-  int bc = 0;   // PE_BC_DIRICHLET or PE_BC_PERIODIC
+  int bc = 0;   // transform the kernels run: PE_BC_DIRICHLET or PE_BC_PERIODIC
+  int user_bc = 0;  // the caller's boundary condition (PE_BC_NEUMANN runs as a periodic plan on
+                    // the even extension of the field to [0, 2H])
+  int N_user = 0;   // grid points the caller sees
   int off = 1;  // index of the first stored depth point in the length-L arrays
   double H = 0, k0 = 0, dr = 0, tol = 0;
   cudaStream_t stream = nullptr;

@@ -232,6 +232,12 @@ cudaError_t launch_dst_batch(int log2L, const float2* in, float2* out, const Tra
   return cudaErrorInvalidValue;
 }
 
+// even extension in place: buf[2K - n] = buf[n], n = 1..K-1 (Neumann plans)
+__global__ void even_extend_kernel(float2* buf, int K) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  if (n < K) buf[2 * K - n] = buf[n];
+}
+
 __global__ void carrier_kernel(const float2* __restrict__ field, float2* __restrict__ out, float c, float s, int N,
                                int off) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -428,9 +434,20 @@ pe_status pe_plan_create_bc(pe_plan** out, int N, double H, double k0, double dr
     return PE_ERR_ARG;
   }
   *out = nullptr;
-  if (bc != PE_BC_DIRICHLET && bc != PE_BC_PERIODIC) {
-    g_create_error = "bc must be PE_BC_DIRICHLET or PE_BC_PERIODIC";
+  if (bc != PE_BC_DIRICHLET && bc != PE_BC_PERIODIC && bc != PE_BC_NEUMANN) {
+    g_create_error = "bc must be PE_BC_DIRICHLET, PE_BC_PERIODIC or PE_BC_NEUMANN";
     return PE_ERR_ARG;
+  }
+  const int user_bc = bc, N_user = N;
+  if (bc == PE_BC_NEUMANN) {
+    // the even extension to [0, 2H]: 2(N-1) periodic points
+    if (N < 5 || ilog2_exact(N - 1) < 2 || 2 * (N - 1) > (1 << kMaxSmemLog2)) {
+      g_create_error = "Neumann grids: N - 1 must be a power of two in [4, 2048]";
+      return PE_ERR_ARG;
+    }
+    N = 2 * (N - 1);
+    H = 2.0 * H;
+    bc = PE_BC_PERIODIC;
   }
   const int log2L = ilog2_exact(bc == PE_BC_PERIODIC ? N : N + 1);
   if (bc == PE_BC_DIRICHLET && (N < 1 || log2L < kMinLog2 || log2L > kMaxLog2)) {
@@ -459,6 +476,8 @@ pe_status pe_plan_create_bc(pe_plan** out, int N, double H, double k0, double dr
   p->log2L = log2L;
   p->bc = bc;
   p->off = (bc == PE_BC_PERIODIC) ? 0 : 1;
+  p->user_bc = user_bc;
+  p->N_user = N_user;
   p->p = pade_order;
   p->terms = neumann_terms;
   p->H = H;
@@ -560,8 +579,13 @@ pe_status pe_set_field(pe_plan* p, const float* u, int on_device, double r) {
   if (!p) return PE_ERR_ARG;
   if (!u) return fail(p, PE_ERR_ARG, "u is NULL");
   if (!std::isfinite(r)) return fail(p, PE_ERR_ARG, "r must be finite");
-  PE_CUDA(p, cudaMemcpyAsync(p->dStage, u, sizeof(float2) * p->N,
+  PE_CUDA(p, cudaMemcpyAsync(p->dStage, u, sizeof(float2) * p->N_user,
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
+  if (p->user_bc == PE_BC_NEUMANN) {
+    const int K = p->N / 2;
+    even_extend_kernel<<<(K + 255) / 256, 256, 0, p->stream>>>(p->dStage, K);
+    PE_CUDA(p, cudaGetLastError());
+  }
   PE_CUDA(p, launch_dst(p->log2L, p->dStage, p->dYhat, 1.0f, p->tabs, p->stream, p->dWork, p->bc));
   // the physical field as given (Dirichlet: index 0 = boundary)
   if (p->off) PE_CUDA(p, cudaMemsetAsync(p->dField, 0, sizeof(float2), p->stream));
@@ -593,7 +617,9 @@ static pe_status append_nodes(pe_plan* p, const double* n2, const double* ranges
   }
   pe_status st = ensure_node_cap(p, p->nodes + count);
   if (st != PE_OK) return st;
-  const size_t per = size_t(p->N) * (is_complex ? 2 : 1);
+  const size_t per = size_t(p->N_user) * (is_complex ? 2 : 1);
+  const bool neumann = (p->user_bc == PE_BC_NEUMANN);
+  const int K = p->N / 2;
   std::vector<double> src;
   const double* s = n2;
   if (on_device) {
@@ -608,8 +634,9 @@ static pe_status append_nodes(pe_plan* p, const double* n2, const double* ranges
   for (int i = 0; i < count; ++i) {
     host[size_t(i) * p->L] = 0.0f;  // Dirichlet boundary (overwritten by data on periodic grids)
     for (int n = 0; n < p->N; ++n) {
-      const double re = is_complex ? s[size_t(i) * per + 2 * n] : s[size_t(i) * per + n];
-      const double im = is_complex ? s[size_t(i) * per + 2 * n + 1] : 0.0;
+      const int q = (neumann && n > K) ? 2 * K - n : n;  // even extension for Neumann plans
+      const double re = is_complex ? s[size_t(i) * per + 2 * q] : s[size_t(i) * per + q];
+      const double im = is_complex ? s[size_t(i) * per + 2 * q + 1] : 0.0;
       if (!std::isfinite(re) || !std::isfinite(im)) return fail(p, PE_ERR_ARG, "n2 must be finite");
       host[size_t(i) * p->L + n + p->off] = float(re - 1.0);
       if (p->complex_profile) hosti[size_t(i) * p->L + n + p->off] = float(im);
@@ -729,21 +756,25 @@ pe_status pe_read_field(pe_plan* p, float* out, int to_device) {
   // carrier e^{i k0 (r - r_set)} in FP64 phase arithmetic (the marcher keeps the envelope)
   const double phase = std::fmod(p->k0 * p->dr * double(p->steps_done), 2.0 * M_PI);
   const float c = float(std::cos(phase)), s = float(std::sin(phase));
-  float2* dst = to_device ? reinterpret_cast<float2*>(out) : p->dStage;
+  const bool direct = to_device && p->N_user == p->N;
+  float2* dst = direct ? reinterpret_cast<float2*>(out) : p->dStage;
   carrier_kernel<<<(p->N + 255) / 256, 256, 0, p->stream>>>(p->dField, dst, c, s, p->N, p->off);
   PE_CUDA(p, cudaGetLastError());
-  if (!to_device)
-    PE_CUDA(p, cudaMemcpyAsync(out, p->dStage, sizeof(float2) * p->N, cudaMemcpyDeviceToHost, p->stream));
+  if (!direct)
+    PE_CUDA(p, cudaMemcpyAsync(out, p->dStage, sizeof(float2) * p->N_user,
+                               to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream));
   return check_status(p);
 }
 
 pe_status pe_read_TL(pe_plan* p, float* out, size_t cap, double* ranges, size_t* n_rows) {
   if (!p) return PE_ERR_ARG;
-  const size_t need = size_t(p->tl_rows) * p->N;
+  const size_t need = size_t(p->tl_rows) * p->N_user;
   if (n_rows) *n_rows = size_t(p->tl_rows);
   if (!out) return PE_OK;  // size query
   if (cap < need) return fail(p, PE_ERR_ARG, "TL buffer too small");
-  if (need > 0) PE_CUDA(p, cudaMemcpyAsync(out, p->dTL, sizeof(float) * need, cudaMemcpyDeviceToHost, p->stream));
+  if (need > 0)  // rows hold N values on the device; the caller gets the first N_user of each
+    PE_CUDA(p, cudaMemcpy2DAsync(out, sizeof(float) * p->N_user, p->dTL, sizeof(float) * p->N,
+                                 sizeof(float) * p->N_user, size_t(p->tl_rows), cudaMemcpyDeviceToHost, p->stream));
   if (ranges)
     for (size_t i = 0; i < p->tl_ranges.size(); ++i) ranges[i] = p->tl_ranges[i];
   return check_status(p);
@@ -762,11 +793,18 @@ pe_status pe_dst1(pe_plan* p, const float* in, float* out, int on_device) {
   float2* tmp = p->dStage;
   float2* res = nullptr;
   PE_CUDA(p, cudaMallocAsync(reinterpret_cast<void**>(&res), sizeof(float2) * p->L, p->stream));
-  PE_CUDA(p, cudaMemcpyAsync(tmp, in, sizeof(float2) * p->N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                             p->stream));
-  PE_CUDA(p, launch_dst(p->log2L, tmp, res, 1.0f, p->tabs, p->stream, p->dWork, p->bc));
-  PE_CUDA(p, cudaMemcpyAsync(out, res + p->off, sizeof(float2) * p->N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                             p->stream));
+  PE_CUDA(p, cudaMemcpyAsync(tmp, in, sizeof(float2) * p->N_user,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
+  float scale = 1.0f;
+  if (p->user_bc == PE_BC_NEUMANN) {  // DCT-I = half the DFT of the even extension
+    const int K = p->N / 2;
+    even_extend_kernel<<<(K + 255) / 256, 256, 0, p->stream>>>(tmp, K);
+    PE_CUDA(p, cudaGetLastError());
+    scale = 0.5f;
+  }
+  PE_CUDA(p, launch_dst(p->log2L, tmp, res, scale, p->tabs, p->stream, p->dWork, p->bc));
+  PE_CUDA(p, cudaMemcpyAsync(out, res + p->off, sizeof(float2) * p->N_user,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream));
   PE_CUDA(p, cudaFreeAsync(res, p->stream));
   if (!on_device) PE_CUDA(p, cudaStreamSynchronize(p->stream));
   return PE_OK;
@@ -775,6 +813,7 @@ pe_status pe_dst1(pe_plan* p, const float* in, float* out, int on_device) {
 pe_status pe_dst1_batch(pe_plan* p, const float* in, float* out, int count) {
   if (!p) return PE_ERR_ARG;
   if (!in || !out || count < 0) return fail(p, PE_ERR_ARG, "in/out NULL or count < 0");
+  if (p->user_bc == PE_BC_NEUMANN) return fail(p, PE_ERR_ARG, "pe_dst1_batch takes Dirichlet or periodic plans");
   if (count == 0) return PE_OK;
   // every field gets an L-long result row (index 0 is the zero mode), then rows 1..N are packed
   float2* res = nullptr;

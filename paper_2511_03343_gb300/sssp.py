@@ -149,7 +149,7 @@ def pade_coefficients(sigma: float, p: int):
 class Plan:
     """One range-march problem on the GPU (pe_plan)."""
 
-    BCS = {"dirichlet": 0, "periodic": 1}
+    BCS = {"dirichlet": 0, "periodic": 1, "neumann": 2}
 
     def __init__(self, N: int, H: float, k0: float, dr: float, pade_order: int, neumann_terms: int = 0,
                  neumann_tol: float = 1e-10, stream=None, bc: str = "dirichlet"):

@@ -498,3 +498,34 @@ def test_modal_starter_against_normal_modes(sssp):
     g = O.Grid(N=s.N, H=s.H, k0=s.k0, dr=s.dr)
     modes = O.modal_field(s.u0, g, s.profiles[0][1], s.steps * s.dr)
     assert np.linalg.norm(u - modes) / np.linalg.norm(modes) < 2e-5
+
+
+# ----------------------------------------------------------------------------- Neumann boundaries
+@pytest.mark.parametrize("N", [9, 65, 1025, 2049])
+def test_dct1_neumann_plan(sssp, N):
+    """A Neumann plan's transform is the DCT-I (computed on the GPU as half the DFT of the even
+    extension)."""
+    rng = np.random.default_rng(N + 9)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    pl = sssp.Plan(N, 100.0, 0.4, 5.0, 4, bc="neumann")
+    X = pl.dst1(x.astype(np.complex64))
+    ref = O.dct1(x)
+    assert np.max(np.abs(X - ref)) / np.max(np.abs(ref)) < 2e-6 * math.log2(2 * (N - 1))
+    pl.close()
+
+
+def test_neumann_mode_and_munk(sssp):
+    """Neumann boundaries: a single mode cos(pi 5 z/H) against its closed form, and a Munk march
+    (N = 1025, [6/6], Neumann series) against the oracle's DCT-I march."""
+    s = inputs.isovelocity(N=513, H=1000.0, freq=150.0, dr=10.0, steps=100, pade_order=6, bc="neumann")
+    s.u0 = np.cos(np.pi * 5 * s.z / s.H).astype(np.complex128)
+    pl = sssp.plan_for(s)
+    pl.march(s.steps)
+    u = pl.read_field()
+    pl.close()
+    plan = O.pade_plan(s.k0 * s.dr, 6)
+    G = np.exp(1j * s.k0 * s.dr) * plan.rational(-(np.pi * 5 / (s.k0 * s.H)) ** 2)
+    assert np.linalg.norm(u - G ** s.steps * s.u0) / np.linalg.norm(s.u0) < 1e-5
+    s = inputs.munk(N=1025, freq=60.0, dr=50.0, steps=40, bc="neumann")
+    u, tl, _, _ = _gpu(sssp, s)
+    _compare(u, tl, _oracle(s))
