@@ -227,6 +227,36 @@ pe_status pe_dst1_batch(pe_plan* plan, const float* in, float* out, int count);
  */
 pe_status pe_dst1_noalloc(const float* in, float* out, int N, void* cuda_stream);
 
+/*
+ * Checkpoint / resume of a march (bit-exact).  The state is the marcher's own variables: the
+ * unnormalised transform coefficients of the envelope and its depth-domain copy, L complex
+ * values each (L = N + 1 Dirichlet, N periodic, 2 (N - 1) Neumann), interleaved re/im, 4 L
+ * floats in all (pe_state_size gives the count), plus the range of the starter and the steps
+ * marched since.  Loading it into a plan of the same parameters (pe_load_state makes no check
+ * that they agree) and marching on gives the same bits as never stopping.  Host memory; both
+ * calls synchronise.  TL rows are not part of the state: a loaded plan records from its
+ * next step.
+ */
+size_t pe_state_size(const pe_plan* plan);
+pe_status pe_save_state(pe_plan* plan, float* state, double* r_set, long long* steps);
+pe_status pe_load_state(pe_plan* plan, const float* state, double r_set, long long steps);
+
+/*
+ * Host FP64 bound on the Neumann series of Eq. (Neumann) for profile node `node`:
+ * rho_j = max|V| max_m |b_j / (1 + b_j lambda_m)| for every Pade term j (the 2-norm of
+ * b_j L_j^{-1} V, since the transform is orthogonal).  rho < 1 guarantees convergence; the
+ * operator is not normal, so a bound above 1 is a warning, not a divergence (the march reports
+ * PE_ERR_NEUMANN_DIVERGED only on an actual blow-up).  rho: pade_order doubles.
+ */
+pe_status pe_neumann_bound(pe_plan* plan, int node, double* rho);
+
+/*
+ * Fault injection for tests of the error path (no GPU fault is involved): writes `status`
+ * (e.g. 4 = diverged, 7 = non-finite) into the plan's device status word with a copy, as a
+ * failing march would; the next pe_sync / pe_read_* reports it.
+ */
+pe_status pe_inject_status(pe_plan* plan, int status);
+
 /* Current range of the field and number of steps marched since pe_set_field. */
 pe_status pe_get_range(const pe_plan* plan, double* r, long long* steps);
 
@@ -296,6 +326,9 @@ pe_status pe_server_state(pe_server* server, unsigned long long id, int* state);
 pe_status pe_server_take(pe_server* server, unsigned long long id, float* field, float* tl, size_t tl_cap,
                          size_t* rows);
 pe_status pe_server_stats(pe_server* server, size_t* bytes_in_use, size_t* peak_bytes, int* peak_live);
+/* Withdraw a queued or running request (its plan is freed at once; state becomes 3, failed,
+ * with the message "cancelled").  PE_ERR_STATE if it already finished. */
+pe_status pe_server_cancel(pe_server* server, unsigned long long id);
 
 #ifdef __cplusplus
 }

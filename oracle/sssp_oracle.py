@@ -294,6 +294,18 @@ def neumann_w(u: np.ndarray, V: np.ndarray, b: np.ndarray, lam: np.ndarray, term
     return (w, counts) if return_counts else w
 
 
+def neumann_bound(V: np.ndarray, b: np.ndarray, lam: np.ndarray) -> np.ndarray:
+    """Per Pade term j, the bound rho_j = max_n |V_n| * max_m |b_j / (1 + b_j lambda_m)| on the
+    2-norm of the Neumann series' operator b_j L_j^{-1} V (Eq. Neumann): the transform of the
+    boundary condition is orthogonal up to scale, so ||L_j^{-1}||_2 = max_m 1/|1 + b_j lambda_m|,
+    and ||V||_2 = max |V| for the diagonal V.  rho_j < 1 makes the series converge geometrically.
+    Equality holds for a constant V.  For Neumann grids the DCT-I is orthogonal in the
+    trapezoid-weighted norm (weight 1/2 on the two boundary points), and the bound is in that norm."""
+    b = np.asarray(b, dtype=np.complex128)
+    vmax = np.max(np.abs(V))
+    return np.array([vmax * np.max(np.abs(bj / (1.0 + bj * lam))) for bj in b])
+
+
 @dataclasses.dataclass
 class Grid:
     """Depth grid: 'dirichlet' N interior points z_n = n H/(N+1), n = 1..N; 'periodic' N points

@@ -831,6 +831,71 @@ pe_status pe_dst1_batch(pe_plan* p, const float* in, float* out, int count) {
   return PE_OK;
 }
 
+size_t pe_state_size(const pe_plan* p) { return p ? 4 * size_t(p->L) : 0; }
+
+pe_status pe_save_state(pe_plan* p, float* state, double* r_set, long long* steps) {
+  if (!p || !state) return PE_ERR_ARG;
+  if (!p->field_set) return fail(p, PE_ERR_STATE, "no field set");
+  // spectral envelope, then its depth-domain copy (what pe_read_field reads)
+  PE_CUDA(p, cudaMemcpyAsync(state, p->dYhat, sizeof(float2) * p->L, cudaMemcpyDeviceToHost, p->stream));
+  PE_CUDA(p, cudaMemcpyAsync(state + 2 * size_t(p->L), p->dField, sizeof(float2) * p->L, cudaMemcpyDeviceToHost,
+                             p->stream));
+  if (r_set) *r_set = p->r_set;
+  if (steps) *steps = p->steps_done;
+  return check_status(p);
+}
+
+pe_status pe_load_state(pe_plan* p, const float* state, double r_set, long long steps) {
+  if (!p || !state) return PE_ERR_ARG;
+  if (steps < 0 || !std::isfinite(r_set)) return fail(p, PE_ERR_ARG, "steps must be >= 0 and r_set finite");
+  PE_CUDA(p, cudaMemcpyAsync(p->dYhat, state, sizeof(float2) * p->L, cudaMemcpyHostToDevice, p->stream));
+  PE_CUDA(p, cudaMemcpyAsync(p->dField, state + 2 * size_t(p->L), sizeof(float2) * p->L, cudaMemcpyHostToDevice,
+                             p->stream));
+  PE_CUDA(p, cudaMemsetAsync(p->dStatus, 0, sizeof(int), p->stream));
+  PE_CUDA(p, cudaStreamSynchronize(p->stream));
+  p->r_set = r_set;
+  p->steps_done = steps;
+  p->tl_rows = 0;
+  p->tl_ranges.clear();
+  p->field_set = true;
+  return PE_OK;
+}
+
+pe_status pe_neumann_bound(pe_plan* p, int node, double* rho) {
+  if (!p || !rho) return PE_ERR_ARG;
+  if (node < 0 || node >= p->nodes) return fail(p, PE_ERR_ARG, "no such profile node");
+  std::vector<float> v(p->L), vi;
+  PE_CUDA(p, cudaMemcpyAsync(v.data(), p->dV + size_t(node) * p->L, sizeof(float) * p->L, cudaMemcpyDeviceToHost,
+                             p->stream));
+  if (p->complex_profile) {
+    vi.resize(p->L);
+    PE_CUDA(p, cudaMemcpyAsync(vi.data(), p->dVi + size_t(node) * p->L, sizeof(float) * p->L, cudaMemcpyDeviceToHost,
+                               p->stream));
+  }
+  PE_CUDA(p, cudaStreamSynchronize(p->stream));
+  double vmax = 0.0;
+  for (int n = 0; n < p->L; ++n) vmax = std::max(vmax, std::hypot(double(v[n]), vi.empty() ? 0.0 : double(vi[n])));
+  const bool periodic = (p->bc == PE_BC_PERIODIC);
+  const double Hk = p->H;  // already the period 2H for Neumann plans
+  for (int j = 0; j < p->p; ++j) {
+    double mx = 0.0;
+    for (int m = (periodic ? 0 : 1); m < p->L; ++m) {
+      const double l = periodic ? double(m <= p->L / 2 ? m : m - p->L) : double(m);
+      const double x = (periodic ? 2.0 : 1.0) * M_PI * l / (p->k0 * Hk);
+      mx = std::max(mx, std::abs(p->pade.b[j] / (1.0 + p->pade.b[j] * (-x * x))));
+    }
+    rho[j] = vmax * mx;
+  }
+  return PE_OK;
+}
+
+pe_status pe_inject_status(pe_plan* p, int status) {
+  if (!p) return PE_ERR_ARG;
+  PE_CUDA(p, cudaMemcpyAsync(p->dStatus, &status, sizeof(int), cudaMemcpyHostToDevice, p->stream));
+  PE_CUDA(p, cudaStreamSynchronize(p->stream));
+  return PE_OK;
+}
+
 pe_status pe_get_range(const pe_plan* p, double* r, long long* steps) {
   if (!p) return PE_ERR_ARG;
   if (r) *r = p->r_set + double(p->steps_done) * p->dr;

@@ -226,6 +226,29 @@ pe_status pe_server_take(pe_server* s, unsigned long long id, float* field, floa
   return PE_OK;
 }
 
+pe_status pe_server_cancel(pe_server* s, unsigned long long id) {
+  if (!s) return PE_ERR_ARG;
+  auto it = s->results.find(id);
+  if (it == s->results.end()) return sfail(s, PE_ERR_ARG, "unknown request id");
+  if (it->second.state >= 2) return sfail(s, PE_ERR_STATE, "request already finished");
+  for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+    if ((*q)->id == id) {
+      s->queue.erase(q);
+      break;
+    }
+  for (auto l = s->live.begin(); l != s->live.end(); ++l)
+    if (l->req->id == id) {
+      pe_sync(l->plan);  // nothing of it may still run when its memory goes
+      pe_plan_destroy(l->plan);
+      s->in_use -= l->req->bytes;
+      s->live.erase(l);
+      break;
+    }
+  it->second.state = 3;
+  it->second.err = "cancelled";
+  return PE_OK;
+}
+
 pe_status pe_server_stats(pe_server* s, size_t* bytes_in_use, size_t* peak_bytes, int* peak_live) {
   if (!s) return PE_ERR_ARG;
   if (bytes_in_use) *bytes_in_use = s->in_use;

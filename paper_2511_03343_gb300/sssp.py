@@ -64,6 +64,12 @@ _SIGNATURES = {
     "pe_get_range": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
     "pe_pade_coefficients": (_i, [_d, _i, _vp, _vp, _vp]),
     "pe_march_batch_steps": (_i, [ctypes.POINTER(_vp), _vp, _i]),
+    "pe_state_size": (_sz, [_vp]),
+    "pe_save_state": (_i, [_vp, _vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
+    "pe_load_state": (_i, [_vp, _vp, _d, ctypes.c_longlong]),
+    "pe_neumann_bound": (_i, [_vp, _i, _vp]),
+    "pe_inject_status": (_i, [_vp, _i]),
+    "pe_server_cancel": (_i, [_vp, ctypes.c_ulonglong]),
     "pe_gemm_batch_create": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i]),
     "pe_gemm_batch_march": (_i, [_vp, _i]),
     "pe_gemm_batch_read_field": (_i, [_vp, _i, _vp]),
@@ -279,6 +285,26 @@ class Plan:
         self._c(lib().pe_get_range(self._p, ctypes.byref(r), ctypes.byref(s)))
         return r.value, s.value
 
+    def save_state(self):
+        """Bit-exact checkpoint: (spectral state, r_set, steps)."""
+        st = np.empty(int(lib().pe_state_size(self._p)) // 2, dtype=np.complex64)  # 2 L values
+        r = _d(0)
+        n = ctypes.c_longlong(0)
+        self._c(lib().pe_save_state(self._p, st.ctypes.data, ctypes.byref(r), ctypes.byref(n)))
+        return st, r.value, n.value
+
+    def load_state(self, state, r_set: float, steps: int):
+        st = np.ascontiguousarray(np.asarray(state, dtype=np.complex64))
+        self._c(lib().pe_load_state(self._p, st.ctypes.data, float(r_set), int(steps)))
+
+    def neumann_bound(self, node: int = 0) -> np.ndarray:
+        rho = np.zeros(self.pade_order)
+        self._c(lib().pe_neumann_bound(self._p, int(node), rho.ctypes.data))
+        return rho
+
+    def inject_status(self, status: int):
+        self._c(lib().pe_inject_status(self._p, int(status)))
+
     def dst1_batch(self, x, out):
         """count DST-I on device tensors x, out of shape (count, N), complex64."""
         assert x.is_cuda and out.is_cuda and x.shape == out.shape and x.shape[-1] == self.N
@@ -365,6 +391,9 @@ class Server:
                                      tl.ctypes.data if tl.size else None, tl.size, ctypes.byref(rows)))
         del self._keep[rid]
         return field, tl
+
+    def cancel(self, rid: int):
+        self._c(lib().pe_server_cancel(self._s, ctypes.c_ulonglong(rid)))
 
     def stats(self):
         a, b, c = _sz(0), _sz(0), _i(0)

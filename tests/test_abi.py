@@ -139,4 +139,12 @@ def test_server_submit_host_checks(L):
     bad.profiles = []
     with pytest.raises(sssp.PEError):
         srv.submit(bad)
+    # cancelling a queued request needs no GPU: it leaves the queue and reads as failed
+    rid2 = srv.submit(s, tl_every=1)
+    srv.cancel(rid2)
+    assert srv.state(rid2) == 3
+    with pytest.raises(sssp.PEError, match="cancelled"):
+        srv.take(rid2)
+    with pytest.raises(sssp.PEError):
+        srv.cancel(987654)                         # unknown id
     srv.close()

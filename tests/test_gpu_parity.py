@@ -529,3 +529,119 @@ def test_neumann_mode_and_munk(sssp):
     s = inputs.munk(N=1025, freq=60.0, dr=50.0, steps=40, bc="neumann")
     u, tl, _, _ = _gpu(sssp, s)
     _compare(u, tl, _oracle(s))
+
+
+# ----------------------------------------------------------------------------- checkpoint / resume
+@pytest.mark.parametrize("case", ["munk_dirichlet", "periodic", "neumann", "large"])
+def test_checkpoint_resume_bitwise(sssp, case):
+    """Saving the spectral state after k steps, loading it into a fresh plan and marching the
+    rest gives the same bits (field and the TL rows after the resume) as one uninterrupted march."""
+    if case == "munk_dirichlet":
+        s = inputs.munk(N=1023, freq=100.0, dr=25.0, steps=40)
+    elif case == "periodic":
+        s = inputs.munk(N=1024, freq=100.0, dr=25.0, steps=40, bc="periodic")
+    elif case == "neumann":
+        s = inputs.munk(N=1025, freq=100.0, dr=25.0, steps=40, bc="neumann")
+    else:
+        s = inputs.munk(N=8191, freq=100.0, dr=25.0, steps=6)
+    k = s.steps // 2
+    ref = sssp.plan_for(s, tl_every=1)
+    ref.march(s.steps)
+    u_ref = ref.read_field()
+    tl_ref, _ = ref.read_tl()
+    ref.close()
+    a = sssp.plan_for(s, tl_every=1)
+    a.march(k)
+    u_k = a.read_field()
+    state, r_set, steps = a.save_state()
+    assert steps == k and state.size == sssp.lib().pe_state_size(a._p) // 2
+    a.close()
+    b = sssp.plan_for(s, tl_every=1)
+    b.load_state(state, r_set, steps)
+    assert np.array_equal(b.read_field(), u_k)
+    b.march(s.steps - k)
+    assert b.range()[1] == s.steps
+    assert np.array_equal(b.read_field(), u_ref)
+    tl_b, rng_b = b.read_tl()
+    assert np.array_equal(tl_b, tl_ref[k:])
+    assert np.allclose(rng_b, s.r0 + s.dr * np.arange(k + 1, s.steps + 1))
+    b.close()
+
+
+def test_load_state_argument_checks(sssp):
+    s = inputs.munk(N=255, steps=3)
+    pl = sssp.plan_for(s)
+    with pytest.raises(sssp.PEError):
+        pl.load_state(np.zeros(256, np.complex64), 0.0, -1)
+    with pytest.raises(sssp.PEError):
+        pl.load_state(np.zeros(256, np.complex64), float("nan"), 0)
+    pl.close()
+    fresh = sssp.Plan(255, 5000.0, 0.2, 25.0, 4)
+    with pytest.raises(sssp.PEError):              # nothing to save before a field is set
+        fresh.save_state()
+    fresh.close()
+
+
+# ----------------------------------------------------------------------------- Neumann bound, status
+@pytest.mark.parametrize("bc,N", [("dirichlet", 1023), ("periodic", 1024), ("neumann", 1025)])
+def test_neumann_bound_matches_oracle(sssp, bc, N):
+    """The library's host bound on the Neumann series (from the device copy of V) against the
+    oracle's, per Pade term; V is FP32 on the device, hence the 1e-6 relative tolerance."""
+    s = inputs.munk(N=N, freq=60.0, dr=25.0, steps=2, bc=bc)
+    pl = sssp.plan_for(s)
+    rho = pl.neumann_bound(0)
+    g = O.Grid(N=s.N, H=s.H, k0=s.k0, dr=s.dr, bc=bc)
+    V = O.profile_at(s.profiles, 0.0) - 1.0
+    ref = O.neumann_bound(V, O.pade_plan(g.sigma, s.pade_order).b, g.lam)
+    assert np.allclose(rho, ref, rtol=1e-6, atol=0), (rho, ref)
+    with pytest.raises(sssp.PEError):
+        pl.neumann_bound(5)                        # no such node
+    pl.close()
+
+
+def test_injected_device_status_is_reported(sssp):
+    """The error path of a failing march, without a failing march: a status word written into
+    the plan's device status is reported by the next call that checks it, and a new starter
+    clears it."""
+    s = inputs.munk(N=255, steps=4)
+    pl = sssp.plan_for(s)
+    pl.march(2)
+    pl.inject_status(4)
+    with pytest.raises(sssp.PEError) as e:
+        pl.sync()
+    assert e.value.status == sssp.PE_ERR_NEUMANN_DIVERGED
+    pl.inject_status(7)
+    with pytest.raises(sssp.PEError) as e:
+        pl.read_field()
+    assert e.value.status == sssp.PE_ERR_NUMERIC
+    pl.set_field(s.u0, r=s.r0)
+    pl.march(4)
+    u = pl.read_field()
+    pl.close()
+    ref = sssp.plan_for(s)
+    ref.march(4)
+    assert np.array_equal(u, ref.read_field())
+    ref.close()
+
+
+def test_server_cancel_running(sssp):
+    """Cancelling a running request frees its budget at once; the others complete unchanged."""
+    srv = sssp.Server(hbm_budget_bytes=200_000_000, max_live=8, chunk_steps=5)
+    solves = [inputs.munk(N=511, freq=f, dr=25.0, steps=30) for f in (80.0, 100.0, 120.0)]
+    ids = [srv.submit(s, tl_every=0) for s in solves]
+    srv.step()
+    assert all(srv.state(i) == 1 for i in ids)
+    before = srv.stats()["bytes_in_use"]
+    srv.cancel(ids[1])
+    assert srv.state(ids[1]) == 3 and srv.stats()["bytes_in_use"] < before
+    while any(srv.state(i) < 2 for i in (ids[0], ids[2])):
+        srv.step()
+    for i, s in ((ids[0], solves[0]), (ids[2], solves[2])):
+        f, _ = srv.take(i)
+        pl = sssp.plan_for(s)
+        pl.march(s.steps)
+        assert np.array_equal(pl.read_field(), f)
+        pl.close()
+    with pytest.raises(sssp.PEError, match="cancelled"):
+        srv.take(ids[1])
+    srv.close()

@@ -557,3 +557,49 @@ def test_modal_starter_isovelocity_closed_form():
         ref += psi_s * psi / kap2 ** 0.25
     ref *= math.sqrt(2 * math.pi)
     assert np.max(np.abs(u - ref)) / np.max(np.abs(ref)) < 1e-9
+
+
+def _dense_neumann_operator(V, bj, grid):
+    """b_j L_j^{-1} diag(V) as a dense matrix, column by column through the oracle's L^{-1}."""
+    I = np.eye(grid.N)
+    cols = [bj * O.apply_Linv(V * I[:, k], bj, grid.lam, grid.bc) for k in range(grid.N)]
+    return np.stack(cols, axis=1)
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic", "neumann"])
+def test_neumann_bound_is_the_operator_norm_for_constant_V(bc):
+    # constant V: b_j L_j^{-1} V = v b_j L_j^{-1}, whose 2-norm is exactly |v| max |b/(1+b lambda)|
+    N = 32 if bc != "neumann" else 33
+    grid = O.Grid(N, 400.0, 2 * np.pi * 25 / 1500.0, 20.0, bc=bc)
+    plan = O.pade_plan(grid.sigma, 4)
+    V = np.full(N, -0.013)
+    rho = O.neumann_bound(V, plan.b, grid.lam)
+    # the DCT-I is orthogonal in the trapezoid-weighted norm (1/2 on both boundary points)
+    w = np.ones(N)
+    if bc == "neumann":
+        w[0] = w[-1] = 0.5
+    for j, bj in enumerate(plan.b):
+        A = _dense_neumann_operator(V, bj, grid)
+        nrm = np.linalg.norm(np.sqrt(w)[:, None] * A / np.sqrt(w)[None, :], 2)
+        assert abs(nrm - rho[j]) <= 1e-10 * rho[j]
+
+
+def test_neumann_bound_bounds_a_varying_V_and_predicts_convergence():
+    grid = O.Grid(63, 500.0, 2 * np.pi * 50 / 1500.0, 25.0)
+    z = inputs.depth_grid(63, 500.0)
+    V = O.profile_at([(0.0, inputs.n2_from_c(inputs.munk_c(z), 1500.0))], 0.0) - 1.0
+    plan = O.pade_plan(grid.sigma, 6)
+    rho = O.neumann_bound(V, plan.b, grid.lam)
+    for j, bj in enumerate(plan.b):
+        nrm = np.linalg.norm(_dense_neumann_operator(V, bj, grid), 2)
+        assert nrm <= rho[j] * (1 + 1e-12)
+    # every rho_j < 1 here: the terms of each series shrink at least geometrically, so 40 terms
+    # reach a relative tolerance of rho^39
+    assert rho.max() < 1.0
+    u = np.sin(np.pi * 3 * z / 500.0).astype(np.complex128)
+    w40, counts = O.neumann_w(u, V, plan.b, grid.lam, 40, 0.0, return_counts=True)
+    w80 = O.neumann_w(u, V, plan.b, grid.lam, 80, 0.0)
+    err = np.linalg.norm(w40 - w80, axis=0) / np.linalg.norm(w80, axis=0)
+    bound = rho ** 40 / (1 - rho) * np.linalg.norm(O.apply_Linv(np.repeat(u[:, None], 6, 1), plan.b, grid.lam), axis=0) \
+        / np.linalg.norm(w80, axis=0)
+    assert np.all(err <= bound * (1 + 1e-6) + 1e-15)
