@@ -228,6 +228,25 @@ pe_status pe_dst1_batch(pe_plan* plan, const float* in, float* out, int count);
 pe_status pe_dst1_noalloc(const float* in, float* out, int N, void* cuda_stream);
 
 /*
+ * Which kernel marches a plan (no counterpart in the paper, which gives no implementation).
+ *   PE_KERNEL_CTA      one CTA per solve, the field in that SM's shared memory (N + 1 <= 4096) or
+ *                      in a per-plan global workspace (larger grids);
+ *   PE_KERNEL_CLUSTER  one solve over a thread-block cluster of 8 CTAs (16 for N + 1 = 32768),
+ *                      every length-(N + 1) array in the cluster's distributed shared memory and
+ *                      each DST-I of Section 3.1 as local FFTs plus one all-to-all exchange;
+ *                      Dirichlet grids with N + 1 in [4096, 32768];
+ *   PE_KERNEL_AUTO     (default) the cluster kernel for Dirichlet grids with N + 1 in
+ *                      [8192, 32768] when the device holds such a cluster, else one CTA.
+ * Both compute the same step; results agree to FP32 rounding, not bit for bit.
+ * pe_plan_set_kernel fails with PE_ERR_ARG for a choice the plan or device cannot take.
+ * pe_plan_get_kernel reports the kernel a march of the plan uses (PE_KERNEL_CTA or _CLUSTER).
+ * pe_dst1 on a plan set to PE_KERNEL_CLUSTER runs the cluster transform.
+ */
+enum { PE_KERNEL_AUTO = 0, PE_KERNEL_CTA = 1, PE_KERNEL_CLUSTER = 2 };
+pe_status pe_plan_set_kernel(pe_plan* plan, int kernel);
+pe_status pe_plan_get_kernel(const pe_plan* plan, int* kernel);
+
+/*
  * Checkpoint / resume of a march (bit-exact).  The state is the marcher's own variables: the
  * unnormalised transform coefficients of the envelope and its depth-domain copy, L complex
  * values each (L = N + 1 Dirichlet, N periodic, 2 (N - 1) Neumann), interleaved re/im, 4 L

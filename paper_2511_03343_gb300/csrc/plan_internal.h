@@ -20,6 +20,7 @@ struct pe_plan {
   int user_bc = 0;  // the caller's boundary condition (PE_BC_NEUMANN runs as a periodic plan on
                     // the even extension of the field to [0, 2H])
   int N_user = 0;   // grid points the caller sees
+  int kernel = 0;   // PE_KERNEL_AUTO / PE_KERNEL_CTA / PE_KERNEL_CLUSTER
   int off = 1;  // index of the first stored depth point in the length-L arrays
   double H = 0, k0 = 0, dr = 0, tol = 0;
   cudaStream_t stream = nullptr;

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/sssp.h"
+#include "cluster_launch.h"
 #include "march_kernel.cuh"
 #include "march_large.cuh"
 #include "pade_host.h"
@@ -314,6 +315,17 @@ int node_for(const pe_plan* p, double rmid) {
 long long records_between(long long a, long long b, int every) {  // multiples of every in (a, b]
   if (every <= 0) return 0;
   return b / every - a / every;
+}
+
+// Whether a march of this plan runs on the cluster kernel (one solve over a thread-block
+// cluster).  Automatic choice: Dirichlet grids with L >= 8192 up to the cluster kernel's
+// largest size, when the device can hold such a cluster.
+bool use_cluster(const pe_plan* p, bool cplx) {
+  if (p->bc != PE_BC_DIRICHLET || !sssp_cluster::supported(p->log2L)) return false;
+  if (p->kernel == PE_KERNEL_CTA) return false;
+  if (p->kernel == PE_KERNEL_AUTO && p->log2L < 13) return false;
+  int clusters = 0;
+  return sssp_cluster::max_active_clusters(p->log2L, cplx, &clusters) == cudaSuccess && clusters > 0;
 }
 
 // Fill the descriptor for one march of `steps` steps and reserve its TL rows.
@@ -683,7 +695,11 @@ pe_status pe_march(pe_plan* p, int steps) {
   if (st != PE_OK) return st;
   if (steps == 0) return PE_OK;
   PE_CUDA(p, cudaMemcpyAsync(p->dDesc, &d, sizeof(d), cudaMemcpyHostToDevice, p->stream));
-  PE_CUDA(p, launch_march(p->log2L, p->dDesc, 1, p->tabs, p->stream, d.Vi != nullptr, p->bc));
+  const bool cplx = d.Vi != nullptr;
+  if (use_cluster(p, cplx))
+    PE_CUDA(p, sssp_cluster::launch_march(p->log2L, p->dDesc, 1, p->stream, cplx, p->device));
+  else
+    PE_CUDA(p, launch_march(p->log2L, p->dDesc, 1, p->tabs, p->stream, cplx, p->bc));
   return PE_OK;
 }
 
@@ -697,10 +713,10 @@ pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
     if (plans[i]->device != p0->device) return fail(p0, PE_ERR_ARG, "plans on different devices");
     if (steps[i] < 0) return fail(p0, PE_ERR_ARG, "steps must be >= 0");
   }
-  // group by (size, complex profile), one launch per group; every CTA marches its own plan its
-  // own step count
-  std::map<std::tuple<int, bool, int>, std::vector<SolveDesc>> groups;
-  std::map<std::tuple<int, bool, int>, TransformTables> tabs;
+  // group by (size, complex profile, boundary condition, kernel), one launch per group; every
+  // CTA (or cluster) marches its own plan its own step count
+  std::map<std::tuple<int, bool, int, bool>, std::vector<SolveDesc>> groups;
+  std::map<std::tuple<int, bool, int, bool>, TransformTables> tabs;
   for (int i = 0; i < count; ++i) {
     if (steps[i] == 0) continue;
     SolveDesc d;
@@ -709,7 +725,8 @@ pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
       p0->err = plans[i]->err;
       return st;
     }
-    const auto key = std::make_tuple(plans[i]->log2L, d.Vi != nullptr, plans[i]->bc);
+    const bool cplx = d.Vi != nullptr;
+    const auto key = std::make_tuple(plans[i]->log2L, cplx, plans[i]->bc, use_cluster(plans[i], cplx));
     groups[key].push_back(d);
     tabs[key] = plans[i]->tabs;
   }
@@ -718,8 +735,12 @@ pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
     const size_t bytes = sizeof(SolveDesc) * kv.second.size();
     PE_CUDA(p0, cudaMallocAsync(reinterpret_cast<void**>(&dd), bytes, p0->stream));
     PE_CUDA(p0, cudaMemcpyAsync(dd, kv.second.data(), bytes, cudaMemcpyHostToDevice, p0->stream));
-    PE_CUDA(p0, launch_march(std::get<0>(kv.first), dd, int(kv.second.size()), tabs[kv.first], p0->stream,
-                             std::get<1>(kv.first), std::get<2>(kv.first)));
+    if (std::get<3>(kv.first))
+      PE_CUDA(p0, sssp_cluster::launch_march(std::get<0>(kv.first), dd, int(kv.second.size()), p0->stream,
+                                             std::get<1>(kv.first), p0->device));
+    else
+      PE_CUDA(p0, launch_march(std::get<0>(kv.first), dd, int(kv.second.size()), tabs[kv.first], p0->stream,
+                               std::get<1>(kv.first), std::get<2>(kv.first)));
     PE_CUDA(p0, cudaFreeAsync(dd, p0->stream));
   }
   return PE_OK;
@@ -802,7 +823,10 @@ pe_status pe_dst1(pe_plan* p, const float* in, float* out, int on_device) {
     PE_CUDA(p, cudaGetLastError());
     scale = 0.5f;
   }
-  PE_CUDA(p, launch_dst(p->log2L, tmp, res, scale, p->tabs, p->stream, p->dWork, p->bc));
+  if (p->user_bc == PE_BC_DIRICHLET && p->kernel == PE_KERNEL_CLUSTER)
+    PE_CUDA(p, sssp_cluster::launch_dst(p->log2L, tmp, res, scale, 1, 0, 0, p->stream, p->device));
+  else
+    PE_CUDA(p, launch_dst(p->log2L, tmp, res, scale, p->tabs, p->stream, p->dWork, p->bc));
   PE_CUDA(p, cudaMemcpyAsync(out, res + p->off, sizeof(float2) * p->N_user,
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream));
   PE_CUDA(p, cudaFreeAsync(res, p->stream));
@@ -828,6 +852,28 @@ pe_status pe_dst1_batch(pe_plan* p, const float* in, float* out, int count) {
                                count, cudaMemcpyDeviceToDevice, p->stream));
   PE_CUDA(p, cudaFreeAsync(res, p->stream));
   if (work) PE_CUDA(p, cudaFreeAsync(work, p->stream));
+  return PE_OK;
+}
+
+pe_status pe_plan_set_kernel(pe_plan* p, int kernel) {
+  if (!p) return PE_ERR_ARG;
+  if (kernel != PE_KERNEL_AUTO && kernel != PE_KERNEL_CTA && kernel != PE_KERNEL_CLUSTER)
+    return fail(p, PE_ERR_ARG, "kernel must be PE_KERNEL_AUTO, PE_KERNEL_CTA or PE_KERNEL_CLUSTER");
+  if (kernel == PE_KERNEL_CLUSTER) {
+    if (p->user_bc != PE_BC_DIRICHLET || !sssp_cluster::supported(p->log2L))
+      return fail(p, PE_ERR_ARG, "the cluster kernel takes Dirichlet grids with N + 1 in [4096, 32768]");
+    int a = 0, b = 0;
+    PE_CUDA(p, sssp_cluster::max_active_clusters(p->log2L, false, &a));
+    PE_CUDA(p, sssp_cluster::max_active_clusters(p->log2L, true, &b));
+    if (a < 1 || b < 1) return fail(p, PE_ERR_ARG, "this device cannot hold a cluster of the required shape");
+  }
+  p->kernel = kernel;
+  return PE_OK;
+}
+
+pe_status pe_plan_get_kernel(const pe_plan* p, int* kernel) {
+  if (!p || !kernel) return PE_ERR_ARG;
+  *kernel = use_cluster(p, p->complex_profile) ? PE_KERNEL_CLUSTER : PE_KERNEL_CTA;
   return PE_OK;
 }
 

@@ -64,6 +64,8 @@ _SIGNATURES = {
     "pe_get_range": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
     "pe_pade_coefficients": (_i, [_d, _i, _vp, _vp, _vp]),
     "pe_march_batch_steps": (_i, [ctypes.POINTER(_vp), _vp, _i]),
+    "pe_plan_set_kernel": (_i, [_vp, _i]),
+    "pe_plan_get_kernel": (_i, [_vp, ctypes.POINTER(_i)]),
     "pe_state_size": (_sz, [_vp]),
     "pe_save_state": (_i, [_vp, _vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
     "pe_load_state": (_i, [_vp, _vp, _d, ctypes.c_longlong]),
@@ -285,6 +287,17 @@ class Plan:
         self._c(lib().pe_get_range(self._p, ctypes.byref(r), ctypes.byref(s)))
         return r.value, s.value
 
+    def set_kernel(self, kernel: str):
+        """'auto', 'cta' (one CTA per solve) or 'cluster' (one solve over a thread-block cluster)."""
+        self._c(lib().pe_plan_set_kernel(self._p, KERNELS[kernel]))
+
+    @property
+    def kernel(self) -> str:
+        """The kernel a march of this plan runs: 'cta' or 'cluster'."""
+        k = _i(0)
+        self._c(lib().pe_plan_get_kernel(self._p, ctypes.byref(k)))
+        return {v: n for n, v in KERNELS.items()}[k.value]
+
     def save_state(self):
         """Bit-exact checkpoint: (spectral state, r_set, steps)."""
         st = np.empty(int(lib().pe_state_size(self._p)) // 2, dtype=np.complex64)  # 2 L values
@@ -400,6 +413,8 @@ class Server:
         self._c(lib().pe_server_stats(self._s, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return {"bytes_in_use": a.value, "peak_bytes": b.value, "peak_live": c.value}
 
+
+KERNELS = {"auto": 0, "cta": 1, "cluster": 2}
 
 GEMM_MODES = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3}
 
