@@ -211,6 +211,7 @@ def bench_other(args):
     plans = []
     for s in solves:
         pl = sssp.Plan(s.N, s.H, s.k0, s.dr, s.pade_order, s.neumann_terms, s.neumann_tol, stream=stream)
+        pl.set_kernel(args.kernel)
         pl.set_output(1)
         if s.neumann_terms > 1:
             pl.set_profile_nodes(s.profiles)
@@ -249,6 +250,7 @@ def bench_other(args):
             "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64", "data": "synthetic",
             "config": {"workload": args.workload, "solves": len(solves), "N": [s.N for s in solves][:1],
+                       "kernel": plans[0].kernel,
                        "range_steps": steps},
             "dst_per_step": (nd1 - nd0) / args.steps, "clocks": clk}
     print(json.dumps(line), flush=True)
@@ -414,6 +416,7 @@ def bench_ours(args):
     s = inputs.munk(steps=args.range_steps)
     stream = torch.cuda.current_stream()
     pl = sssp.Plan(s.N, s.H, s.k0, s.dr, s.pade_order, s.neumann_terms, s.neumann_tol, stream=stream)
+    pl.set_kernel(args.kernel)
     pl.set_output(1)
     pl.set_profile_nodes(s.profiles)
     u0_dev = torch.from_numpy(s.u0.astype(np.complex64)).cuda()
@@ -495,10 +498,11 @@ def bench_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-                "config": _config(),
+                "config": _config({"kernel": pl.kernel}),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak, "traffic": None,
-                             "kernel": "sssp_march_kernel<12> (one CTA, one SM)",
+                             "kernel": ("sssp_march_cluster_kernel<12, 8> (one solve over an 8-CTA cluster, 8 SMs)"
+                                        if pl.kernel == "cluster" else "sssp_march_kernel<12> (one CTA, one SM)"),
                              "flops_per_launch": flops, "dst_per_launch": dst_per_launch,
                              "kernel_ms": kern_avg,
                              "peak_note": "FP32 FMA peak of all 152 SMs at the sampled max SM clock (derived, not measured)"},
@@ -530,6 +534,8 @@ def main():
     ap.add_argument("--chunk-steps", type=int, default=50)
     ap.add_argument("--serve-baseline", action="store_true")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--kernel", default="auto", choices=["auto", "cta", "cluster"],
+                    help="march kernel: one CTA per solve, one solve per thread-block cluster, or automatic")
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)

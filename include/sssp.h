@@ -236,7 +236,10 @@ pe_status pe_dst1_noalloc(const float* in, float* out, int N, void* cuda_stream)
  *                      each DST-I of Section 3.1 as local FFTs plus one all-to-all exchange;
  *                      Dirichlet grids with N + 1 in [4096, 32768];
  *   PE_KERNEL_AUTO     (default) the cluster kernel for Dirichlet grids with N + 1 in
- *                      [8192, 32768] when the device holds such a cluster, else one CTA.
+ *                      [4096, 32768] when the device holds such a cluster, else one CTA; for
+ *                      N + 1 = 4096 in a batched march only while that size's solves fit on
+ *                      the device as clusters at once (beyond that one CTA per solve gives
+ *                      more throughput).
  * Both compute the same step; results agree to FP32 rounding, not bit for bit.
  * pe_plan_set_kernel fails with PE_ERR_ARG for a choice the plan or device cannot take.
  * pe_plan_get_kernel reports the kernel a march of the plan uses (PE_KERNEL_CTA or _CLUSTER).

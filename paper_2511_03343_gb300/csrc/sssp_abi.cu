@@ -318,14 +318,17 @@ long long records_between(long long a, long long b, int every) {  // multiples o
 }
 
 // Whether a march of this plan runs on the cluster kernel (one solve over a thread-block
-// cluster).  Automatic choice: Dirichlet grids with L >= 8192 up to the cluster kernel's
-// largest size, when the device can hold such a cluster.
-bool use_cluster(const pe_plan* p, bool cplx) {
+// cluster), when it is launched together with `group` solves of its size.  Automatic choice:
+// Dirichlet grids with L in [4096, 32768] when the device holds such a cluster; at L = 4096
+// only while the group's clusters fit on the device at once (the one-CTA kernel does the same
+// work on fewer SMs, so it gives more throughput once every SM is busy).
+bool use_cluster(const pe_plan* p, bool cplx, int group = 1) {
   if (p->bc != PE_BC_DIRICHLET || !sssp_cluster::supported(p->log2L)) return false;
   if (p->kernel == PE_KERNEL_CTA) return false;
-  if (p->kernel == PE_KERNEL_AUTO && p->log2L < 13) return false;
   int clusters = 0;
-  return sssp_cluster::max_active_clusters(p->log2L, cplx, &clusters) == cudaSuccess && clusters > 0;
+  if (sssp_cluster::max_active_clusters(p->log2L, cplx, &clusters) != cudaSuccess || clusters < 1) return false;
+  if (p->kernel == PE_KERNEL_AUTO && p->log2L == 12 && group > clusters) return false;
+  return true;
 }
 
 // Fill the descriptor for one march of `steps` steps and reserve its TL rows.
@@ -717,6 +720,10 @@ pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
   // CTA (or cluster) marches its own plan its own step count
   std::map<std::tuple<int, bool, int, bool>, std::vector<SolveDesc>> groups;
   std::map<std::tuple<int, bool, int, bool>, TransformTables> tabs;
+  std::map<std::tuple<int, bool, int>, int> size_count;  // solves per (size, complex, bc)
+  for (int i = 0; i < count; ++i)
+    if (steps[i] > 0)
+      ++size_count[std::make_tuple(plans[i]->log2L, plans[i]->complex_profile, plans[i]->bc)];
   for (int i = 0; i < count; ++i) {
     if (steps[i] == 0) continue;
     SolveDesc d;
@@ -726,7 +733,8 @@ pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
       return st;
     }
     const bool cplx = d.Vi != nullptr;
-    const auto key = std::make_tuple(plans[i]->log2L, cplx, plans[i]->bc, use_cluster(plans[i], cplx));
+    const int group = size_count[std::make_tuple(plans[i]->log2L, plans[i]->complex_profile, plans[i]->bc)];
+    const auto key = std::make_tuple(plans[i]->log2L, cplx, plans[i]->bc, use_cluster(plans[i], cplx, group));
     groups[key].push_back(d);
     tabs[key] = plans[i]->tabs;
   }

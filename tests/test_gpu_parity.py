@@ -645,3 +645,142 @@ def test_server_cancel_running(sssp):
     with pytest.raises(sssp.PEError, match="cancelled"):
         srv.take(ids[1])
     srv.close()
+
+
+# ----------------------------------------------------------------------------- cluster kernel
+@pytest.mark.parametrize("N", [4095, 8191, 16383, 32767])
+def test_cluster_dst_matches_oracle(sssp, N):
+    """The cluster transform (residue rows over 8 or 16 CTAs, local FFTs + one all-to-all, the
+    scan-free DST-I) against the oracle: every output at N = 4095, sampled outputs beyond."""
+    rng = np.random.default_rng(N + 11)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    pl = sssp.Plan(N, 100.0, 0.4, 5.0, 4)
+    pl.set_kernel("cluster")
+    X = pl.dst1(x.astype(np.complex64))
+    pl.close()
+    scale = np.sqrt(N / 2.0) * np.sqrt(2.0)
+    if N == 4095:
+        err = np.max(np.abs(X - O.dst1(x))) / scale
+    else:
+        ms = np.concatenate([[1, 2, 3, N // 2, N // 2 + 1, N - 1, N], rng.integers(1, N + 1, 40)])
+        err = np.max(np.abs(X[ms - 1] - O.dst1_at(x, ms))) / scale
+    # the scan-free form has the FFT's error (no prefix scan): a few FP32 ulps times log2 L
+    assert err < 1e-6 * math.log2(N + 1), err
+
+
+def test_cluster_kernel_choice(sssp):
+    """Automatic choice: the cluster kernel for Dirichlet N + 1 >= 4096, one CTA below; the
+    cluster kernel is refused where it does not apply."""
+    big = sssp.Plan(8191, 5000.0, 0.4, 25.0, 6, 12)
+    assert big.kernel == "cluster"
+    big.set_kernel("cta")
+    assert big.kernel == "cta"
+    big.close()
+    mid = sssp.Plan(4095, 5000.0, 0.4, 25.0, 6, 12)
+    assert mid.kernel == "cluster"
+    mid.set_kernel("cta")
+    assert mid.kernel == "cta"
+    mid.close()
+    for pl in (sssp.Plan(1023, 5000.0, 0.4, 25.0, 6, 12), sssp.Plan(65535, 5000.0, 0.4, 25.0, 6, 12),
+               sssp.Plan(4096, 5000.0, 0.4, 25.0, 6, 12, bc="periodic")):
+        with pytest.raises(sssp.PEError) as e:
+            pl.set_kernel("cluster")
+        assert e.value.status == sssp.PE_ERR_ARG
+        pl.close()
+
+
+def test_cluster_march_n4095_matches_oracle_and_cta(sssp):
+    """Munk N = 4095, 100 Hz, [6/6], 12 terms, 30 steps on the cluster kernel: against the
+    oracle (field and TL bars) and against the one-CTA kernel (FP32 rounding apart)."""
+    s = inputs.munk(N=4095, freq=100.0, dr=25.0, steps=30)
+    out = {}
+    for k in ("cluster", "cta"):
+        pl = sssp.plan_for(s, tl_every=1)
+        pl.set_kernel(k)
+        pl.march(s.steps)
+        out[k] = (pl.read_field(), pl.read_tl()[0], pl.transform_count())
+        pl.close()
+    ref = _oracle(s)
+    rel = _compare(out["cluster"][0], out["cluster"][1], ref)
+    print("cluster N=4095 30 steps field rel-L2 vs oracle:", rel)
+    d = np.linalg.norm(out["cluster"][0] - out["cta"][0]) / np.linalg.norm(out["cta"][0])
+    assert d < 2e-5, d
+    # the same Neumann term counts up to stop decisions at the FP32 rounding edge
+    assert abs(out["cluster"][2] - out["cta"][2]) <= 0.02 * out["cta"][2]
+
+
+def test_cluster_isovelocity_mode_n32767(sssp):
+    """N = 32767 on the 16-CTA cluster, isovelocity: a sine mode is an eigenvector of the step,
+    so after n steps it is (e^{i sigma} R(lambda_m))^n times itself (closed form); the TL rows
+    come from the cluster's inverse transform."""
+    N, m0, steps = 32767, 57, 25
+    s = inputs.isovelocity(N=N, H=5000.0, freq=200.0, dr=25.0, steps=steps, pade_order=8)
+    s.u0 = np.sin(np.pi * m0 * s.z / s.H).astype(np.complex128)
+    pl = sssp.plan_for(s, tl_every=5)
+    assert pl.kernel == "cluster"
+    pl.march(steps)
+    u = pl.read_field()
+    tl, _ = pl.read_tl()
+    pl.close()
+    plan = O.pade_plan(s.k0 * s.dr, 8)
+    G = np.exp(1j * s.k0 * s.dr) * plan.rational(-(np.pi * m0 / (s.k0 * s.H)) ** 2)
+    ref = G ** steps * s.u0
+    assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < 1e-5
+    ref_tl = -20 * np.log10(np.abs(ref)) + 10 * np.log10(s.r0 + s.dr * steps)
+    mask = ref_tl < 100
+    assert np.max(np.abs(tl[-1][mask] - ref_tl[mask])) < TL_TOL
+
+
+def test_cluster_munk_n32767_vs_cta(sssp):
+    """Munk N = 32767, 300 Hz, [6/6], 12 terms, 4 steps: the 16-CTA cluster kernel against the
+    one-CTA global-workspace kernel, and norm conservation for the real profile."""
+    s = inputs.munk(N=32767, freq=300.0, dr=25.0, steps=4)
+    out = {}
+    for k in ("cluster", "cta"):
+        pl = sssp.plan_for(s)
+        pl.set_kernel(k)
+        pl.march(s.steps)
+        out[k] = pl.read_field()
+        pl.close()
+    d = np.linalg.norm(out["cluster"] - out["cta"]) / np.linalg.norm(out["cta"])
+    assert d < 1e-5, d
+    assert abs(np.linalg.norm(out["cluster"]) / np.linalg.norm(s.u0) - 1) < 1e-5
+
+
+def test_cluster_divergence_is_reported(sssp):
+    """A diverging Neumann series on the cluster kernel: every CTA takes the same stop decision
+    (the status is reported, the march ends, the plan stays usable)."""
+    N = 4095
+    pl = sssp.Plan(N, 100.0, 0.4, 5.0, 4, 12, 1e-10)
+    pl.set_kernel("cluster")
+    pl.set_profile(np.full(N, 40.0), 0.0)
+    pl.set_field(np.ones(N, dtype=np.complex64))
+    pl.march(3)
+    with pytest.raises(sssp.PEError) as e:
+        pl.sync()
+    assert e.value.status == sssp.PE_ERR_NEUMANN_DIVERGED
+    pl.set_profile(np.full(N, 1.0), 1.0)
+    pl.set_field(np.ones(N, dtype=np.complex64))
+    pl.march(2)
+    pl.sync()
+    pl.close()
+
+
+def test_cluster_batch_alone_vs_mix(sssp):
+    """Cluster solves and one-CTA solves in one batched call: each result has the same bits as
+    marching it alone."""
+    solves = [inputs.munk(N=8191, freq=90.0, dr=25.0, steps=5), inputs.munk(N=1023, freq=60.0, steps=5),
+              inputs.munk(N=8191, freq=120.0, dr=25.0, steps=5), inputs.munk(N=16383, freq=200.0, dr=25.0, steps=5)]
+    alone = []
+    for s in solves:
+        pl = sssp.plan_for(s, tl_every=1)
+        pl.march(5)
+        alone.append((pl.read_field(), pl.read_tl()[0]))
+        pl.close()
+    plans = [sssp.plan_for(s, tl_every=1) for s in solves]
+    assert [p.kernel for p in plans] == ["cluster", "cta", "cluster", "cluster"]
+    sssp.march_batch(plans, 5)
+    for pl, (u, tl) in zip(plans, alone):
+        assert np.array_equal(pl.read_field(), u)
+        assert np.array_equal(pl.read_tl()[0], tl)
+        pl.close()
