@@ -35,6 +35,15 @@ def _rank_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def _hbm_peak():
+    """Measured HBM copy bandwidth (GB/s) of the GB300s, else the stated fallback."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
 def _config(extra=None):
     c = {"workload": WORKLOAD, "N": 4095, "H_m": 5000.0, "freq_hz": 50.0, "dr_m": 50.0, "range_steps": 2000,
          "pade_order": 6, "neumann_terms": 12, "neumann_tol": 1e-10, "tl_every": 1, "solves_per_gpu": 1,
@@ -206,6 +215,9 @@ def bench_other(args):
         solves = inputs.munk_batch(count=args.batch_count, steps=steps)
     elif args.workload == "eddy":
         solves = [inputs.munk_eddy(steps=steps)]
+    elif args.workload == "large":
+        # grids of 65536 points, a batch whose footprint is several times the L2: the HBM-bound case
+        solves = inputs.munk_batch(count=args.large_count, N=65535, steps=steps, seed=6, fmin=100.0, fmax=1000.0)
     else:
         solves = [inputs.isovelocity(steps=steps)]
     plans = []
@@ -253,6 +265,14 @@ def bench_other(args):
                        "kernel": plans[0].kernel,
                        "range_steps": steps},
             "dst_per_step": (nd1 - nd0) / args.steps, "clocks": clk}
+    if args.workload == "large":
+        # algorithmic bytes of a transform of length L = N + 1: two global passes of 16 B per point
+        L = solves[0].N + 1
+        gbs = 32.0 * L * (nd1 - nd0) / (tot * 1e-3) / 1e9
+        peak = _hbm_peak()
+        line["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                            "traffic": None, "bytes_per_transform": 32.0 * L,
+                            "peak_note": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"}
     print(json.dumps(line), flush=True)
     for pl in plans:
         pl.close()
@@ -528,7 +548,9 @@ def main():
     ap.add_argument("--range-steps", type=int, default=2000,
                     help="range steps per march (2000 = the workload; fewer only for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="munk", choices=["munk", "batch", "eddy", "iso", "serve", "gemm", "dst"])
+    ap.add_argument("--workload", default="munk",
+                    choices=["munk", "batch", "eddy", "iso", "serve", "gemm", "dst", "large"])
+    ap.add_argument("--large-count", type=int, default=64, help="solves in the N = 65535 batch ('large')")
     ap.add_argument("--serve-requests", type=int, default=100)
     ap.add_argument("--range-scale", type=float, default=0.05)
     ap.add_argument("--chunk-steps", type=int, default=50)

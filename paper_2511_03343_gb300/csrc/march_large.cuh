@@ -2,23 +2,24 @@
 //
 // Same method as march_kernel.cuh (product-form Pade stages with hi/lo multipliers, Neumann
 // series, spectral-resident field), but every length-L array lives in a per-solve workspace
-// in global memory (L2-resident for a single solve, HBM for large batches), one CTA of 1024
+// in global memory (L2-resident for a single solve, HBM for large batches), one CTA of 512
 // threads per solve, with a __syncthreads between passes (global writes are visible to the
-// block after it).  The DST-I here is the scan-free form (two batched length-L FFTs, see
-// dst_global): the prefix-scan form's odd outputs lose accuracy like sqrt(L) (3.6e-5 relative
-// at L = 65536 in FP32), which these grids cannot afford.
-// Element-wise work walks the natural index i = t + 1024 q, so every access is coalesced.
+// block after it).  The DST-I here is the DFT of the odd extension in two passes of
+// shared-memory tiles (see dst_global), with no prefix scan: the scan form's odd outputs lose
+// accuracy like sqrt(L) (3.6e-5 relative at L = 65536 in FP32), which these grids cannot afford.
+// Element-wise work walks the natural index i = t + 512 q, so every access is coalesced.
 #pragma once
 #include "march_kernel.cuh"
 
 namespace sssp {
 
-constexpr int kLargeNT = 1024;
+constexpr int kLargeNT = 512;
+constexpr int kLargeLog2Tile = 12;  // 8 points per thread per tile
 constexpr int kLargeMinLog2 = 13;
 constexpr int kLargeMaxLog2 = 16;
 
-// workspace layout (float2 units): X (L) | W1 (2L) | W2 (2L) | acc (L) | t0 (L)
-__host__ __device__ constexpr size_t large_work_elems(int L) { return 7 * size_t(L); }
+// workspace layout (float2 units): X (L) | W (2L) | acc (L) | t0 (L)
+__host__ __device__ constexpr size_t large_work_elems(int L) { return 5 * size_t(L); }
 
 template <int LOG2L>
 struct CfgL {
@@ -44,99 +45,241 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
   return s;
 }
 
-// One global-memory Stockham pass (radix R, span NS) over TWO independent length-L FFTs stored
-// back to back (butterfly j < L/R belongs to the first, the rest to the second).
-template <int LOG2L, int R, int NS>
-__device__ __forceinline__ void gfft2_pass(const float2* __restrict__ src, float2* __restrict__ dst,
-                                           const float2* __restrict__ tw) {
-  constexpr int L = 1 << LOG2L, NB = L / R, PERB = 2 * NB / kLargeNT;
-  constexpr int OFF = NS - 8;
-  for (int q = 0; q < PERB; ++q) {
-    const int jj = threadIdx.x + q * kLargeNT;
-    const int h = (jj >= NB) ? L : 0;  // which of the two transforms
-    const int j = jj - (h ? NB : 0);
-    float2 v[R];
+// Tables of the two-pass transform: per-pass Stockham twiddles of the P- and Q-point FFTs
+// and w_{2L}^q, q in [0, 2L).
+struct LargeTabs {
+  const float2* twP;
+  const float2* twQ;
+  const float2* tw2L;
+};
+
+// The DST-I of length N = L - 1 is the DFT of the odd extension z (length 2L: z_n = x_n,
+// z_{2L-n} = -x_n, z_0 = z_L = 0): S_k = (i/2) Z_k, k in [1, L).  Four-step with 2L = P Q,
+// n = Q n1 + n2, k = k1 + P k2:
+//   pass A (columns n2): Y[k1][n2] = w_{2L}^{n2 k1} sum_{n1} z_{Q n1 + n2} w_P^{n1 k1}
+//   pass B (rows k1):    Z_{k1 + P k2} = sum_{n2} Y[k1][n2] w_Q^{n2 k2},  only k2 < Q/2 kept.
+// Each pass moves tiles of 8192 points through shared memory (8 per thread), so a transform
+// reads and writes global memory twice: 56 B per point (the odd extension reads x twice).
+template <int LOG2L>
+struct BigCfg {
+  static constexpr int L = 1 << LOG2L;
+  static constexpr int LOG2P = (LOG2L + 1) / 2;
+  static constexpr int LOG2Q = LOG2L + 1 - LOG2P;
+  static constexpr int P = 1 << LOG2P, Q = 1 << LOG2Q;
+  static constexpr int TILE = 8 * kLargeNT;
+  static_assert(TILE == (1 << kLargeLog2Tile), "tile size");
+  static constexpr int LOG2TC = kLargeLog2Tile - LOG2P, LOG2TR = kLargeLog2Tile - LOG2Q;
+  static constexpr int TC = 1 << LOG2TC, TR = 1 << LOG2TR;  // columns / rows per tile
+  static constexpr int RSP = P + P / 16 + 1, RSQ = Q + Q / 16 + 1;  // padded FFT strides
+  static constexpr int BUF = (TC * RSP > TR * RSQ) ? TC * RSP : TR * RSQ;
+  // two tile buffers, then the P- and Q-point twiddle tables
+  static constexpr size_t SMEM = sizeof(float2) * (2 * size_t(BUF) + P + Q);
+};
+
+// One Stockham pass (radix RAD, span NS) over NF = 8192 / 2^LOG2F independent FFTs of length
+// 2^LOG2F, FFT f at shared offset f RS (padded index inside).
+template <int LOG2F, int RS, int RAD, int NS>
+__device__ __forceinline__ void tpass(const float2* __restrict__ src, float2* __restrict__ dst,
+                                      const float2* __restrict__ tw) {  // tw in shared memory
+  constexpr int F = 1 << LOG2F, NB = F / RAD, PER = (8 * kLargeNT / RAD) / kLargeNT;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[h + j + r * NB];
-    const int k = j & (NS - 1);
+  for (int q = 0; q < PER; ++q) {
+    const int jb = threadIdx.x + q * kLargeNT;
+    const int f = jb / NB, jj = jb & (NB - 1);
+    const float2* s = src + f * RS;
+    float2 v[RAD];
 #pragma unroll
-    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(tw + OFF + (r - 1) * NS + k));
-    dftR<R>(v);
-    const int base = (j - k) * R + k;
+    for (int r = 0; r < RAD; ++r) v[r] = s[pidx(jj + r * NB)];
+    const int k = jj & (NS - 1);
+    if constexpr (NS > 1) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[h + base + r * NS] = v[r];
+      for (int r = 1; r < RAD; ++r) v[r] = cmul(v[r], tw[NS - 8 + (r - 1) * NS + k]);
+    }
+    dftR<RAD>(v);
+    float2* d = dst + f * RS;
+    const int base = (jj - k) * RAD + k;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) d[pidx(base + r * NS)] = v[r];
   }
 }
 
-template <int LOG2L, int NS>
-__device__ __forceinline__ float2* gfft2_rest(float2* src, float2* dst, const float2* tw) {
-  constexpr int L = 1 << LOG2L;
-  if constexpr (NS >= L) {
+// all passes of the tile's FFTs, src -> ...; returns the buffer holding the result
+template <int LOG2F, int RS, int NS>
+__device__ __forceinline__ float2* tfft(float2* src, float2* dst, const float2* tw) {
+  constexpr int F = 1 << LOG2F;
+  if constexpr (NS >= F) {
     return src;
   } else {
-    constexpr int R = (L / NS) >= 8 ? 8 : (L / NS);
-    gfft2_pass<LOG2L, R, NS>(src, dst, tw);
+    constexpr int RAD = (F / NS) >= 8 ? 8 : (F / NS);
+    tpass<LOG2F, RS, RAD, NS>(src, dst, tw);
     __syncthreads();
-    return gfft2_rest<LOG2L, NS * R>(dst, src, tw);
+    return tfft<LOG2F, RS, NS * RAD>(dst, src, tw);
   }
 }
 
-// Unnormalised DST-I of the L values in X (natural order, X[0] ignored), in place: on return
-// X[m] = S_m (S_0 = 0).  W1, W2: 2L scratch each.  Scan-free (accurate) formulation of the
-// odd extension's length-2L DFT after one radix-2 split:
-//   S_{2k}   = (i/2) FFT_L(x_n - x_{L-n})_k,
-//   S_{2k+1} = (i/2) FFT_L((x_n + x_{L-n}) e^{-i pi n/L})_k,   k < L/2,
-// the two transforms run as one batched Stockham sequence.  On return all threads are past a
-// barrier after the last write.
+// copy the P- and Q-point twiddle tables behind the two tile buffers (once per kernel)
 template <int LOG2L>
-__device__ void dst_global(float2* X, float2* W1, float2* W2, const float2* __restrict__ tw,
-                           const float* __restrict__ sinw) {
-  constexpr int L = 1 << LOG2L;
-  const int t = threadIdx.x;
-  // first radix-8 pass (span 1) fused with the split into the two inputs; X -> W1
-  for (int q = 0; q < (2 * (L / 8)) / kLargeNT; ++q) {
-    const int jj = t + q * kLargeNT;
-    const bool second = jj >= L / 8;
-    const int j = second ? jj - L / 8 : jj;
-    float2 v[8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int n = j + r * (L / 8);
-      const float2 xn = (n == 0) ? make_float2(0.f, 0.f) : X[n];
-      const float2 xm = (n == 0) ? make_float2(0.f, 0.f) : X[L - n];
-      if (!second) {
-        v[r] = xn - xm;
-      } else {
-        // e^{-i pi n/L} = cos - i sin, cos(pi n/L) from the sine table
-        const float sn = __ldg(sinw + n);
-        const float cs = (n <= L / 2) ? __ldg(sinw + (L / 2 - n)) : -__ldg(sinw + (n - L / 2));
-        const float2 sm = xn + xm;
-        v[r] = make_float2(fmaf(sm.x, cs, sm.y * sn), fmaf(sm.y, cs, -sm.x * sn));
-      }
-    }
-    dft8(v);
-    const int h = second ? L : 0;
-#pragma unroll
-    for (int r = 0; r < 8; ++r) W1[h + 8 * j + r] = v[r];
-  }
-  __syncthreads();
-  const float2* F = gfft2_rest<LOG2L, 8>(W1, W2, tw);
-  for (int q = 0; q < (L / 2) / kLargeNT; ++q) {
-    const int k = t + q * kLargeNT;
-    const float2 fe = F[k];        // FFT of the differences
-    const float2 fo = F[L + k];    // FFT of the weighted sums
-    X[2 * k] = (k == 0) ? make_float2(0.f, 0.f) : make_float2(-0.5f * fe.y, 0.5f * fe.x);
-    X[2 * k + 1] = make_float2(-0.5f * fo.y, 0.5f * fo.x);
-  }
-  __syncthreads();
+__device__ __forceinline__ void load_large_twiddles(float2* sm, const LargeTabs& tb) {
+  using C = BigCfg<LOG2L>;
+  float2* twP = sm + 2 * C::BUF;
+  for (int i = threadIdx.x; i < C::P; i += kLargeNT) twP[i] = tb.twP[i];
+  for (int i = threadIdx.x; i < C::Q; i += kLargeNT) twP[C::P + i] = tb.twQ[i];
 }
+
+// Unnormalised DST-I S_k = sum_n x_n sin(pi n k/L), k in [0, L) (S_0 = 0), of the values the
+// source gives: src(m, first) returns x_m (m in [1, L)); it is called twice per m in pass A (for
+// z_m and z_{2L-m}), `first` true on the first.  The sink takes snk(k, S_k) once per k in pass B.
+// Pass A reads every source value before pass B writes anything, so a source and sink may share
+// an array (in-place transform).  W: 2L scratch.  On return all threads are past a barrier.
+template <int LOG2L, class SRC, class SNK>
+__device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC& src, SNK& snk) {
+  using C = BigCfg<LOG2L>;
+  constexpr int L = C::L, P = C::P, Q = C::Q;
+  const int t = threadIdx.x;
+  float2* bufA = sm;
+  float2* bufB = sm + C::BUF;
+  const float2* twP = sm + 2 * C::BUF;  // copied by load_large_twiddles
+  const float2* twQ = twP + P;
+  // The next tile's global loads are issued into registers before the current tile's FFT, so
+  // their latency hides behind the shared-memory passes.
+  float2 pre[8];
+  // pass A: column FFTs of the odd extension, twiddled, rows of W
+  auto loadA = [&](int c) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int idx = t + q * kLargeNT;
+      const int n1 = idx >> C::LOG2TC, f = idx & (C::TC - 1);
+      const int n = Q * n1 + c * C::TC + f;
+      float2 z = make_float2(0.f, 0.f);
+      if (n != 0 && n != L) {
+        const float2 x = n < L ? src(n, true) : src(2 * L - n, false);
+        z = n < L ? x : make_float2(-x.x, -x.y);
+      }
+      pre[q] = z;
+    }
+  };
+  loadA(0);
+  for (int c = 0; c < Q / C::TC; ++c) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int idx = t + q * kLargeNT;
+      bufA[(idx & (C::TC - 1)) * C::RSP + pidx(idx >> C::LOG2TC)] = pre[q];
+    }
+    __syncthreads();
+    if (c + 1 < Q / C::TC) loadA(c + 1);
+    const float2* F = tfft<C::LOG2P, C::RSP, 1>(bufA, bufB, twP);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int idx = t + q * kLargeNT;
+      const int k1 = idx >> C::LOG2TC, f = idx & (C::TC - 1);
+      const int n2 = c * C::TC + f;
+      const float2 w = __ldg(tb.tw2L + ((n2 * k1) & (2 * L - 1)));
+      W[k1 * Q + n2] = cmul(F[f * C::RSP + pidx(k1)], w);
+    }
+    __syncthreads();
+  }
+  // pass B: row FFTs, the first Q/2 outputs of each row are S_k = (i/2) Z_k, k = k1 + P k2.
+  // (W is complete: every thread is past the barrier after the last pass-A store, and global
+  // writes of the block are visible to it after __syncthreads.)
+  auto loadB = [&](int r) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int idx = t + q * kLargeNT;
+      pre[q] = W[(r * C::TR + (idx >> C::LOG2Q)) * Q + (idx & (Q - 1))];
+    }
+  };
+  loadB(0);
+  for (int r = 0; r < P / C::TR; ++r) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int idx = t + q * kLargeNT;
+      bufA[(idx >> C::LOG2Q) * C::RSQ + pidx(idx & (Q - 1))] = pre[q];
+    }
+    __syncthreads();
+    if (r + 1 < P / C::TR) loadB(r + 1);
+    const float2* F = tfft<C::LOG2Q, C::RSQ, 1>(bufA, bufB, twQ);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = t + q * kLargeNT;
+      const int k2 = idx >> C::LOG2TR, f = idx & (C::TR - 1);
+      const int k = r * C::TR + f + P * k2;
+      const float2 zk = F[f * C::RSQ + pidx(k2)];
+      snk(k, (k == 0) ? make_float2(0.f, 0.f) : make_float2(-0.5f * zk.y, 0.5f * zk.x));
+    }
+    __syncthreads();
+  }
+}
+
+// sources (depth or spectral values the transform reads) and sinks (where its outputs go)
+struct SrcArr {  // x_m = a[m]
+  const float2* a;
+  __device__ __forceinline__ float2 operator()(int m, bool) const { return a[m]; }
+};
+struct SrcV {  // x_m = V_m a[m] (V real, or V + i Vi)
+  const float2* a;
+  const float* V;
+  const float* Vi;
+  __device__ __forceinline__ float2 operator()(int m, bool) const {
+    const float2 x = a[m];
+    return Vi ? cmul(make_float2(__ldg(V + m), __ldg(Vi + m)), x) : __ldg(V + m) * x;
+  }
+};
+struct SrcStage {  // x_m = t0_m = A_m y_m; on the first visit also t0[m] = x_m, acc[m] = 0
+  const float2* A;
+  const float2* y;
+  float2* t0;
+  float2* acc;
+  __device__ __forceinline__ float2 operator()(int m, bool first) const {
+    const float2 v = cmul(__ldg(A + m), y[m]);
+    if (first) {
+      t0[m] = v;
+      acc[m] = make_float2(0.f, 0.f);
+    }
+    return v;
+  }
+};
+struct SrcScaled {  // x_m = s y_m
+  const float2* y;
+  float s;
+  __device__ __forceinline__ float2 operator()(int m, bool) const { return s * y[m]; }
+};
+struct SnkArr {
+  float2* a;
+  __device__ __forceinline__ void operator()(int k, float2 v) { a[k] = v; }
+};
+struct SnkTerm {  // t_m = B_k S_k: acc += t_m, X = t_m, and the norm partials of the stop test
+  const float2* B;
+  const float2* t0;
+  float2* acc;
+  float2* X;
+  float nt, nw;
+  __device__ __forceinline__ void operator()(int k, float2 v) {
+    if (k == 0) {  // the zero mode: t_m = 0, acc[0] and t0[0] stay 0
+      X[0] = make_float2(0.f, 0.f);
+      return;
+    }
+    const float2 th = cmul(__ldg(B + k), v);
+    const float2 a = acc[k] + th;
+    acc[k] = a;
+    X[k] = th;
+    nt += cabs2(th);
+    nw += cabs2(t0[k] + a);
+  }
+};
+struct SnkTL {  // TL row: -10 log10 |u_n|^2 + 10 log10 r, n = 1..N
+  float* row;
+  float lr;
+  __device__ __forceinline__ void operator()(int k, float2 v) {
+    if (k >= 1) row[k - 1] = fmaf(-10.f, log10f(cabs2(v)), lr);
+  }
+};
 
 template <int LOG2L>
 __global__ void __launch_bounds__(kLargeNT, 1)
-    sssp_march_large_kernel(const SolveDesc* __restrict__ descs, const float2* __restrict__ tw_g,
-                            const float* __restrict__ sin_g) {
+    sssp_march_large_kernel(const SolveDesc* __restrict__ descs, const LargeTabs tb) {
   using C = CfgL<LOG2L>;
   constexpr int L = C::L;
+  extern __shared__ __align__(16) float2 tile_smem[];
   __shared__ SolveDesc d;
   __shared__ float red[2 * C::NW];
   const int t = threadIdx.x;
@@ -148,10 +291,9 @@ __global__ void __launch_bounds__(kLargeNT, 1)
   __syncthreads();
   float2* const y = d.yhat;
   float2* const X = d.work;
-  float2* const W1 = d.work + L;
-  float2* const W2 = d.work + 3 * L;
-  float2* const acc = d.work + 5 * L;
-  float2* const t0 = d.work + 6 * L;
+  float2* const W = d.work + L;
+  float2* const acc = d.work + 3 * L;
+  float2* const t0 = d.work + 4 * L;
   const float out_scale = 2.0f / float(L);
   const bool iso = d.terms <= 1;
   const float tol2f = float(d.tol2);
@@ -162,6 +304,12 @@ __global__ void __launch_bounds__(kLargeNT, 1)
   double next_r = (node + 1 < d.nodes) ? d.node_r[node + 1] : 1e300;
   const float* V = iso ? nullptr : d.V + (size_t)node * L;
   const float* Vi = (iso || d.Vi == nullptr) ? nullptr : d.Vi + (size_t)node * L;
+  if (t == 0) {  // the zero mode is never visited by the transform's source
+    acc[0] = make_float2(0.f, 0.f);
+    t0[0] = make_float2(0.f, 0.f);
+  }
+  load_large_twiddles<LOG2L>(tile_smem, tb);
+  __syncthreads();
 
   for (int s = 0; s < d.steps && status == kStatusOk; ++s) {
     if (iso) {
@@ -179,39 +327,19 @@ __global__ void __launch_bounds__(kLargeNT, 1)
         if (d.Vi != nullptr) Vi = d.Vi + (size_t)node * L;
       }
       for (int j = 0; j < d.p && status == kStatusOk; ++j) {
-        const float2* Aj = d.A + (size_t)j * L;
-        const float2* Bj = d.B + (size_t)j * L;
-        for (int q = 0; q < C::PER; ++q) {
-          const int i = t + q * kLargeNT;
-          const float2 v = cmul(__ldg(Aj + i), y[i]);
-          t0[i] = v;
-          X[i] = v;
-          acc[i] = make_float2(0.f, 0.f);
+        // t_0 = L_j^{-1} y in depth space; the source also sets t0 (spectral) and acc = 0
+        {
+          SnkArr sk{X};
+          dst_global<LOG2L>(W, tb, tile_smem, SrcStage{d.A + (size_t)j * L, y, t0, acc}, sk);
         }
-        __syncthreads();
-        dst_global<LOG2L>(X, W1, W2, tw_g, sin_g);  // t_0 in depth space
         ++ndst;
         float first = 0.f;
         for (int m = 1; m < d.terms; ++m) {
-          for (int q = 0; q < C::PER; ++q) {
-            const int i = t + q * kLargeNT;
-            X[i] = Vi ? cmul(make_float2(__ldg(V + i), __ldg(Vi + i)), X[i]) : __ldg(V + i) * X[i];
-          }
-          __syncthreads();
-          dst_global<LOG2L>(X, W1, W2, tw_g, sin_g);  // DST(V t_{m-1})
+          SnkTerm sk{d.B + (size_t)j * L, t0, acc, X, 0.f, 0.f};
+          dst_global<LOG2L>(W, tb, tile_smem, SrcV{X, V, Vi}, sk);  // B DST(V t_{m-1}), acc += t_m
           ++ndst;
-          float nt = 0.f, nw = 0.f;
-          for (int q = 0; q < C::PER; ++q) {
-            const int i = t + q * kLargeNT;
-            const float2 th = cmul(__ldg(Bj + i), X[i]);
-            const float2 a = acc[i] + th;
-            acc[i] = a;
-            X[i] = th;
-            nt += cabs2(th);
-            nw += cabs2(t0[i] + a);
-          }
-          const float snt = block_sum<LOG2L>(nt, red);
-          const float snw = block_sum<LOG2L>(nw, red + C::NW);
+          const float snt = block_sum<LOG2L>(sk.nt, red);
+          const float snw = block_sum<LOG2L>(sk.nw, red + C::NW);
           if (m == d.terms - 1) break;
           if (!isfinite(snt) || !isfinite(snw)) {
             status = kStatusNumeric;
@@ -223,12 +351,14 @@ __global__ void __launch_bounds__(kLargeNT, 1)
             break;
           }
           if (snt <= tol2f * snw) break;
-          dst_global<LOG2L>(X, W1, W2, tw_g, sin_g);  // t_m in depth space
+          SnkArr sx{X};
+          dst_global<LOG2L>(W, tb, tile_smem, SrcArr{X}, sx);  // t_m in depth space
           ++ndst;
         }
         {
           const float4* rp = d.R + (size_t)j * L;
           const float2 bj = d.beta[j];
+#pragma unroll 4
           for (int q = 0; q < C::PER; ++q) {
             const int i = t + q * kLargeNT;
             y[i] = ffmul(__ldg(rp + i), y[i]) + cmul(bj, acc[i]);
@@ -240,34 +370,17 @@ __global__ void __launch_bounds__(kLargeNT, 1)
     }
     const long long gs = d.step0 + s + 1;
     if (d.tl_every > 0 && gs % d.tl_every == 0) {
-      for (int q = 0; q < C::PER; ++q) {
-        const int i = t + q * kLargeNT;
-        X[i] = out_scale * y[i];
-      }
-      __syncthreads();
-      dst_global<LOG2L>(X, W1, W2, tw_g, sin_g);
-      ++ndst;
       const float lr = float(10.0 * log10(d.r0 + double(s + 1) * d.dr));
-      float* row = d.tl + (size_t)(d.rec0 + nrec) * d.N;
-      for (int q = 0; q < C::PER; ++q) {
-        const int n = t + q * kLargeNT;
-        if (n >= 1) row[n - 1] = fmaf(-10.f, log10f(cabs2(X[n])), lr);
-      }
+      SnkTL sk{d.tl + (size_t)(d.rec0 + nrec) * d.N, lr};
+      dst_global<LOG2L>(W, tb, tile_smem, SrcScaled{y, out_scale}, sk);
+      ++ndst;
       ++nrec;
-      __syncthreads();
     }
   }
-  // physical envelope for pe_read_field
-  for (int q = 0; q < C::PER; ++q) {
-    const int i = t + q * kLargeNT;
-    X[i] = out_scale * y[i];
-  }
-  __syncthreads();
-  dst_global<LOG2L>(X, W1, W2, tw_g, sin_g);
-  ++ndst;
-  for (int q = 0; q < C::PER; ++q) {
-    const int i = t + q * kLargeNT;
-    d.field[i] = X[i];
+  {  // physical envelope for pe_read_field
+    SnkArr sk{d.field};
+    dst_global<LOG2L>(W, tb, tile_smem, SrcScaled{y, out_scale}, sk);
+    ++ndst;
   }
   if (t == 0) {
     if (status != kStatusOk) atomicMax(d.status, status);
@@ -276,21 +389,29 @@ __global__ void __launch_bounds__(kLargeNT, 1)
 }
 
 // One DST-I of a large grid: out = scale * DST(in); in holds N values, out L values.
-// work: large_work_elems(L) float2 of scratch.
+// work: large_work_elems(L) float2 of scratch (2L used).
+struct SrcIn {  // x_m = in[m - 1]
+  const float2* in;
+  __device__ __forceinline__ float2 operator()(int m, bool) const { return in[m - 1]; }
+};
+struct SnkScaled {
+  float2* out;
+  float s;
+  __device__ __forceinline__ void operator()(int k, float2 v) { out[k] = s * v; }
+};
+
 template <int LOG2L>
 __global__ void __launch_bounds__(kLargeNT, 1)
     sssp_dst_large_kernel(const float2* __restrict__ in, float2* __restrict__ out, float scale, float2* work,
-                          const float2* __restrict__ tw_g, const float* __restrict__ sin_g, long long in_stride = 0,
-                          long long out_stride = 0) {
-  constexpr int L = 1 << LOG2L;
+                          const LargeTabs tb, long long in_stride = 0, long long out_stride = 0) {
+  extern __shared__ __align__(16) float2 tile_smem[];
   in += blockIdx.x * in_stride;
   out += blockIdx.x * out_stride;
-  work += blockIdx.x * (long long)large_work_elems(L);
-  float2* X = work;
-  for (int n = threadIdx.x; n < L; n += kLargeNT) X[n] = (n == 0) ? make_float2(0.f, 0.f) : in[n - 1];
+  work += blockIdx.x * (long long)large_work_elems(1 << LOG2L);
+  load_large_twiddles<LOG2L>(tile_smem, tb);
   __syncthreads();
-  dst_global<LOG2L>(X, work + L, work + 3 * L, tw_g, sin_g);
-  for (int n = threadIdx.x; n < L; n += kLargeNT) out[n] = scale * X[n];
+  SnkScaled sk{out, scale};
+  dst_global<LOG2L>(work, tb, tile_smem, SrcIn{in}, sk);
 }
 
 }  // namespace sssp

@@ -156,17 +156,63 @@ cudaError_t launch_dst_t(const float2* in, float2* out, float scale, const Trans
   return cudaGetLastError();
 }
 
+// tables of the two-pass large-grid transform on the current device (cached per size)
 template <int LOG2L>
-cudaError_t launch_march_large_t(const SolveDesc* dDescs, int count, const TransformTables& tabs, cudaStream_t st) {
-  sssp::sssp_march_large_kernel<LOG2L><<<count, sssp::kLargeNT, 0, st>>>(dDescs, tabs.tw, tabs.sinw);
+cudaError_t large_tabs(sssp::LargeTabs* out) {
+  using B = sssp::BigCfg<LOG2L>;
+  static std::mutex mu;
+  static std::map<int, sssp::LargeTabs> cache;  // device -> tables
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) {
+    *out = it->second;
+    return cudaSuccess;
+  }
+  TransformTables tp, tq;
+  if ((e = get_tables(dev, B::LOG2P, &tp)) != cudaSuccess) return e;
+  if ((e = get_tables(dev, B::LOG2Q, &tq)) != cudaSuccess) return e;
+  const int n2 = 2 * B::L;
+  std::vector<float2> w(n2);
+  for (int q = 0; q < n2; ++q) {
+    const double ang = -2.0 * M_PI * double(q) / double(n2);
+    w[q] = make_float2(float(std::cos(ang)), float(std::sin(ang)));
+  }
+  float2* d = nullptr;
+  if ((e = cudaMalloc(&d, sizeof(float2) * n2)) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(d, w.data(), sizeof(float2) * n2, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    cudaFree(d);
+    return e;
+  }
+  sssp::LargeTabs t{tp.tw, tq.tw, d};
+  cache[dev] = t;
+  *out = t;
+  if ((e = cudaFuncSetAttribute(sssp::sssp_march_large_kernel<LOG2L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(B::SMEM))) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(sssp::sssp_dst_large_kernel<LOG2L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(B::SMEM));
+}
+
+template <int LOG2L>
+cudaError_t launch_march_large_t(const SolveDesc* dDescs, int count, const TransformTables&, cudaStream_t st) {
+  sssp::LargeTabs tb;
+  cudaError_t e = large_tabs<LOG2L>(&tb);
+  if (e != cudaSuccess) return e;
+  sssp::sssp_march_large_kernel<LOG2L><<<count, sssp::kLargeNT, sssp::BigCfg<LOG2L>::SMEM, st>>>(dDescs, tb);
   return cudaGetLastError();
 }
 
 template <int LOG2L>
-cudaError_t launch_dst_large_t(const float2* in, float2* out, float scale, float2* work, const TransformTables& tabs,
+cudaError_t launch_dst_large_t(const float2* in, float2* out, float scale, float2* work, const TransformTables&,
                                cudaStream_t st, int count = 1, long long in_stride = 0, long long out_stride = 0) {
-  sssp::sssp_dst_large_kernel<LOG2L><<<count, sssp::kLargeNT, 0, st>>>(in, out, scale, work, tabs.tw, tabs.sinw,
-                                                                        in_stride, out_stride);
+  sssp::LargeTabs tb;
+  cudaError_t e = large_tabs<LOG2L>(&tb);
+  if (e != cudaSuccess) return e;
+  sssp::sssp_dst_large_kernel<LOG2L><<<count, sssp::kLargeNT, sssp::BigCfg<LOG2L>::SMEM, st>>>(
+      in, out, scale, work, tb, in_stride, out_stride);
   return cudaGetLastError();
 }
 

@@ -41,8 +41,9 @@ def _oracle(s, steps=None, tl_every=1, form="product"):
                    r0=s.r0, tl_every=tl_every, form=form)
 
 
-def _gpu(sssp, s, steps=None, tl_every=1):
+def _gpu(sssp, s, steps=None, tl_every=1, kernel="auto"):
     pl = sssp.plan_for(s, tl_every=tl_every)
+    pl.set_kernel(kernel)
     pl.march(steps or s.steps)
     u = pl.read_field()
     tl, rng = pl.read_tl()
@@ -163,19 +164,22 @@ def test_range_dependent_eddy(sssp):
     _compare(u, tl, ref)
 
 
-def test_munk_large_grid_short(sssp):
-    """Munk on N = 8191 (the global-workspace kernel), 100 Hz, [6/6], 12 terms, 8 steps."""
+@pytest.mark.parametrize("kernel", ["auto", "cta"])
+def test_munk_large_grid_short(sssp, kernel):
+    """Munk on N = 8191, 100 Hz, [6/6], 12 terms, 8 steps, on the cluster kernel (auto) and on
+    the one-CTA global-workspace kernel."""
     s = inputs.munk(N=8191, freq=100.0, dr=25.0, steps=8)
-    u, tl, _, _ = _gpu(sssp, s)
+    u, tl, _, _ = _gpu(sssp, s, kernel=kernel)
     ref = _oracle(s)
     _compare(u, tl, ref)
 
 
-def test_eddy_n16383_short(sssp):
+@pytest.mark.parametrize("kernel", ["auto", "cta"])
+def test_eddy_n16383_short(sssp, kernel):
     """The range-dependent workload's grid and Pade order (N = 16383, 250 Hz, [8/8], dr = 25 m,
-    profile node per step) for its first 3 steps against the oracle."""
+    profile node per step) for its first 3 steps against the oracle, on both kernels."""
     s = inputs.munk_eddy(steps=3)
-    u, tl, _, _ = _gpu(sssp, s)
+    u, tl, _, _ = _gpu(sssp, s, kernel=kernel)
     ref = _oracle(s)
     _compare(u, tl, ref)
 
