@@ -14,7 +14,9 @@
 namespace sssp {
 
 constexpr int kLargeNT = 512;
-constexpr int kLargeLog2Tile = 12;  // 8 points per thread per tile
+constexpr int kLargeLog2Tile = 13;  // points per tile (16 per thread)
+constexpr int kLargeTile = 1 << kLargeLog2Tile;
+constexpr int kLargePT = kLargeTile / kLargeNT;  // points per thread per tile
 constexpr int kLargeMinLog2 = 13;
 constexpr int kLargeMaxLog2 = 16;
 
@@ -58,16 +60,18 @@ struct LargeTabs {
 // n = Q n1 + n2, k = k1 + P k2:
 //   pass A (columns n2): Y[k1][n2] = w_{2L}^{n2 k1} sum_{n1} z_{Q n1 + n2} w_P^{n1 k1}
 //   pass B (rows k1):    Z_{k1 + P k2} = sum_{n2} Y[k1][n2] w_Q^{n2 k2},  only k2 < Q/2 kept.
-// Each pass moves tiles of 8192 points through shared memory (8 per thread), so a transform
-// reads and writes global memory twice: 56 B per point (the odd extension reads x twice).
+// z being odd, column Q - n2 is column n2 negated with its rows reversed, so only the columns
+// n2 in [0, Q/2] are transformed and stored (L + P values), and pass B rebuilds the rest of a
+// row from its partner row P - k1.  Each pass moves tiles of 8192 points through shared memory
+// (16 per thread); a transform reads x once, writes and reads the half intermediate once and
+// writes S once: 32 B per point, the two global passes of 16 B per point.
 template <int LOG2L>
 struct BigCfg {
   static constexpr int L = 1 << LOG2L;
   static constexpr int LOG2P = (LOG2L + 1) / 2;
   static constexpr int LOG2Q = LOG2L + 1 - LOG2P;
   static constexpr int P = 1 << LOG2P, Q = 1 << LOG2Q;
-  static constexpr int TILE = 8 * kLargeNT;
-  static_assert(TILE == (1 << kLargeLog2Tile), "tile size");
+  static constexpr int TILE = kLargeTile;
   static constexpr int LOG2TC = kLargeLog2Tile - LOG2P, LOG2TR = kLargeLog2Tile - LOG2Q;
   static constexpr int TC = 1 << LOG2TC, TR = 1 << LOG2TR;  // columns / rows per tile
   static constexpr int RSP = P + P / 16 + 1, RSQ = Q + Q / 16 + 1;  // padded FFT strides
@@ -81,7 +85,7 @@ struct BigCfg {
 template <int LOG2F, int RS, int RAD, int NS>
 __device__ __forceinline__ void tpass(const float2* __restrict__ src, float2* __restrict__ dst,
                                       const float2* __restrict__ tw) {  // tw in shared memory
-  constexpr int F = 1 << LOG2F, NB = F / RAD, PER = (8 * kLargeNT / RAD) / kLargeNT;
+  constexpr int F = 1 << LOG2F, NB = F / RAD, PER = (kLargeTile / RAD) / kLargeNT;
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int jb = threadIdx.x + q * kLargeNT;
@@ -134,77 +138,106 @@ __device__ __forceinline__ void load_large_twiddles(float2* sm, const LargeTabs&
 template <int LOG2L, class SRC, class SNK>
 __device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC& src, SNK& snk) {
   using C = BigCfg<LOG2L>;
-  constexpr int L = C::L, P = C::P, Q = C::Q;
+  constexpr int L = C::L, P = C::P, Q = C::Q, QH = Q / 2, QS = QH + 1;
+  constexpr int TC = C::TC, TR = C::TR, TRH = TR / 2;
+  constexpr int LOG2QH = C::LOG2Q - 1;
+  constexpr int NA = QH / TC + 1;  // pass-A tiles; the last ends at column Q/2 (overlap rewrites)
+  constexpr int NBT = P / TR + 1;  // pass-B tiles; the last holds row P/2
   const int t = threadIdx.x;
   float2* bufA = sm;
   float2* bufB = sm + C::BUF;
   const float2* twP = sm + 2 * C::BUF;  // copied by load_large_twiddles
   const float2* twQ = twP + P;
-  // The next tile's global loads are issued into registers before the current tile's FFT, so
-  // their latency hides behind the shared-memory passes.
-  float2 pre[8];
-  // pass A: column FFTs of the odd extension, twiddled, rows of W
+  constexpr int PT = kLargePT, PH = kLargePT / 2;
+  float2 pre[PT + 1];
+  // pass A: the P-point FFTs of the stored columns n2 in [0, Q/2], twiddled, into W[k1][n2]
   auto loadA = [&](int c) {
+    const int cb = c < NA - 1 ? c * TC : QH - TC + 1;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < PT; ++q) {
       const int idx = t + q * kLargeNT;
-      const int n1 = idx >> C::LOG2TC, f = idx & (C::TC - 1);
-      const int n = Q * n1 + c * C::TC + f;
+      const int n1 = idx >> C::LOG2TC, col = cb + (idx & (TC - 1));
+      const int n = Q * n1 + col;
       float2 z = make_float2(0.f, 0.f);
       if (n != 0 && n != L) {
-        const float2 x = n < L ? src(n, true) : src(2 * L - n, false);
+        // a point of a self-mirrored column (0, Q/2) is visited twice, the others once
+        const bool first = (n < L) || (col != 0 && col != QH);
+        const float2 x = n < L ? src(n, first) : src(2 * L - n, first);
         z = n < L ? x : make_float2(-x.x, -x.y);
       }
       pre[q] = z;
     }
   };
   loadA(0);
-  for (int c = 0; c < Q / C::TC; ++c) {
+  for (int c = 0; c < NA; ++c) {
+    const int cb = c < NA - 1 ? c * TC : QH - TC + 1;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < PT; ++q) {
       const int idx = t + q * kLargeNT;
-      bufA[(idx & (C::TC - 1)) * C::RSP + pidx(idx >> C::LOG2TC)] = pre[q];
+      bufA[(idx & (TC - 1)) * C::RSP + pidx(idx >> C::LOG2TC)] = pre[q];
     }
     __syncthreads();
-    if (c + 1 < Q / C::TC) loadA(c + 1);
+    if (c + 1 < NA) loadA(c + 1);
     const float2* F = tfft<C::LOG2P, C::RSP, 1>(bufA, bufB, twP);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < PT; ++q) {
       const int idx = t + q * kLargeNT;
-      const int k1 = idx >> C::LOG2TC, f = idx & (C::TC - 1);
-      const int n2 = c * C::TC + f;
-      const float2 w = __ldg(tb.tw2L + ((n2 * k1) & (2 * L - 1)));
-      W[k1 * Q + n2] = cmul(F[f * C::RSP + pidx(k1)], w);
+      const int k1 = idx >> C::LOG2TC, f = idx & (TC - 1);
+      const int col = cb + f;
+      const float2 w = __ldg(tb.tw2L + ((col * k1) & (2 * L - 1)));
+      W[k1 * QS + col] = cmul(F[f * C::RSP + pidx(k1)], w);
     }
     __syncthreads();
   }
-  // pass B: row FFTs, the first Q/2 outputs of each row are S_k = (i/2) Z_k, k = k1 + P k2.
-  // (W is complete: every thread is past the barrier after the last pass-A store, and global
-  // writes of the block are visible to it after __syncthreads.)
-  auto loadB = [&](int r) {
+  // pass B: rows in pairs (k, P - k); the odd symmetry of z gives the unstored half of a row
+  // from its partner: Y[k][Q - n] = -w_Q^{-n} Y[P - k][n] (k != 0), -Y[0][n] (k = 0).
+  // The first Q/2 outputs of each row are S_k' = (i/2) Z_k', k' = k + P k2.
+  auto rowof = [&](int tile, int s) {
+    const int own = (tile < NBT - 1 ? tile * TRH : P / 2 - TRH + 1) + (s & (TRH - 1));
+    return s < TRH ? own : ((P - own) & (P - 1));
+  };
+  auto loadB = [&](int tile) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < PH; ++q) {
       const int idx = t + q * kLargeNT;
-      pre[q] = W[(r * C::TR + (idx >> C::LOG2Q)) * Q + (idx & (Q - 1))];
+      pre[q] = W[rowof(tile, idx >> LOG2QH) * QS + (idx & (QH - 1))];
     }
+    if (t < TR) pre[PH] = W[rowof(tile, t) * QS + QH];
   };
   loadB(0);
-  for (int r = 0; r < P / C::TR; ++r) {
+  for (int tile = 0; tile < NBT; ++tile) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < PH; ++q) {
       const int idx = t + q * kLargeNT;
-      bufA[(idx >> C::LOG2Q) * C::RSQ + pidx(idx & (Q - 1))] = pre[q];
+      bufA[(idx >> LOG2QH) * C::RSQ + pidx(idx & (QH - 1))] = pre[q];
+    }
+    if (t < TR) bufA[t * C::RSQ + pidx(QH)] = pre[PH];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PH; ++q) {
+      const int idx = t + q * kLargeNT;
+      const int sl = idx >> LOG2QH, np = idx & (QH - 1);
+      if (np != 0) {
+        const float2 v = bufA[(sl ^ TRH) * C::RSQ + pidx(np)];
+        float2 r = make_float2(-v.x, -v.y);
+        if (rowof(tile, sl) != 0) r = cmul(r, conjf2(__ldg(tb.tw2L + P * np)));  // w_Q^{-np}
+        bufA[sl * C::RSQ + pidx(Q - np)] = r;
+      }
     }
     __syncthreads();
-    if (r + 1 < P / C::TR) loadB(r + 1);
+    if (tile + 1 < NBT) loadB(tile + 1);
     const float2* F = tfft<C::LOG2Q, C::RSQ, 1>(bufA, bufB, twQ);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < PH; ++q) {
       const int idx = t + q * kLargeNT;
-      const int k2 = idx >> C::LOG2TR, f = idx & (C::TR - 1);
-      const int k = r * C::TR + f + P * k2;
-      const float2 zk = F[f * C::RSQ + pidx(k2)];
-      snk(k, (k == 0) ? make_float2(0.f, 0.f) : make_float2(-0.5f * zk.y, 0.5f * zk.x));
+      const int k2 = idx >> C::LOG2TR, sl = idx & (TR - 1);
+      const int ownrow = rowof(tile, sl & (TRH - 1));
+      const bool emit = (tile < NBT - 1) ? (sl < TRH || ownrow != 0) : (sl < TRH && ownrow == P / 2);
+      if (emit) {
+        const int k = rowof(tile, sl) + P * k2;
+        const float2 zk = F[sl * C::RSQ + pidx(k2)];
+        snk(k, (k == 0) ? make_float2(0.f, 0.f) : make_float2(-0.5f * zk.y, 0.5f * zk.x));
+      }
     }
     __syncthreads();
   }
