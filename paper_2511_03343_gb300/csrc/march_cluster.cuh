@@ -16,8 +16,9 @@
 // FFT_L = local M-point FFTs of every residue row (4 per CTA: two rows, u and v), the twiddle
 // w_L^{r k1}, then for every k1 an R-point DFT across the residues:
 //   X[k1 + M k2] = sum_r w_R^{r k2} (w_L^{r k1} FFT_M(row r)[k1]).
-// CTA j owns k1 in [jQ, (j+1)Q), Q = M/NCTA, reads the R values it needs for those k1 from
-// the other CTAs' shared memory (the one all-to-all exchange of a transform) and keeps the
+// CTA j owns k1 in [jQ, (j+1)Q), Q = M/NCTA: the twiddled FFT outputs reach the CTA owning
+// their k1 (the one all-to-all exchange of a transform) either pushed by remote stores before
+// the barrier or pulled by remote loads after it (CCfg::PUSH); the owner keeps the
 // outputs k = k1 + M k2 < L/2 (k2 < R/2): spectral layout, thread (k1', e, h) owning
 // S_{2(k1 + M k2) + e} for k2 in [h R/4, (h+1) R/4).  The R-point DFT of a thread pair is
 // split by residue parity: thread h transforms the R/2 residues of parity h and the pair swaps
@@ -52,6 +53,9 @@ struct CCfg {
   static constexpr int PAD4 = P4 + P4 / 16;
   static constexpr int NW = NT / 32;
   static constexpr int DV = 2 * M / NT;   // depth points per thread in element-wise loops
+  // exchange by remote stores (push) or remote loads (pull): push measured faster from
+  // L = 8192 on (eddy N = 16383: 2.84 s against 3.12 s), pull at L = 4096 (312 ms against 320 ms)
+  static constexpr bool PUSH = LOG2L >= 13;
   // bufA, bufB, E0, E1 (padded) | X, wL rows, c rows (2M each) | twM (M) | wR (H) | part (4)
   // | V rows (2M floats) | red (2 NW floats)
   static constexpr size_t SMEM =
@@ -174,13 +178,24 @@ struct StBuf {
   float2* dst;
   __device__ __forceinline__ void operator()(int f, int o, float2 v) const { dst[pidx(f * M + o)] = v; }
 };
-// last forward pass: twiddle w_L^{r k1} of the row, into the exchange area
-template <int M>
+// last forward pass: twiddle w_L^{r k1} of the row, pushed into the exchange area of the CTA
+// that owns k1, at ((2 r + e) Q + k1 - its first k1)
+// (pull: into this CTA's own area at (f M + k1), read by the owner of k1 after the barrier)
+template <int LOG2L, int NCTA>
 struct StExch {
-  float2* E;
+  float2* E;  // this CTA's exchange area (mapped to the owner per store when pushing)
   const float2* wLs;
+  int j;
   __device__ __forceinline__ void operator()(int f, int o, float2 v) const {
-    E[pidx(f * M + o)] = cmul(v, wLs[(f >> 1) * M + o]);
+    using C = CCfg<LOG2L, NCTA>;
+    const float2 w = cmul(v, wLs[(f >> 1) * C::M + o]);
+    if constexpr (C::PUSH) {
+      const int r = res_of<NCTA>(j, f >> 1);
+      float2* Eo = cooperative_groups::this_cluster().map_shared_rank(E, o >> C::LOG2Q);
+      Eo[pidx((2 * r + (f & 1)) * C::Q + (o & (C::Q - 1)))] = w;
+    } else {
+      E[pidx(f * C::M + o)] = w;
+    }
   }
 };
 
@@ -231,21 +246,25 @@ struct LdPre {
   }
 };
 
-// Inverse first pass: the exchange values of residue row `row`, term e, from the CTA that
-// owns k1, times w_L^{r k1}.
+// Inverse first pass: the values the other CTAs pushed for residue row f >> 1, term f & 1, at
+// (f M + k1) of this CTA's exchange area, times w_L^{r k1}.
+// (pull: read from the area of the CTA owning k1, at ((2 r + e) Q + k1 - its first k1))
 template <int LOG2L, int NCTA>
-struct LdRemote {
-  const float2* E;  // this CTA's exchange area (mapped to the owner per load)
+struct LdExch {
+  const float2* E;
   const float2* wLs;
   int j;
   __device__ __forceinline__ float2 operator()(int f, int k1) const {
     using C = CCfg<LOG2L, NCTA>;
-    const int row = f >> 1, e = f & 1;
-    const int r = res_of<NCTA>(j, row);
-    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
-    const float2* Eo = cl.map_shared_rank(E, k1 >> C::LOG2Q);
-    const float2 z = Eo[pidx((2 * r + e) * C::Q + (k1 & (C::Q - 1)))];
-    return cmul(z, wLs[row * C::M + k1]);
+    float2 z;
+    if constexpr (C::PUSH) {
+      z = E[pidx(f * C::M + k1)];
+    } else {
+      const int r = res_of<NCTA>(j, f >> 1);
+      const float2* Eo = cooperative_groups::this_cluster().map_shared_rank(E, k1 >> C::LOG2Q);
+      z = Eo[pidx((2 * r + (f & 1)) * C::Q + (k1 & (C::Q - 1)))];
+    }
+    return cmul(z, wLs[(f >> 1) * C::M + k1]);
   }
 };
 
@@ -277,18 +296,21 @@ __device__ __forceinline__ void cdst_fwd(CSmem<LOG2L, NCTA>& sm, int j, const Sp
   cpass<C::LOG2M, C::NT, 8, 1>(LdPre<LOG2L, NCTA, WITHV, CPLX>{sm.X, sm.Vs, sm.Vis, sm.cs, j}, StBuf<M>{sm.bufA},
                               sm.twM);
   __syncthreads();
-  cfft_rest<C::LOG2M, C::NT, 8>(sm.bufA, sm.bufB, sm.twM, StExch<M>{E, sm.wLs});
-  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
-  cl.sync();
+  cfft_rest<C::LOG2M, C::NT, 8>(sm.bufA, sm.bufB, sm.twM, StExch<LOG2L, NCTA>{E, sm.wLs, j});
+  cooperative_groups::this_cluster().sync();  // the pushed values are visible after it
   ++ph;
   // R-point DFT across residues, split by residue parity over the thread pair (h = 0, 1)
   float2 D[C::H];
+  const int k1l = sp.k1 & (C::Q - 1);
 #pragma unroll
   for (int s = 0; s < C::H; ++s) {
-    int own, row;
-    owner_of<NCTA>(2 * s + sp.h, own, row);
-    const float2* Eo = cl.map_shared_rank(E, own);
-    D[s] = Eo[pidx((2 * row + sp.e) * M + sp.k1)];
+    if constexpr (C::PUSH) {
+      D[s] = E[pidx((2 * (2 * s + sp.h) + sp.e) * C::Q + k1l)];
+    } else {
+      int own, row;
+      owner_of<NCTA>(2 * s + sp.h, own, row);
+      D[s] = cooperative_groups::this_cluster().map_shared_rank(E, own)[pidx((2 * row + sp.e) * M + sp.k1)];
+    }
   }
   dftN<C::H>(D);
   if (sp.h) {
@@ -329,10 +351,21 @@ __device__ __forceinline__ void cdst_inv_begin(CSmem<LOG2L, NCTA>& sm, const Spe
     for (int s = 1; s < C::H; ++s) W[s] = cmul(W[s], sm.wR[s]);
   }
   dftN<C::H>(W);
+  // push Z_r[k1] to the CTA holding residue r, at ((2 row + e) M + k1); or keep it here at
+  // ((2 r + e) Q + k1') for that CTA to pull
+  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
   const int k1l = sp.k1 & (C::Q - 1);
 #pragma unroll
-  for (int s = 0; s < C::H; ++s) E[pidx((2 * (2 * s + sp.h) + sp.e) * C::Q + k1l)] = W[s];
-  cooperative_groups::this_cluster().sync();
+  for (int s = 0; s < C::H; ++s) {
+    if constexpr (C::PUSH) {
+      int own, row;
+      owner_of<NCTA>(2 * s + sp.h, own, row);
+      cl.map_shared_rank(E, own)[pidx((2 * row + sp.e) * C::M + sp.k1)] = W[s];
+    } else {
+      E[pidx((2 * (2 * s + sp.h) + sp.e) * C::Q + k1l)] = W[s];
+    }
+  }
+  cl.sync();
   ++ph;
 }
 
@@ -343,7 +376,7 @@ __device__ __forceinline__ void cdst_inv_end(CSmem<LOG2L, NCTA>& sm, int j, int 
                                              float lr) {
   using C = CCfg<LOG2L, NCTA>;
   constexpr int M = C::M;
-  cpass<C::LOG2M, C::NT, 8, 1>(LdRemote<LOG2L, NCTA>{sm.E[(ph - 1) & 1], sm.wLs, j}, StBuf<M>{sm.bufA}, sm.twM);
+  cpass<C::LOG2M, C::NT, 8, 1>(LdExch<LOG2L, NCTA>{sm.E[(ph - 1) & 1], sm.wLs, j}, StBuf<M>{sm.bufA}, sm.twM);
   __syncthreads();
   constexpr bool inA = CPasses<C::LOG2M>::LAST_IN_A;
   float2* F = inA ? sm.bufA : sm.bufB;
