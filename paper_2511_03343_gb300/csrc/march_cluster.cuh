@@ -56,10 +56,10 @@ struct CCfg {
   // exchange by remote stores (push) or remote loads (pull): push measured faster from
   // L = 8192 on (eddy N = 16383: 2.84 s against 3.12 s), pull at L = 4096 (312 ms against 320 ms)
   static constexpr bool PUSH = LOG2L >= 13;
-  // bufA, bufB, E0, E1 (padded) | X, wL rows, c rows (2M each) | twM (M) | wR (H) | part (4)
-  // | V rows (2M floats) | red (2 NW floats)
+  // bufA, bufB, E0, E1 (padded) | X, wL rows, c rows (2M each) | twM (M) | wR (H)
+  // | part (2 parities x NCTA CTA partials of the stop test) | V rows (2M floats) | red (2 NW)
   static constexpr size_t SMEM =
-      sizeof(float2) * (4 * size_t(PAD4) + 6 * M + M + H + 4) + sizeof(float) * (2 * M + 2 * NW);
+      sizeof(float2) * (4 * size_t(PAD4) + 6 * M + M + H + 2 * NCTA) + sizeof(float) * (2 * M + 2 * NW);
   static constexpr size_t SMEM_CPLX = SMEM + sizeof(float) * 2 * M;
   static_assert(NCTA == 8 || NCTA == 16, "cluster of 8 or 16 CTAs");
   static_assert(NT >= 32 && NT % 32 == 0 && M >= 64, "grid too small for this cluster");
@@ -81,7 +81,7 @@ struct CSmem {
     twM = cs + 2 * C::M;
     wR = twM + C::M;
     part = wR + C::H;
-    Vs = reinterpret_cast<float*>(part + 4);
+    Vs = reinterpret_cast<float*>(part + 2 * NCTA);
     red = Vs + 2 * C::M;
     Vis = red + 2 * C::NW;  // complex-profile kernel only
   }
@@ -539,19 +539,19 @@ __global__ void __launch_bounds__(CCfg<LOG2L, NCTA>::NT, 1)
             sm.red[2 * warp + 1] = nw;
           }
           __syncthreads();
-          if (t == 0) {
+          const int pbase = (ph & 1) * NCTA;
+          if (warp == 0) {  // the CTA total, pushed by lane c into slot j of CTA c
             float a = 0.f, b = 0.f;
             for (int w = 0; w < C::NW; ++w) {
               a += sm.red[2 * w];
               b += sm.red[2 * w + 1];
             }
-            sm.part[2 * (ph & 1)] = make_float2(a, b);
+            if (lane < NCTA) cl.map_shared_rank(sm.part, lane)[pbase + j] = make_float2(a, b);
           }
-          const int pslot = ph & 1;
           cdst_inv_begin<LOG2L, NCTA>(sm, sp, ph, tp);  // (its cluster barrier publishes part)
           float snt = 0.f, snw = 0.f;
           for (int c = 0; c < NCTA; ++c) {
-            const float2 pc = cl.map_shared_rank(sm.part, c)[2 * pslot];
+            const float2 pc = sm.part[pbase + c];
             snt += pc.x;
             snw += pc.y;
           }
