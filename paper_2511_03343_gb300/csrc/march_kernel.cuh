@@ -128,9 +128,38 @@ __device__ __forceinline__ void dft8(float2 (&v)[8]) {
   v[1] = b0; v[3] = b1; v[5] = b2; v[7] = b3;
 }
 
+// forward DFT of length 16 in natural order (one radix-2 frequency split, two length-8 DFTs)
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+  float2 a[8], b[8];
+  // w16^r = e^{-2 pi i r/16}
+  const float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f, h = 0.70710678118654752440f;
+  const float2 w[8] = {make_float2(1.f, 0.f), make_float2(c1, -s1), make_float2(h, -h), make_float2(s1, -c1),
+                       make_float2(0.f, -1.f), make_float2(-s1, -c1), make_float2(-h, -h), make_float2(-c1, -s1)};
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    a[r] = v[r] + v[r + 8];
+    b[r] = cmul(v[r] - v[r + 8], w[r]);
+  }
+  dft8(a);
+  dft8(b);
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    v[2 * r] = a[r];
+    v[2 * r + 1] = b[r];
+  }
+}
+
+
+template <int N>
+__device__ __forceinline__ void dftN(float2 (&v)[N]) {
+  if constexpr (N == 16) dft16(v);
+  else dft8(v);
+}
+
 template <int R>
 __device__ __forceinline__ void dftR(float2 (&v)[R]) {
-  if constexpr (R == 8) dft8(v);
+  if constexpr (R == 16) dft16(v);
+  else if constexpr (R == 8) dft8(v);
   else if constexpr (R == 4) dft4(v[0], v[1], v[2], v[3]);
   else dft2(v[0], v[1]);
 }

@@ -80,8 +80,19 @@ struct BigCfg {
   static constexpr size_t SMEM = sizeof(float2) * (2 * size_t(BUF) + P + Q);
 };
 
-// One Stockham pass (radix RAD, span NS) over NF = 8192 / 2^LOG2F independent FFTs of length
-// 2^LOG2F, FFT f at shared offset f RS (padded index inside).
+// Tile FFTs use radix-16 Stockham passes (radix min(16, F/NS) at span NS), one butterfly of 16
+// points per thread.  Twiddles of the pass at span NS > 1: entry off(NS) + (r - 1) NS + k holds
+// w^{r k / (NS RAD)}, off(NS) the entries of the earlier passes (the first pass needs none).
+__host__ __device__ constexpr int large_rad(int F, int ns) { return (F / ns) >= 16 ? 16 : (F / ns); }
+__host__ __device__ constexpr int large_twoff(int F, int NS) {
+  int off = 0;
+  for (int ns = 1; ns < NS; ns *= large_rad(F, ns))
+    if (ns > 1) off += (large_rad(F, ns) - 1) * ns;
+  return off;
+}
+
+// One Stockham pass (radix RAD, span NS) over the tile's independent FFTs of length 2^LOG2F,
+// FFT f at shared offset f RS (padded index inside).
 template <int LOG2F, int RS, int RAD, int NS>
 __device__ __forceinline__ void tpass(const float2* __restrict__ src, float2* __restrict__ dst,
                                       const float2* __restrict__ tw) {  // tw in shared memory
@@ -96,8 +107,9 @@ __device__ __forceinline__ void tpass(const float2* __restrict__ src, float2* __
     for (int r = 0; r < RAD; ++r) v[r] = s[pidx(jj + r * NB)];
     const int k = jj & (NS - 1);
     if constexpr (NS > 1) {
+      constexpr int OFF = large_twoff(F, NS);
 #pragma unroll
-      for (int r = 1; r < RAD; ++r) v[r] = cmul(v[r], tw[NS - 8 + (r - 1) * NS + k]);
+      for (int r = 1; r < RAD; ++r) v[r] = cmul(v[r], tw[OFF + (r - 1) * NS + k]);
     }
     dftR<RAD>(v);
     float2* d = dst + f * RS;
@@ -114,7 +126,7 @@ __device__ __forceinline__ float2* tfft(float2* src, float2* dst, const float2* 
   if constexpr (NS >= F) {
     return src;
   } else {
-    constexpr int RAD = (F / NS) >= 8 ? 8 : (F / NS);
+    constexpr int RAD = large_rad(F, NS);
     tpass<LOG2F, RS, RAD, NS>(src, dst, tw);
     __syncthreads();
     return tfft<LOG2F, RS, NS * RAD>(dst, src, tw);

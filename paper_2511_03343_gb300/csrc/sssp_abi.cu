@@ -171,22 +171,34 @@ cudaError_t large_tabs(sssp::LargeTabs* out) {
     *out = it->second;
     return cudaSuccess;
   }
-  TransformTables tp, tq;
-  if ((e = get_tables(dev, B::LOG2P, &tp)) != cudaSuccess) return e;
-  if ((e = get_tables(dev, B::LOG2Q, &tq)) != cudaSuccess) return e;
+  // per-pass twiddles of the radix-16 tile FFTs (P and Q points), then w_{2L}^q
+  auto passes = [](int F) {
+    std::vector<float2> tw(F, make_float2(0.f, 0.f));
+    for (int ns = 1; ns < F; ns *= sssp::large_rad(F, ns)) {
+      if (ns == 1) continue;
+      const int rad = sssp::large_rad(F, ns), off = sssp::large_twoff(F, ns);
+      for (int r = 1; r < rad; ++r)
+        for (int k = 0; k < ns; ++k) {
+          const double ang = -2.0 * M_PI * double(r) * double(k) / (double(ns) * double(rad));
+          tw[off + (r - 1) * ns + k] = make_float2(float(std::cos(ang)), float(std::sin(ang)));
+        }
+    }
+    return tw;
+  };
   const int n2 = 2 * B::L;
-  std::vector<float2> w(n2);
+  std::vector<float2> all = passes(B::P), tq = passes(B::Q);
+  all.insert(all.end(), tq.begin(), tq.end());
   for (int q = 0; q < n2; ++q) {
     const double ang = -2.0 * M_PI * double(q) / double(n2);
-    w[q] = make_float2(float(std::cos(ang)), float(std::sin(ang)));
+    all.push_back(make_float2(float(std::cos(ang)), float(std::sin(ang))));
   }
   float2* d = nullptr;
-  if ((e = cudaMalloc(&d, sizeof(float2) * n2)) != cudaSuccess) return e;
-  if ((e = cudaMemcpy(d, w.data(), sizeof(float2) * n2, cudaMemcpyHostToDevice)) != cudaSuccess) {
+  if ((e = cudaMalloc(&d, sizeof(float2) * all.size())) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(d, all.data(), sizeof(float2) * all.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
     cudaFree(d);
     return e;
   }
-  sssp::LargeTabs t{tp.tw, tq.tw, d};
+  sssp::LargeTabs t{d, d + B::P, d + B::P + B::Q};
   cache[dev] = t;
   *out = t;
   if ((e = cudaFuncSetAttribute(sssp::sssp_march_large_kernel<LOG2L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
