@@ -149,10 +149,25 @@ def sine_matrix(N: int) -> np.ndarray:
     return _SINE_CACHE[N]
 
 
+_DST_BACKEND = {"name": "matrix"}
+
+
+def set_dst_backend(name: str) -> None:
+    """'matrix' (default): the explicit sine sums below.  'fft': scipy.fft.dst(type=1), a library
+    routine for the same sums (its unnormalised DST-I is twice this one), for full-length runs
+    of the largest grids that the explicit sums cannot finish; pinned against 'matrix'."""
+    if name not in ("matrix", "fft"):
+        raise ValueError(name)
+    _DST_BACKEND["name"] = name
+
+
 def dst1(x: np.ndarray) -> np.ndarray:
     """DST-I along axis 0: X_m = sum_{n=1..N} x_n sin(pi n m/(N+1)), by the explicit sine sum."""
     x = np.asarray(x)
     N = x.shape[0]
+    if _DST_BACKEND["name"] == "fft":
+        import scipy.fft
+        return 0.5 * scipy.fft.dst(x, type=1, axis=0)
     if N <= 16383:
         S = sine_matrix(N)
         return S @ x.real + 1j * (S @ x.imag) if np.iscomplexobj(x) else S @ x

@@ -1,8 +1,16 @@
-"""Write the stored expected values of the full-size Munk workload (N = 4095, 2000 steps of
-50 m, [6/6] Pade, Neumann to 1e-10 or 12 terms, f = 50 Hz, source at 1000 m) by running the
-FP64 oracle only.  Output: munk_n4095_s2000.txt (sampled final field and TL rows).
+"""Write stored expected values of full-length workloads by running the FP64 oracle only.
 
-    python tests/golden/make_golden.py            # several minutes on a multi-core host
+    python tests/golden/make_golden.py            # Munk: N = 4095, 2000 steps of 50 m, [6/6],
+                                                  # Neumann to 1e-10 or 12 terms, f = 50 Hz
+                                                  # -> munk_n4095_s2000.txt (several minutes)
+    python tests/golden/make_golden.py eddy       # Munk + eddy: N = 16383, 4000 steps of 25 m,
+                                                  # [8/8], f = 250 Hz, a profile node per step
+                                                  # -> eddy_n16383_s4000.txt (product form)
+                                                  # and eddy_n16383_s4000_sum.txt (Algorithm 1's
+                                                  # sum form), with the oracle's library DST-I
+                                                  # backend; about 12 minutes each
+
+Each file holds the sampled final field and sampled TL rows.
 """
 import os
 import sys
@@ -64,5 +72,46 @@ def load(path=os.path.join(HERE, "munk_n4095_s2000.txt")):
     return meta, np.array(field_idx), np.array(field), np.array(tl_r), np.array(tl)
 
 
+EDDY_FIELD_STRIDE = 16
+EDDY_TL_EVERY = 400
+EDDY_TL_STRIDE = 64
+
+
+def main_eddy(path=None, form="product"):
+    """The 12-term Neumann series does not reach 1e-10 on this workload, so the product form
+    (the one the GPU marches) and the sum form are different approximations (1e-3 apart after
+    4000 steps, in FP64): both are written."""
+    if path is None:
+        path = os.path.join(HERE, "eddy_n16383_s4000.txt" if form == "product" else "eddy_n16383_s4000_sum.txt")
+    s = inputs.munk_eddy()
+    g = O.Grid(N=s.N, H=s.H, k0=s.k0, dr=s.dr)
+    O.set_dst_backend("fft")  # the explicit sums would take days at N = 16383 over 4000 steps
+    t0 = time.time()
+    res = O.march(s.u0, s.profiles, g, s.pade_order, s.steps, s.neumann_terms, s.neumann_tol,
+                  tl_every=EDDY_TL_EVERY, form=form)
+    el = time.time() - t0
+    O.set_dst_backend("matrix")
+    idx = np.arange(0, s.N, EDDY_FIELD_STRIDE)
+    tidx = np.arange(0, s.N, EDDY_TL_STRIDE)
+    with open(path, "w") as f:
+        f.write(f"# FP64 oracle ({form} form, library DST-I backend), written by "
+                "tests/golden/make_golden.py eddy\n")
+        f.write(f"# munk_eddy N={s.N} H={s.H} f={s.freq} dr={s.dr} steps={s.steps} p={s.pade_order} "
+                f"terms={s.neumann_terms} tol={s.neumann_tol} zs={s.zs} c0={s.c0} dc={s.eddy_dc:.17e} "
+                f"oracle_seconds={el:.1f}\n")
+        f.write(f"field_stride {EDDY_FIELD_STRIDE} tl_every {EDDY_TL_EVERY} tl_stride {EDDY_TL_STRIDE} "
+                f"norm {np.linalg.norm(res.u):.17e}\n")
+        f.write("field\n")
+        for i in idx:
+            f.write(f"{i} {res.u[i].real:.17e} {res.u[i].imag:.17e}\n")
+        f.write("tl\n")
+        for r, row in zip(res.tl_ranges, res.tl):
+            f.write(f"{r:.6f} " + " ".join(f"{row[i]:.10e}" for i in tidx) + "\n")
+    print("wrote", path, "in", round(el, 1), "s")
+
+
 if __name__ == "__main__":
-    main()
+    if len(sys.argv) > 1 and sys.argv[1] == "eddy":
+        main_eddy(form=sys.argv[2] if len(sys.argv) > 2 else "product")
+    else:
+        main()

@@ -603,3 +603,23 @@ def test_neumann_bound_bounds_a_varying_V_and_predicts_convergence():
     bound = rho ** 40 / (1 - rho) * np.linalg.norm(O.apply_Linv(np.repeat(u[:, None], 6, 1), plan.b, grid.lam), axis=0) \
         / np.linalg.norm(w80, axis=0)
     assert np.all(err <= bound * (1 + 1e-6) + 1e-15)
+
+
+@pytest.mark.parametrize("N", [7, 255, 1023, 4095])
+def test_fft_dst_backend_equals_the_sine_sums(N):
+    """The library DST-I backend (used for full-length runs of the largest grids) gives the
+    explicit sine sums, for vectors and for matrices of columns."""
+    rng = np.random.default_rng(N + 3)
+    x = rng.standard_normal((N, 3)) + 1j * rng.standard_normal((N, 3))
+    ref = O.dst1(x)
+    try:
+        O.set_dst_backend("fft")
+        got = O.dst1(x)
+        got1 = O.dst1(x[:, 0])
+    finally:
+        O.set_dst_backend("matrix")
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(got - ref)) <= 1e-12 * scale * math.log2(N + 1)
+    assert np.max(np.abs(got1 - ref[:, 0])) <= 1e-12 * scale * math.log2(N + 1)
+    with pytest.raises(ValueError):
+        O.set_dst_backend("cuda")
