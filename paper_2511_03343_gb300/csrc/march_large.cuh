@@ -48,11 +48,13 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
 }
 
 // Tables of the two-pass transform: per-pass Stockham twiddles of the P- and Q-point FFTs
-// and w_{2L}^q, q in [0, 2L).
+// and w_{2L}^q, q in [0, 2L), each as a hi + lo pair of floats (float-float): a twiddle's
+// FP32 representation error is the same in every transform, so it adds up coherently over
+// the range steps; with the lo part every twiddle product carries only its own rounding.
 struct LargeTabs {
-  const float2* twP;
-  const float2* twQ;
-  const float2* tw2L;
+  const float4* twP;
+  const float4* twQ;
+  const float4* tw2L;
 };
 
 // The DST-I of length N = L - 1 is the DFT of the odd extension z (length 2L: z_n = x_n,
@@ -76,8 +78,8 @@ struct BigCfg {
   static constexpr int TC = 1 << LOG2TC, TR = 1 << LOG2TR;  // columns / rows per tile
   static constexpr int RSP = P + P / 16 + 1, RSQ = Q + Q / 16 + 1;  // padded FFT strides
   static constexpr int BUF = (TC * RSP > TR * RSQ) ? TC * RSP : TR * RSQ;
-  // two tile buffers, then the P- and Q-point twiddle tables
-  static constexpr size_t SMEM = sizeof(float2) * (2 * size_t(BUF) + P + Q);
+  // two tile buffers, then the P- and Q-point twiddle tables (hi + lo)
+  static constexpr size_t SMEM = sizeof(float2) * 2 * size_t(BUF) + sizeof(float4) * (P + Q);
 };
 
 // Tile FFTs use radix-16 Stockham passes (radix min(16, F/NS) at span NS), one butterfly of 16
@@ -91,11 +93,60 @@ __host__ __device__ constexpr int large_twoff(int F, int NS) {
   return off;
 }
 
+// Butterflies whose irrational constants (cos and sin of pi/4, pi/8) are applied as hi + lo
+// pairs, for the same reason as the twiddle tables: a constant's FP32 error would repeat in
+// every transform.
+__device__ __forceinline__ float ff_mul(float hi, float lo, float s) { return fmaf(hi, s, lo * s); }
+__device__ __forceinline__ void dft8_ff(float2 (&v)[8]) {
+  constexpr double H = 0.70710678118654752440;
+  constexpr float hh = float(H), hl = float(H - double(float(H)));
+  float2 a0 = v[0] + v[4], a1 = v[1] + v[5], a2 = v[2] + v[6], a3 = v[3] + v[7];
+  float2 b0 = v[0] - v[4], b1 = v[1] - v[5], b2 = v[2] - v[6], b3 = v[3] - v[7];
+  b1 = make_float2(ff_mul(hh, hl, b1.x + b1.y), ff_mul(hh, hl, b1.y - b1.x));    // * e^{-i pi/4}
+  b2 = mul_negi(b2);                                                              // * e^{-i pi/2}
+  b3 = make_float2(ff_mul(hh, hl, b3.y - b3.x), -ff_mul(hh, hl, b3.x + b3.y));   // * e^{-3i pi/4}
+  dft4(a0, a1, a2, a3);
+  dft4(b0, b1, b2, b3);
+  v[0] = a0; v[2] = a1; v[4] = a2; v[6] = a3;
+  v[1] = b0; v[3] = b1; v[5] = b2; v[7] = b3;
+}
+__device__ __forceinline__ void dft16_ff(float2 (&v)[16]) {
+  constexpr double C1 = 0.92387953251128675613, S1 = 0.38268343236508977173, H = 0.70710678118654752440;
+  constexpr float c1h = float(C1), c1l = float(C1 - double(float(C1)));
+  constexpr float s1h = float(S1), s1l = float(S1 - double(float(S1)));
+  constexpr float hh = float(H), hl = float(H - double(float(H)));
+  // w16^r = e^{-2 pi i r/16}, r = 0..7, as hi + lo
+  const float4 w[8] = {make_float4(1.f, 0.f, 0.f, 0.f),     make_float4(c1h, -s1h, c1l, -s1l),
+                       make_float4(hh, -hh, hl, -hl),        make_float4(s1h, -c1h, s1l, -c1l),
+                       make_float4(0.f, -1.f, 0.f, 0.f),     make_float4(-s1h, -c1h, -s1l, -c1l),
+                       make_float4(-hh, -hh, -hl, -hl),      make_float4(-c1h, -s1h, -c1l, -s1l)};
+  float2 a[8], b[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    a[r] = v[r] + v[r + 8];
+    b[r] = (r == 0) ? v[r] - v[r + 8] : ffmul(w[r], v[r] - v[r + 8]);
+  }
+  dft8_ff(a);
+  dft8_ff(b);
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    v[2 * r] = a[r];
+    v[2 * r + 1] = b[r];
+  }
+}
+template <int R>
+__device__ __forceinline__ void dftR_ff(float2 (&v)[R]) {
+  if constexpr (R == 16) dft16_ff(v);
+  else if constexpr (R == 8) dft8_ff(v);
+  else if constexpr (R == 4) dft4(v[0], v[1], v[2], v[3]);
+  else dft2(v[0], v[1]);
+}
+
 // One Stockham pass (radix RAD, span NS) over the tile's independent FFTs of length 2^LOG2F,
 // FFT f at shared offset f RS (padded index inside).
 template <int LOG2F, int RS, int RAD, int NS>
 __device__ __forceinline__ void tpass(const float2* __restrict__ src, float2* __restrict__ dst,
-                                      const float2* __restrict__ tw) {  // tw in shared memory
+                                      const float4* __restrict__ tw) {  // tw in shared memory
   constexpr int F = 1 << LOG2F, NB = F / RAD, PER = (kLargeTile / RAD) / kLargeNT;
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
@@ -109,9 +160,9 @@ __device__ __forceinline__ void tpass(const float2* __restrict__ src, float2* __
     if constexpr (NS > 1) {
       constexpr int OFF = large_twoff(F, NS);
 #pragma unroll
-      for (int r = 1; r < RAD; ++r) v[r] = cmul(v[r], tw[OFF + (r - 1) * NS + k]);
+      for (int r = 1; r < RAD; ++r) v[r] = ffmul(tw[OFF + (r - 1) * NS + k], v[r]);
     }
-    dftR<RAD>(v);
+    dftR_ff<RAD>(v);
     float2* d = dst + f * RS;
     const int base = (jj - k) * RAD + k;
 #pragma unroll
@@ -121,7 +172,7 @@ __device__ __forceinline__ void tpass(const float2* __restrict__ src, float2* __
 
 // all passes of the tile's FFTs, src -> ...; returns the buffer holding the result
 template <int LOG2F, int RS, int NS>
-__device__ __forceinline__ float2* tfft(float2* src, float2* dst, const float2* tw) {
+__device__ __forceinline__ float2* tfft(float2* src, float2* dst, const float4* tw) {
   constexpr int F = 1 << LOG2F;
   if constexpr (NS >= F) {
     return src;
@@ -137,7 +188,7 @@ __device__ __forceinline__ float2* tfft(float2* src, float2* dst, const float2* 
 template <int LOG2L>
 __device__ __forceinline__ void load_large_twiddles(float2* sm, const LargeTabs& tb) {
   using C = BigCfg<LOG2L>;
-  float2* twP = sm + 2 * C::BUF;
+  float4* twP = reinterpret_cast<float4*>(sm + 2 * C::BUF);
   for (int i = threadIdx.x; i < C::P; i += kLargeNT) twP[i] = tb.twP[i];
   for (int i = threadIdx.x; i < C::Q; i += kLargeNT) twP[C::P + i] = tb.twQ[i];
 }
@@ -158,8 +209,8 @@ __device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC
   const int t = threadIdx.x;
   float2* bufA = sm;
   float2* bufB = sm + C::BUF;
-  const float2* twP = sm + 2 * C::BUF;  // copied by load_large_twiddles
-  const float2* twQ = twP + P;
+  const float4* twP = reinterpret_cast<const float4*>(sm + 2 * C::BUF);  // copied by load_large_twiddles
+  const float4* twQ = twP + P;
   constexpr int PT = kLargePT, PH = kLargePT / 2;
   float2 pre[PT + 1];
   // pass A: the P-point FFTs of the stored columns n2 in [0, Q/2], twiddled, into W[k1][n2]
@@ -196,8 +247,8 @@ __device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC
       const int idx = t + q * kLargeNT;
       const int k1 = idx >> C::LOG2TC, f = idx & (TC - 1);
       const int col = cb + f;
-      const float2 w = __ldg(tb.tw2L + ((col * k1) & (2 * L - 1)));
-      W[k1 * QS + col] = cmul(F[f * C::RSP + pidx(k1)], w);
+      const float4 w = __ldg(tb.tw2L + ((col * k1) & (2 * L - 1)));
+      W[k1 * QS + col] = ffmul(w, F[f * C::RSP + pidx(k1)]);
     }
     __syncthreads();
   }
@@ -232,7 +283,10 @@ __device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC
       if (np != 0) {
         const float2 v = bufA[(sl ^ TRH) * C::RSQ + pidx(np)];
         float2 r = make_float2(-v.x, -v.y);
-        if (rowof(tile, sl) != 0) r = cmul(r, conjf2(__ldg(tb.tw2L + P * np)));  // w_Q^{-np}
+        if (rowof(tile, sl) != 0) {  // times w_Q^{-np} = conj(w_{2L}^{P np})
+          const float4 w = __ldg(tb.tw2L + P * np);
+          r = ffmul(make_float4(w.x, -w.y, w.z, -w.w), r);
+        }
         bufA[sl * C::RSQ + pidx(Q - np)] = r;
       }
     }

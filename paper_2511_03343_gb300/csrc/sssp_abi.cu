@@ -171,30 +171,30 @@ cudaError_t large_tabs(sssp::LargeTabs* out) {
     *out = it->second;
     return cudaSuccess;
   }
-  // per-pass twiddles of the radix-16 tile FFTs (P and Q points), then w_{2L}^q
-  auto passes = [](int F) {
-    std::vector<float2> tw(F, make_float2(0.f, 0.f));
+  // per-pass twiddles of the radix-16 tile FFTs (P and Q points), then w_{2L}^q, all as hi + lo
+  auto ff = [](double ang) {
+    const double c = std::cos(ang), sn = std::sin(ang);
+    const float ch = float(c), sh = float(sn);
+    return make_float4(ch, sh, float(c - double(ch)), float(sn - double(sh)));
+  };
+  auto passes = [&](int F) {
+    std::vector<float4> tw(F, make_float4(0.f, 0.f, 0.f, 0.f));
     for (int ns = 1; ns < F; ns *= sssp::large_rad(F, ns)) {
       if (ns == 1) continue;
       const int rad = sssp::large_rad(F, ns), off = sssp::large_twoff(F, ns);
       for (int r = 1; r < rad; ++r)
-        for (int k = 0; k < ns; ++k) {
-          const double ang = -2.0 * M_PI * double(r) * double(k) / (double(ns) * double(rad));
-          tw[off + (r - 1) * ns + k] = make_float2(float(std::cos(ang)), float(std::sin(ang)));
-        }
+        for (int k = 0; k < ns; ++k)
+          tw[off + (r - 1) * ns + k] = ff(-2.0 * M_PI * double(r) * double(k) / (double(ns) * double(rad)));
     }
     return tw;
   };
   const int n2 = 2 * B::L;
-  std::vector<float2> all = passes(B::P), tq = passes(B::Q);
+  std::vector<float4> all = passes(B::P), tq = passes(B::Q);
   all.insert(all.end(), tq.begin(), tq.end());
-  for (int q = 0; q < n2; ++q) {
-    const double ang = -2.0 * M_PI * double(q) / double(n2);
-    all.push_back(make_float2(float(std::cos(ang)), float(std::sin(ang))));
-  }
-  float2* d = nullptr;
-  if ((e = cudaMalloc(&d, sizeof(float2) * all.size())) != cudaSuccess) return e;
-  if ((e = cudaMemcpy(d, all.data(), sizeof(float2) * all.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+  for (int q = 0; q < n2; ++q) all.push_back(ff(-2.0 * M_PI * double(q) / double(n2)));
+  float4* d = nullptr;
+  if ((e = cudaMalloc(&d, sizeof(float4) * all.size())) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(d, all.data(), sizeof(float4) * all.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
     cudaFree(d);
     return e;
   }

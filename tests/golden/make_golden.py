@@ -10,6 +10,11 @@
                                                   # sum form), with the oracle's library DST-I
                                                   # backend; about 12 minutes each
 
+    python tests/golden/make_golden.py large      # Munk: N = 65535, 500 Hz, 2000 steps of 25 m,
+                                                  # [6/6], 12 terms, product form
+                                                  # -> munk_n65535_s2000.txt (library DST-I
+                                                  # backend)
+
 Each file holds the sampled final field and sampled TL rows.
 """
 import os
@@ -110,8 +115,36 @@ def main_eddy(path=None, form="product"):
     print("wrote", path, "in", round(el, 1), "s")
 
 
+def main_large(path=os.path.join(HERE, "munk_n65535_s2000.txt")):
+    s = inputs.munk(N=65535, freq=500.0, dr=25.0, steps=2000)
+    g = O.Grid(N=s.N, H=s.H, k0=s.k0, dr=s.dr)
+    O.set_dst_backend("fft")
+    t0 = time.time()
+    res = O.march(s.u0, s.profiles, g, s.pade_order, s.steps, s.neumann_terms, s.neumann_tol,
+                  tl_every=200, form="product")
+    el = time.time() - t0
+    O.set_dst_backend("matrix")
+    idx = np.arange(0, s.N, 64)
+    tidx = np.arange(0, s.N, 256)
+    with open(path, "w") as f:
+        f.write("# FP64 oracle (product form, library DST-I backend), written by "
+                "tests/golden/make_golden.py large\n")
+        f.write(f"# munk N={s.N} H={s.H} f={s.freq} dr={s.dr} steps={s.steps} p={s.pade_order} "
+                f"terms={s.neumann_terms} tol={s.neumann_tol} zs={s.zs} c0={s.c0} oracle_seconds={el:.1f}\n")
+        f.write(f"field_stride 64 tl_every 200 tl_stride 256 norm {np.linalg.norm(res.u):.17e}\n")
+        f.write("field\n")
+        for i in idx:
+            f.write(f"{i} {res.u[i].real:.17e} {res.u[i].imag:.17e}\n")
+        f.write("tl\n")
+        for r, row in zip(res.tl_ranges, res.tl):
+            f.write(f"{r:.6f} " + " ".join(f"{row[i]:.10e}" for i in tidx) + "\n")
+    print("wrote", path, "in", round(el, 1), "s")
+
+
 if __name__ == "__main__":
-    if len(sys.argv) > 1 and sys.argv[1] == "eddy":
+    if len(sys.argv) > 1 and sys.argv[1] == "large":
+        main_large()
+    elif len(sys.argv) > 1 and sys.argv[1] == "eddy":
         main_eddy(form=sys.argv[2] if len(sys.argv) > 2 else "product")
     else:
         main()
