@@ -114,14 +114,20 @@ __device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2&
   x1 = d0 + d1;
   x3 = d0 - d1;
 }
+// Irrational butterfly constants (cos and sin of pi/4, pi/8) are applied as hi + lo float
+// pairs: a constant's FP32 representation error (up to 3e-8 relative) would be the same in
+// every transform and add up coherently over thousands of range steps.
+__device__ __forceinline__ float ff_mul(float hi, float lo, float s) { return fmaf(hi, s, lo * s); }
+
 // forward DFT of length 8 (one radix-2 frequency split, then two length-4 DFTs)
 __device__ __forceinline__ void dft8(float2 (&v)[8]) {
-  const float h = 0.70710678118654752440f;
+  constexpr double H = 0.70710678118654752440;
+  constexpr float hh = float(H), hl = float(H - double(float(H)));
   float2 a0 = v[0] + v[4], a1 = v[1] + v[5], a2 = v[2] + v[6], a3 = v[3] + v[7];
   float2 b0 = v[0] - v[4], b1 = v[1] - v[5], b2 = v[2] - v[6], b3 = v[3] - v[7];
-  b1 = make_float2(h * (b1.x + b1.y), h * (b1.y - b1.x));     // * e^{-i pi/4}
-  b2 = mul_negi(b2);                                           // * e^{-i pi/2}
-  b3 = make_float2(h * (b3.y - b3.x), -h * (b3.x + b3.y));    // * e^{-3i pi/4}
+  b1 = make_float2(ff_mul(hh, hl, b1.x + b1.y), ff_mul(hh, hl, b1.y - b1.x));    // * e^{-i pi/4}
+  b2 = mul_negi(b2);                                                              // * e^{-i pi/2}
+  b3 = make_float2(ff_mul(hh, hl, b3.y - b3.x), -ff_mul(hh, hl, b3.x + b3.y));   // * e^{-3i pi/4}
   dft4(a0, a1, a2, a3);
   dft4(b0, b1, b2, b3);
   v[0] = a0; v[2] = a1; v[4] = a2; v[6] = a3;
@@ -130,15 +136,20 @@ __device__ __forceinline__ void dft8(float2 (&v)[8]) {
 
 // forward DFT of length 16 in natural order (one radix-2 frequency split, two length-8 DFTs)
 __device__ __forceinline__ void dft16(float2 (&v)[16]) {
+  constexpr double C1 = 0.92387953251128675613, S1 = 0.38268343236508977173, H = 0.70710678118654752440;
+  constexpr float c1h = float(C1), c1l = float(C1 - double(float(C1)));
+  constexpr float s1h = float(S1), s1l = float(S1 - double(float(S1)));
+  constexpr float hh = float(H), hl = float(H - double(float(H)));
+  // w16^r = e^{-2 pi i r/16}, r = 0..7, as hi + lo
+  const float4 w[8] = {make_float4(1.f, 0.f, 0.f, 0.f),     make_float4(c1h, -s1h, c1l, -s1l),
+                       make_float4(hh, -hh, hl, -hl),        make_float4(s1h, -c1h, s1l, -c1l),
+                       make_float4(0.f, -1.f, 0.f, 0.f),     make_float4(-s1h, -c1h, -s1l, -c1l),
+                       make_float4(-hh, -hh, -hl, -hl),      make_float4(-c1h, -s1h, -c1l, -s1l)};
   float2 a[8], b[8];
-  // w16^r = e^{-2 pi i r/16}
-  const float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f, h = 0.70710678118654752440f;
-  const float2 w[8] = {make_float2(1.f, 0.f), make_float2(c1, -s1), make_float2(h, -h), make_float2(s1, -c1),
-                       make_float2(0.f, -1.f), make_float2(-s1, -c1), make_float2(-h, -h), make_float2(-c1, -s1)};
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     a[r] = v[r] + v[r + 8];
-    b[r] = cmul(v[r] - v[r + 8], w[r]);
+    b[r] = (r == 0) ? v[r] - v[r + 8] : ffmul(w[r], v[r] - v[r + 8]);
   }
   dft8(a);
   dft8(b);
@@ -148,7 +159,6 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
     v[2 * r + 1] = b[r];
   }
 }
-
 
 template <int N>
 __device__ __forceinline__ void dftN(float2 (&v)[N]) {

@@ -93,55 +93,6 @@ __host__ __device__ constexpr int large_twoff(int F, int NS) {
   return off;
 }
 
-// Butterflies whose irrational constants (cos and sin of pi/4, pi/8) are applied as hi + lo
-// pairs, for the same reason as the twiddle tables: a constant's FP32 error would repeat in
-// every transform.
-__device__ __forceinline__ float ff_mul(float hi, float lo, float s) { return fmaf(hi, s, lo * s); }
-__device__ __forceinline__ void dft8_ff(float2 (&v)[8]) {
-  constexpr double H = 0.70710678118654752440;
-  constexpr float hh = float(H), hl = float(H - double(float(H)));
-  float2 a0 = v[0] + v[4], a1 = v[1] + v[5], a2 = v[2] + v[6], a3 = v[3] + v[7];
-  float2 b0 = v[0] - v[4], b1 = v[1] - v[5], b2 = v[2] - v[6], b3 = v[3] - v[7];
-  b1 = make_float2(ff_mul(hh, hl, b1.x + b1.y), ff_mul(hh, hl, b1.y - b1.x));    // * e^{-i pi/4}
-  b2 = mul_negi(b2);                                                              // * e^{-i pi/2}
-  b3 = make_float2(ff_mul(hh, hl, b3.y - b3.x), -ff_mul(hh, hl, b3.x + b3.y));   // * e^{-3i pi/4}
-  dft4(a0, a1, a2, a3);
-  dft4(b0, b1, b2, b3);
-  v[0] = a0; v[2] = a1; v[4] = a2; v[6] = a3;
-  v[1] = b0; v[3] = b1; v[5] = b2; v[7] = b3;
-}
-__device__ __forceinline__ void dft16_ff(float2 (&v)[16]) {
-  constexpr double C1 = 0.92387953251128675613, S1 = 0.38268343236508977173, H = 0.70710678118654752440;
-  constexpr float c1h = float(C1), c1l = float(C1 - double(float(C1)));
-  constexpr float s1h = float(S1), s1l = float(S1 - double(float(S1)));
-  constexpr float hh = float(H), hl = float(H - double(float(H)));
-  // w16^r = e^{-2 pi i r/16}, r = 0..7, as hi + lo
-  const float4 w[8] = {make_float4(1.f, 0.f, 0.f, 0.f),     make_float4(c1h, -s1h, c1l, -s1l),
-                       make_float4(hh, -hh, hl, -hl),        make_float4(s1h, -c1h, s1l, -c1l),
-                       make_float4(0.f, -1.f, 0.f, 0.f),     make_float4(-s1h, -c1h, -s1l, -c1l),
-                       make_float4(-hh, -hh, -hl, -hl),      make_float4(-c1h, -s1h, -c1l, -s1l)};
-  float2 a[8], b[8];
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    a[r] = v[r] + v[r + 8];
-    b[r] = (r == 0) ? v[r] - v[r + 8] : ffmul(w[r], v[r] - v[r + 8]);
-  }
-  dft8_ff(a);
-  dft8_ff(b);
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    v[2 * r] = a[r];
-    v[2 * r + 1] = b[r];
-  }
-}
-template <int R>
-__device__ __forceinline__ void dftR_ff(float2 (&v)[R]) {
-  if constexpr (R == 16) dft16_ff(v);
-  else if constexpr (R == 8) dft8_ff(v);
-  else if constexpr (R == 4) dft4(v[0], v[1], v[2], v[3]);
-  else dft2(v[0], v[1]);
-}
-
 // One Stockham pass (radix RAD, span NS) over the tile's independent FFTs of length 2^LOG2F,
 // FFT f at shared offset f RS (padded index inside).
 template <int LOG2F, int RS, int RAD, int NS>
@@ -162,7 +113,7 @@ __device__ __forceinline__ void tpass(const float2* __restrict__ src, float2* __
 #pragma unroll
       for (int r = 1; r < RAD; ++r) v[r] = ffmul(tw[OFF + (r - 1) * NS + k], v[r]);
     }
-    dftR_ff<RAD>(v);
+    dftR<RAD>(v);
     float2* d = dst + f * RS;
     const int base = (jj - k) * RAD + k;
 #pragma unroll
