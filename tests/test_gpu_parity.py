@@ -126,28 +126,38 @@ def test_munk_short(sssp):
     _compare(u, tl, _oracle(s))
 
 
-def test_munk_full_size_against_stored_oracle(sssp):
-    """The full Munk workload (N = 4095, 2000 steps) against the stored FP64 oracle run
-    (tests/golden/munk_n4095_s2000.txt): sampled final field and TL rows."""
+@pytest.mark.parametrize("kernel", ["auto", "cta"])
+def test_munk_full_size_against_stored_oracle(sssp, kernel):
+    """The full Munk workload (N = 4095, 2000 steps) against the stored FP64 oracle runs: the
+    product form the GPU marches (tests/golden/munk_n4095_s2000_product.txt; field and TL bars)
+    and Algorithm 1's sum form (munk_n4095_s2000.txt; TL bar).  The 12-term series does not
+    reach 1e-10 here, so the two forms differ by ~8.5e-5 in the field after 2000 steps."""
     import importlib.util
     here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
     spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "make_golden.py"))
     mg = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mg)
-    meta, fidx, fref, tl_r, tl_ref = mg.load()
+    runs = {form: mg.load(os.path.join(here, name))
+            for form, name in (("product", "munk_n4095_s2000_product.txt"), ("sum", "munk_n4095_s2000.txt"))}
     s = inputs.munk()
-    pl = sssp.plan_for(s, tl_every=int(meta["tl_every"]))
+    pl = sssp.plan_for(s, tl_every=int(runs["product"][0]["tl_every"]))
+    pl.set_kernel(kernel)
     pl.march(s.steps)
     u = pl.read_field()
     tl, rng = pl.read_tl()
     pl.close()
-    rel = np.linalg.norm(u[fidx] - fref) / np.linalg.norm(fref)
-    assert rel <= FIELD_TOL, rel
-    assert abs(np.linalg.norm(u) / meta["norm"] - 1) < 1e-4
-    assert np.allclose(rng, tl_r)
-    tsub = tl[:, ::int(meta["tl_stride"])].astype(np.float64)
-    mask = tl_ref < 100
-    assert np.max(np.abs(tsub - tl_ref)[mask]) <= TL_TOL
+    err = {}
+    for form, (meta, fidx, fref, tl_r, tl_ref) in runs.items():
+        assert np.allclose(rng, tl_r)
+        rel = np.linalg.norm(u[fidx] - fref) / np.linalg.norm(fref)
+        tsub = tl[:, ::int(meta["tl_stride"])].astype(np.float64)
+        mask = tl_ref < 100
+        err[form] = (rel, np.max(np.abs(tsub - tl_ref)[mask]))
+        print(f"munk N=4095 2000 steps ({kernel}) vs the {form} form: sampled field rel-L2 {rel:.3e}, "
+              f"max TL error {err[form][1]:.4f} dB")
+    assert abs(np.linalg.norm(u) / runs["product"][0]["norm"] - 1) < 1e-4
+    assert err["product"][0] <= FIELD_TOL and err["product"][1] <= TL_TOL
+    assert err["sum"][0] <= FIELD_TOL and err["sum"][1] <= TL_TOL
 
 
 @pytest.mark.parametrize("kernel", ["auto", "cta"])
