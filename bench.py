@@ -530,7 +530,7 @@ def bench_ours(args):
                              "frac": achieved / peak,
                              # DRAM bytes (read + write) of one full march launch, ncu 1-pass capture
                              # (profiles/march_cluster_kernel_munk_n4095_launch_list.md)
-                             "traffic": (1.56e6 + 0.114e6) if pl.kernel == "cluster" else None,
+                             "traffic": (1.49e6 + 0.104e6) if pl.kernel == "cluster" else None,
                              "kernel": ("sssp_march_cluster_kernel<12, 8> (one solve over an 8-CTA cluster, 8 SMs)"
                                         if pl.kernel == "cluster" else "sssp_march_kernel<12> (one CTA, one SM)"),
                              "flops_per_launch": flops, "dst_per_launch": dst_per_launch,
