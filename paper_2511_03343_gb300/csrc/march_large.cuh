@@ -242,6 +242,13 @@ __device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC
       }
     }
     __syncthreads();
+    // the sink's own operands for this tile's outputs, and the next tile, load during the FFT
+#pragma unroll
+    for (int q = 0; q < PH; ++q) {
+      const int idx = t + q * kLargeNT;
+      const int k2 = idx >> C::LOG2TR, sl = idx & (TR - 1);
+      snk.prefetch(q, rowof(tile, sl) + P * k2);
+    }
     if (tile + 1 < NBT) loadB(tile + 1);
     const float2* F = tfft<C::LOG2Q, C::RSQ, 1>(bufA, bufB, twQ);
 #pragma unroll
@@ -253,7 +260,7 @@ __device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC
       if (emit) {
         const int k = rowof(tile, sl) + P * k2;
         const float2 zk = F[sl * C::RSQ + pidx(k2)];
-        snk(k, (k == 0) ? make_float2(0.f, 0.f) : make_float2(-0.5f * zk.y, 0.5f * zk.x));
+        snk.put(q, k, (k == 0) ? make_float2(0.f, 0.f) : make_float2(-0.5f * zk.y, 0.5f * zk.x));
       }
     }
     __syncthreads();
@@ -293,9 +300,12 @@ struct SrcScaled {  // x_m = s y_m
   float s;
   __device__ __forceinline__ float2 operator()(int m, bool) const { return s * y[m]; }
 };
+// A sink takes put(q, k, S_k) for its q-th output of a tile; prefetch(q, k) is called for the
+// same (q, k) before the tile's FFT, so a sink can load its own operands early.
 struct SnkArr {
   float2* a;
-  __device__ __forceinline__ void operator()(int k, float2 v) { a[k] = v; }
+  __device__ __forceinline__ void prefetch(int, int) {}
+  __device__ __forceinline__ void put(int, int k, float2 v) { a[k] = v; }
 };
 struct SnkTerm {  // t_m = B_k S_k: acc += t_m, X = t_m, and the norm partials of the stop test
   const float2* B;
@@ -303,23 +313,30 @@ struct SnkTerm {  // t_m = B_k S_k: acc += t_m, X = t_m, and the norm partials o
   float2* acc;
   float2* X;
   float nt, nw;
-  __device__ __forceinline__ void operator()(int k, float2 v) {
+  float2 pb[kLargePT / 2], pa[kLargePT / 2], pt[kLargePT / 2];  // B, acc, t0 of the tile's outputs
+  __device__ __forceinline__ void prefetch(int q, int k) {
+    pb[q] = __ldg(B + k);
+    pa[q] = acc[k];
+    pt[q] = t0[k];
+  }
+  __device__ __forceinline__ void put(int q, int k, float2 v) {
     if (k == 0) {  // the zero mode: t_m = 0, acc[0] and t0[0] stay 0
       X[0] = make_float2(0.f, 0.f);
       return;
     }
-    const float2 th = cmul(__ldg(B + k), v);
-    const float2 a = acc[k] + th;
+    const float2 th = cmul(pb[q], v);
+    const float2 a = pa[q] + th;
     acc[k] = a;
     X[k] = th;
     nt += cabs2(th);
-    nw += cabs2(t0[k] + a);
+    nw += cabs2(pt[q] + a);
   }
 };
 struct SnkTL {  // TL row: -10 log10 |u_n|^2 + 10 log10 r, n = 1..N
   float* row;
   float lr;
-  __device__ __forceinline__ void operator()(int k, float2 v) {
+  __device__ __forceinline__ void prefetch(int, int) {}
+  __device__ __forceinline__ void put(int, int k, float2 v) {
     if (k >= 1) row[k - 1] = fmaf(-10.f, log10f(cabs2(v)), lr);
   }
 };
@@ -385,7 +402,7 @@ __global__ void __launch_bounds__(kLargeNT, 1)
         ++ndst;
         float first = 0.f;
         for (int m = 1; m < d.terms; ++m) {
-          SnkTerm sk{d.B + (size_t)j * L, t0, acc, X, 0.f, 0.f};
+          SnkTerm sk{d.B + (size_t)j * L, t0, acc, X, 0.f, 0.f, {}, {}, {}};
           dst_global<LOG2L>(W, tb, tile_smem, SrcV{X, V, Vi}, sk);  // B DST(V t_{m-1}), acc += t_m
           ++ndst;
           const float snt = block_sum<LOG2L>(sk.nt, red);
@@ -447,7 +464,8 @@ struct SrcIn {  // x_m = in[m - 1]
 struct SnkScaled {
   float2* out;
   float s;
-  __device__ __forceinline__ void operator()(int k, float2 v) { out[k] = s * v; }
+  __device__ __forceinline__ void prefetch(int, int) {}
+  __device__ __forceinline__ void put(int, int k, float2 v) { out[k] = s * v; }
 };
 
 template <int LOG2L>
