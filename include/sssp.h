@@ -250,6 +250,16 @@ pe_status pe_plan_set_kernel(pe_plan* plan, int kernel);
 pe_status pe_plan_get_kernel(const pe_plan* plan, int* kernel);
 
 /*
+ * Autotuner (no counterpart in the paper): times `steps` range steps of the plan's own march on
+ * each kernel it can take (one CTA; the cluster where supported), a warm-up run then a timed
+ * run each, restores the marcher's state and TL bookkeeping after every run (pe_save_state /
+ * pe_load_state), and sets the faster kernel on the plan.  ms: 2 floats, the timed milliseconds
+ * of PE_KERNEL_CTA and PE_KERNEL_CLUSTER (-1 where not a candidate), or NULL; chosen: the kernel
+ * set, or NULL.  Needs a field (and a profile when Neumann terms are asked for); synchronises.
+ */
+pe_status pe_plan_autotune(pe_plan* plan, int steps, float* ms, int* chosen);
+
+/*
  * Checkpoint / resume of a march (bit-exact).  The state is the marcher's own variables: the
  * unnormalised transform coefficients of the envelope and its depth-domain copy, L complex
  * values each (L = N + 1 Dirichlet, N periodic, 2 (N - 1) Neumann), interleaved re/im, 4 L

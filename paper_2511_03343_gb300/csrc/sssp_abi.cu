@@ -13,6 +13,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/sssp.h"
 #include "cluster_launch.h"
 #include "march_kernel.cuh"
@@ -85,6 +87,12 @@ int ilog2_exact(int v) {
 
 
 namespace {
+
+// NVTX range over an ABI call (visible in Nsight timelines; no cost without a tool attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 pe_status fail(pe_plan* p, pe_status s, const std::string& msg) {
   if (p) p->err = msg;
@@ -501,6 +509,7 @@ pe_status pe_plan_create(pe_plan** out, int N, double H, double k0, double dr, i
 
 pe_status pe_plan_create_bc(pe_plan** out, int N, double H, double k0, double dr, int pade_order, int neumann_terms,
                             double neumann_tol, int bc, void* cuda_stream) {
+  NvtxRange nvtx_("pe_plan_create");
   g_create_error.clear();
   if (!out) {
     g_create_error = "out is NULL";
@@ -650,6 +659,7 @@ pe_status pe_set_output(pe_plan* p, int tl_every) {
 
 pe_status pe_set_field(pe_plan* p, const float* u, int on_device, double r) {
   if (!p) return PE_ERR_ARG;
+  NvtxRange nvtx_("pe_set_field");
   if (!u) return fail(p, PE_ERR_ARG, "u is NULL");
   if (!std::isfinite(r)) return fail(p, PE_ERR_ARG, "r must be finite");
   PE_CUDA(p, cudaMemcpyAsync(p->dStage, u, sizeof(float2) * p->N_user,
@@ -734,6 +744,7 @@ pe_status pe_set_profile(pe_plan* p, const double* n2, int is_complex, double ra
 }
 
 pe_status pe_set_profiles(pe_plan* p, const double* n2, const double* ranges, int count, int on_device) {
+  NvtxRange nvtx_("pe_set_profiles");
   if (!p) return PE_ERR_ARG;
   if (!n2 || !ranges || count < 0) return fail(p, PE_ERR_ARG, "n2/ranges NULL or count < 0");
   return append_nodes(p, n2, ranges, count, on_device);
@@ -751,6 +762,7 @@ pe_status pe_clear_profiles(pe_plan* p) {
 
 pe_status pe_march(pe_plan* p, int steps) {
   if (!p) return PE_ERR_ARG;
+  NvtxRange nvtx_("pe_march");
   SolveDesc d;
   pe_status st = prepare_desc(p, steps, &d);
   if (st != PE_OK) return st;
@@ -766,6 +778,7 @@ pe_status pe_march(pe_plan* p, int steps) {
 
 pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
   if (!plans || !steps || count < 0) return PE_ERR_ARG;
+  NvtxRange nvtx_("pe_march_batch_steps");
   if (count == 0) return PE_OK;
   pe_plan* p0 = plans[0];
   if (!p0) return PE_ERR_ARG;
@@ -839,6 +852,7 @@ pe_status pe_sync(pe_plan* p) {
 
 pe_status pe_read_field(pe_plan* p, float* out, int to_device) {
   if (!p) return PE_ERR_ARG;
+  NvtxRange nvtx_("pe_read_field");
   if (!out) return fail(p, PE_ERR_ARG, "out is NULL");
   // carrier e^{i k0 (r - r_set)} in FP64 phase arithmetic (the marcher keeps the envelope)
   const double phase = std::fmod(p->k0 * p->dr * double(p->steps_done), 2.0 * M_PI);
@@ -854,6 +868,7 @@ pe_status pe_read_field(pe_plan* p, float* out, int to_device) {
 }
 
 pe_status pe_read_TL(pe_plan* p, float* out, size_t cap, double* ranges, size_t* n_rows) {
+  NvtxRange nvtx_("pe_read_TL");
   if (!p) return PE_ERR_ARG;
   const size_t need = size_t(p->tl_rows) * p->N_user;
   if (n_rows) *n_rows = size_t(p->tl_rows);
@@ -934,6 +949,64 @@ pe_status pe_plan_set_kernel(pe_plan* p, int kernel) {
     if (a < 1 || b < 1) return fail(p, PE_ERR_ARG, "this device cannot hold a cluster of the required shape");
   }
   p->kernel = kernel;
+  return PE_OK;
+}
+
+pe_status pe_plan_autotune(pe_plan* p, int steps, float* ms, int* chosen) {
+  if (!p || steps < 1) return PE_ERR_ARG;
+  NvtxRange nvtx_("pe_plan_autotune");
+  if (!p->field_set) return fail(p, PE_ERR_STATE, "pe_plan_autotune before pe_set_field");
+  if (p->terms > 1 && p->nodes == 0) return fail(p, PE_ERR_STATE, "pe_plan_autotune with Neumann terms but no profile");
+  int cands[2] = {PE_KERNEL_CTA, PE_KERNEL_CLUSTER};
+  int ncand = 1;
+  int clusters = 0;
+  if (p->user_bc == PE_BC_DIRICHLET && sssp_cluster::supported(p->log2L) &&
+      sssp_cluster::max_active_clusters(p->log2L, p->complex_profile, &clusters) == cudaSuccess && clusters > 0)
+    ncand = 2;
+  // the marcher's state and bookkeeping, restored after every trial
+  std::vector<float> state(pe_state_size(p));
+  double r_set = 0.0;
+  long long steps_done = 0;
+  pe_status st = pe_save_state(p, state.data(), &r_set, &steps_done);
+  if (st != PE_OK) return st;
+  const long long tl_rows = p->tl_rows;
+  const std::vector<double> tl_ranges = p->tl_ranges;
+  const int kernel0 = p->kernel;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  PE_CUDA(p, cudaEventCreate(&e0));
+  PE_CUDA(p, cudaEventCreate(&e1));
+  float best = 0.f;
+  int best_k = kernel0 == PE_KERNEL_AUTO ? PE_KERNEL_CTA : kernel0;
+  for (int c = 0; c < ncand; ++c) {
+    p->kernel = cands[c];
+    float t = 0.f;
+    for (int rep = 0; rep < 2 && st == PE_OK; ++rep) {  // the first run warms tables and caches
+      PE_CUDA(p, cudaEventRecord(e0, p->stream));
+      st = pe_march(p, steps);
+      PE_CUDA(p, cudaEventRecord(e1, p->stream));
+      if (st == PE_OK) st = check_status(p);
+      if (st == PE_OK) PE_CUDA(p, cudaEventElapsedTime(&t, e0, e1));
+      pe_status rs = pe_load_state(p, state.data(), r_set, steps_done);
+      p->tl_rows = tl_rows;
+      p->tl_ranges = tl_ranges;
+      if (st == PE_OK) st = rs;
+    }
+    if (st != PE_OK) break;
+    if (ms) ms[c] = t;
+    if (c == 0 || t < best) {
+      best = t;
+      best_k = cands[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != PE_OK) {
+    p->kernel = kernel0;
+    return st;
+  }
+  if (ncand < 2 && ms) ms[1] = -1.f;
+  p->kernel = best_k;
+  if (chosen) *chosen = best_k;
   return PE_OK;
 }
 

@@ -66,6 +66,7 @@ _SIGNATURES = {
     "pe_march_batch_steps": (_i, [ctypes.POINTER(_vp), _vp, _i]),
     "pe_plan_set_kernel": (_i, [_vp, _i]),
     "pe_plan_get_kernel": (_i, [_vp, ctypes.POINTER(_i)]),
+    "pe_plan_autotune": (_i, [_vp, _i, _vp, ctypes.POINTER(_i)]),
     "pe_state_size": (_sz, [_vp]),
     "pe_save_state": (_i, [_vp, _vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
     "pe_load_state": (_i, [_vp, _vp, _d, ctypes.c_longlong]),
@@ -297,6 +298,39 @@ class Plan:
         k = _i(0)
         self._c(lib().pe_plan_get_kernel(self._p, ctypes.byref(k)))
         return {v: n for n, v in KERNELS.items()}[k.value]
+
+    def autotune(self, steps: int = 4, cache: bool = True) -> dict:
+        """Choose this plan's kernel by timing `steps` range steps of its own march on each
+        candidate (pe_plan_autotune; the march's state is restored).  The choice is cached in a
+        JSON file keyed by the device and the plan's shape — $SSSP_TUNE_CACHE, else
+        ~/.cache/sssp_gb300/tune.json — and a cached choice is applied without timing."""
+        import json
+        path = os.environ.get("SSSP_TUNE_CACHE",
+                              os.path.join(os.path.expanduser("~"), ".cache", "sssp_gb300", "tune.json"))
+        try:
+            import torch
+            dev = torch.cuda.get_device_name(torch.cuda.current_device())
+        except Exception:  # noqa: BLE001 - the key only needs a stable device label
+            dev = "cuda"
+        key = f"{dev}|N={self.N}|bc={self.bc}|p={self.pade_order}|terms={self.neumann_terms}|steps={int(steps)}"
+        data = {}
+        if cache and os.path.exists(path):
+            with open(path) as f:
+                data = json.load(f)
+            if key in data:
+                self.set_kernel(data[key]["kernel"])
+                return dict(data[key], cached=True)
+        ms = (ctypes.c_float * 2)()
+        ch = _i(0)
+        self._c(lib().pe_plan_autotune(self._p, int(steps), ctypes.cast(ms, _vp), ctypes.byref(ch)))
+        res = {"kernel": {v: n for n, v in KERNELS.items()}[ch.value], "ms_cta": float(ms[0]),
+               "ms_cluster": float(ms[1]) if ms[1] >= 0 else None, "steps": int(steps)}
+        if cache:
+            os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+            data[key] = res
+            with open(path, "w") as f:
+                json.dump(data, f, indent=1, sort_keys=True)
+        return dict(res, cached=False)
 
     def save_state(self):
         """Bit-exact checkpoint: (spectral state, r_set, steps)."""

@@ -866,3 +866,40 @@ def test_cluster_batch_alone_vs_mix(sssp):
         assert np.array_equal(pl.read_field(), u)
         assert np.array_equal(pl.read_tl()[0], tl)
         pl.close()
+
+
+# ----------------------------------------------------------------------------- autotuner
+def test_autotune_restores_the_march_and_caches(sssp, tmp_path, monkeypatch):
+    """pe_plan_autotune in the middle of a march: the march goes on with the same bits as
+    marching on the chosen kernel without tuning (state and TL bookkeeping restored), and the
+    choice is cached for a plan of the same shape."""
+    monkeypatch.setenv("SSSP_TUNE_CACHE", str(tmp_path / "tune.json"))
+    s = inputs.munk(N=4095, freq=100.0, dr=25.0, steps=10)
+    pl = sssp.plan_for(s, tl_every=1)
+    first = pl.kernel
+    pl.march(3)
+    res = pl.autotune(steps=2)
+    assert res["kernel"] in ("cta", "cluster") and not res["cached"]
+    assert res["ms_cta"] > 0 and res["ms_cluster"] is not None and res["ms_cluster"] > 0
+    assert pl.kernel == res["kernel"]
+    pl.march(7)
+    u = pl.read_field()
+    tl, rng = pl.read_tl()
+    pl.close()
+    ref = sssp.plan_for(s, tl_every=1)
+    ref.set_kernel(first)
+    ref.march(3)
+    ref.set_kernel(res["kernel"])
+    ref.march(7)
+    assert np.array_equal(u, ref.read_field())
+    tl_ref, rng_ref = ref.read_tl()
+    assert np.array_equal(tl, tl_ref) and np.allclose(rng, rng_ref)
+    ref.close()
+    again = sssp.plan_for(s, tl_every=1)
+    res2 = again.autotune(steps=2)
+    assert res2["cached"] and res2["kernel"] == res["kernel"] and again.kernel == res["kernel"]
+    again.close()
+    small = sssp.plan_for(inputs.munk(N=255, steps=4), tl_every=0)  # one candidate only
+    r3 = small.autotune(steps=2, cache=False)
+    assert r3["kernel"] == "cta" and r3["ms_cluster"] is None
+    small.close()
