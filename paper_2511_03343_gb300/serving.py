@@ -41,6 +41,22 @@ def build_solve(req: Dict, range_scale: float = 1.0, node_spacing: float = 5000.
     return s
 
 
+def _depth_summary(depth, points: int = 24) -> Dict:
+    """Admitted concurrency and queue depth over time: maxima, time averages and an evenly
+    decimated trace of (seconds, live, queued)."""
+    if not depth:
+        return {"max_live": 0, "max_queued": 0, "mean_live": 0.0, "mean_queued": 0.0, "trace": []}
+    t = np.array([d[0] for d in depth])
+    live = np.array([d[1] for d in depth], dtype=np.float64)
+    q = np.array([d[2] for d in depth], dtype=np.float64)
+    w = np.diff(np.concatenate([[0.0], t]))  # time each sample stood for
+    idx = np.unique(np.linspace(0, len(depth) - 1, min(points, len(depth))).astype(int))
+    return {"max_live": int(live.max()), "max_queued": int(q.max()),
+            "mean_live": float((live * w).sum() / max(w.sum(), 1e-12)),
+            "mean_queued": float((q * w).sum() / max(w.sum(), 1e-12)),
+            "trace": [[round(float(t[i]), 3), int(live[i]), int(q[i])] for i in idx]}
+
+
 def replay(trace: List[Dict], hbm_budget: float, chunk_steps: int = 50, tl_every: int = 10,
            range_scale: float = 1.0, max_live: int = 1024, stream=None, keep_results: bool = False):
     """Replay ``trace`` against a fresh server; returns latency / throughput figures."""
@@ -54,6 +70,7 @@ def replay(trace: List[Dict], hbm_budget: float, chunk_steps: int = 50, tl_every
     failed = {}
     t0 = time.perf_counter()
     nsteps = 0
+    depth = []  # (seconds since start, live solves, queued requests) after every server step
     while pending or running:
         now = time.perf_counter() - t0
         while pending and trace[pending[0]]["t_arrival"] <= now:
@@ -64,9 +81,10 @@ def replay(trace: List[Dict], hbm_budget: float, chunk_steps: int = 50, tl_every
         if not running:
             time.sleep(max(0.0, trace[pending[0]]["t_arrival"] - (time.perf_counter() - t0)))
             continue
-        srv.step()
+        live, queued, _ = srv.step()
         nsteps += 1
         tnow = time.perf_counter()
+        depth.append((tnow - t0, live, queued))
         for rid in list(running):
             state = srv.state(rid)
             if state == 3:  # the march failed on the device (e.g. a diverging Neumann series)
@@ -90,7 +108,8 @@ def replay(trace: List[Dict], hbm_budget: float, chunk_steps: int = 50, tl_every
     out = {"requests": len(trace), "completed": len(lat), "failed": len(failed),
            "failed_ids": sorted(failed), "wall_s": wall, "server_steps": nsteps,
            "throughput": units / wall, "p50_s": float(np.percentile(L, 50)), "p99_s": float(np.percentile(L, 99)),
-           "mean_s": float(L.mean()), "peak_live": st["peak_live"], "peak_bytes": st["peak_bytes"]}
+           "mean_s": float(L.mean()), "peak_live": st["peak_live"], "peak_bytes": st["peak_bytes"],
+           "queue_depth": _depth_summary(depth)}
     if keep_results:
         out["results"] = results
     return out
