@@ -148,3 +148,18 @@ def test_server_submit_host_checks(L):
     with pytest.raises(sssp.PEError):
         srv.cancel(987654)                         # unknown id
     srv.close()
+
+
+def test_serving_queue_depth_summary():
+    """Queue depth over time (host logic of the serving replay): maxima, time-weighted means
+    and the decimated trace."""
+    from paper_2511_03343_gb300 import serving
+    d = serving._depth_summary([(0.1, 2, 5), (0.3, 4, 1), (0.6, 1, 0)])
+    assert d["max_live"] == 4 and d["max_queued"] == 5
+    # samples stand for 0.1, 0.2 and 0.3 s
+    assert abs(d["mean_live"] - (2 * 0.1 + 4 * 0.2 + 1 * 0.3) / 0.6) < 1e-12
+    assert abs(d["mean_queued"] - (5 * 0.1 + 1 * 0.2) / 0.6) < 1e-12
+    assert d["trace"] == [[0.1, 2, 5], [0.3, 4, 1], [0.6, 1, 0]]
+    many = serving._depth_summary([(0.01 * i, i % 7, i % 3) for i in range(1, 1001)], points=24)
+    assert len(many["trace"]) == 24 and many["trace"][-1][0] == 10.0
+    assert serving._depth_summary([])["trace"] == []
