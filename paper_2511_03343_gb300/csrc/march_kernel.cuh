@@ -20,7 +20,7 @@
 // with a block-wide prefix scan for the odd outputs.  The FFT is a Stockham autosort FFT
 // with radix-8 passes (one radix-8 butterfly per thread, 8 points per thread) and a final
 // radix-2/4 pass, ping-ponging between two padded shared buffers (index i stored at
-// i + i/8 to spread the strided accesses over the banks).
+// i + i/16 to spread the strided accesses over the banks).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
