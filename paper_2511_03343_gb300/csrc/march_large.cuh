@@ -63,8 +63,9 @@ struct LargeTabs {
 //   pass A (columns n2): Y[k1][n2] = w_{2L}^{n2 k1} sum_{n1} z_{Q n1 + n2} w_P^{n1 k1}
 //   pass B (rows k1):    Z_{k1 + P k2} = sum_{n2} Y[k1][n2] w_Q^{n2 k2},  only k2 < Q/2 kept.
 // z being odd, column Q - n2 is column n2 negated with its rows reversed, so only the columns
-// n2 in [0, Q/2] are transformed and stored (L + P values), and pass B rebuilds the rest of a
-// row from its partner row P - k1.  Each pass moves tiles of 8192 points through shared memory
+// n2 in [0, Q/2] are transformed and stored (L + P values); pass B rebuilds the rest of a row
+// from its partner row P - k1, and (Z being odd too) transforms only the rows k1 <= P/2, whose
+// upper outputs are the partner rows' S values: half a 2L-point FFT in all.  Each pass moves tiles of 8192 points through shared memory
 // (16 per thread); a transform reads x once, writes and reads the half intermediate once and
 // writes S once: 32 B per point, the two global passes of 16 B per point.
 template <int LOG2L>
@@ -153,10 +154,9 @@ template <int LOG2L, class SRC, class SNK>
 __device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC& src, SNK& snk) {
   using C = BigCfg<LOG2L>;
   constexpr int L = C::L, P = C::P, Q = C::Q, QH = Q / 2, QS = QH + 1;
-  constexpr int TC = C::TC, TR = C::TR, TRH = TR / 2;
+  constexpr int TC = C::TC, TR = C::TR;
   constexpr int LOG2QH = C::LOG2Q - 1;
   constexpr int NA = QH / TC + 1;  // pass-A tiles; the last ends at column Q/2 (overlap rewrites)
-  constexpr int NBT = P / TR + 1;  // pass-B tiles; the last holds row P/2
   const int t = threadIdx.x;
   float2* bufA = sm;
   float2* bufB = sm + C::BUF;
@@ -203,64 +203,91 @@ __device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC
     }
     __syncthreads();
   }
-  // pass B: rows in pairs (k, P - k); the odd symmetry of z gives the unstored half of a row
-  // from its partner: Y[k][Q - n] = -w_Q^{-n} Y[P - k][n] (k != 0), -Y[0][n] (k = 0).
-  // The first Q/2 outputs of each row are S_k' = (i/2) Z_k', k' = k + P k2.
-  auto rowof = [&](int tile, int s) {
-    const int own = (tile < NBT - 1 ? tile * TRH : P / 2 - TRH + 1) + (s & (TRH - 1));
-    return s < TRH ? own : ((P - own) & (P - 1));
-  };
+  // pass B: the rows k in [0, P/2].  The odd symmetry of z gives the unstored half of a row from
+  // its partner row P - k: Y[k][Q - n] = -w_Q^{-n} Y[P - k][n] (k != 0), -Y[0][n] (k = 0).  A row's
+  // Q outputs are Z_{k + P k2}; those with k + P k2 >= L are -Z at 2L - k - P k2 = (P - k) +
+  // P (Q - 1 - k2), the partner row's, so one FFT per row pair yields both rows' S values
+  // (rows 0 and P/2 are their own partners: only their first Q/2 outputs are kept).
+  constexpr int NBT = (P / 2) / TR + 1;  // the last tile ends at row P/2 (its other rows: done)
+  auto rowof = [&](int tile, int sl) { return (tile < NBT - 1 ? tile * TR : P / 2 - TR + 1) + sl; };
   auto loadB = [&](int tile) {
 #pragma unroll
-    for (int q = 0; q < PH; ++q) {
+    for (int q = 0; q < PH; ++q) {  // own stored half, columns [0, Q/2)
       const int idx = t + q * kLargeNT;
       pre[q] = W[rowof(tile, idx >> LOG2QH) * QS + (idx & (QH - 1))];
     }
-    if (t < TR) pre[PH] = W[rowof(tile, t) * QS + QH];
+#pragma unroll
+    for (int q = 0; q < PH; ++q) {  // the partner's stored columns [1, Q/2) (column 0 unused)
+      const int idx = t + q * kLargeNT;
+      const int k = rowof(tile, idx >> LOG2QH);
+      pre[PH + q] = W[((P - k) & (P - 1)) * QS + (idx & (QH - 1))];
+    }
+    if (t < TR) pre[PT] = W[rowof(tile, t) * QS + QH];
+  };
+  // output slot q of this thread: its target index, or false where another slot has it
+  auto target = [&](int tile, int q, int& tgt, bool& neg) {
+    const int idx = t + q * kLargeNT;
+    const int k2 = idx >> C::LOG2TR, k = rowof(tile, idx & (TR - 1));
+    if (tile == NBT - 1 && k != P / 2) return false;
+    const int kap = k + P * k2;
+    if (kap < L) {
+      tgt = kap;
+      neg = false;
+      return true;
+    }
+    if (k == 0 || k == P / 2) return false;
+    tgt = 2 * L - kap;
+    neg = true;
+    return true;
   };
   loadB(0);
   for (int tile = 0; tile < NBT; ++tile) {
 #pragma unroll
     for (int q = 0; q < PH; ++q) {
       const int idx = t + q * kLargeNT;
-      bufA[(idx >> LOG2QH) * C::RSQ + pidx(idx & (QH - 1))] = pre[q];
-    }
-    if (t < TR) bufA[t * C::RSQ + pidx(QH)] = pre[PH];
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < PH; ++q) {
-      const int idx = t + q * kLargeNT;
-      const int sl = idx >> LOG2QH, np = idx & (QH - 1);
-      if (np != 0) {
-        const float2 v = bufA[(sl ^ TRH) * C::RSQ + pidx(np)];
-        float2 r = make_float2(-v.x, -v.y);
-        if (rowof(tile, sl) != 0) {  // times w_Q^{-np} = conj(w_{2L}^{P np})
-          const float4 w = __ldg(tb.tw2L + P * np);
+      const int sl = idx >> LOG2QH, n = idx & (QH - 1);
+      bufA[sl * C::RSQ + pidx(n)] = pre[q];
+      if (n != 0) {  // Y[k][Q - n] from the partner row
+        float2 r = make_float2(-pre[PH + q].x, -pre[PH + q].y);
+        if (rowof(tile, sl) != 0) {  // times w_Q^{-n} = conj(w_{2L}^{P n})
+          const float4 w = __ldg(tb.tw2L + P * n);
           r = ffmul(make_float4(w.x, -w.y, w.z, -w.w), r);
         }
-        bufA[sl * C::RSQ + pidx(Q - np)] = r;
+        bufA[sl * C::RSQ + pidx(Q - n)] = r;
       }
     }
+    if (t < TR) bufA[t * C::RSQ + pidx(QH)] = pre[PT];
     __syncthreads();
-    // the sink's own operands for this tile's outputs, and the next tile, load during the FFT
+    // the sink's operands for the first half of this tile's outputs, and the next tile, load
+    // during the FFT
 #pragma unroll
     for (int q = 0; q < PH; ++q) {
-      const int idx = t + q * kLargeNT;
-      const int k2 = idx >> C::LOG2TR, sl = idx & (TR - 1);
-      snk.prefetch(q, rowof(tile, sl) + P * k2);
+      int tg;
+      bool ng;
+      if (target(tile, q, tg, ng)) snk.prefetch(q, tg);
     }
     if (tile + 1 < NBT) loadB(tile + 1);
     const float2* F = tfft<C::LOG2Q, C::RSQ, 1>(bufA, bufB, twQ);
 #pragma unroll
-    for (int q = 0; q < PH; ++q) {
-      const int idx = t + q * kLargeNT;
-      const int k2 = idx >> C::LOG2TR, sl = idx & (TR - 1);
-      const int ownrow = rowof(tile, sl & (TRH - 1));
-      const bool emit = (tile < NBT - 1) ? (sl < TRH || ownrow != 0) : (sl < TRH && ownrow == P / 2);
-      if (emit) {
-        const int k = rowof(tile, sl) + P * k2;
-        const float2 zk = F[sl * C::RSQ + pidx(k2)];
-        snk.put(q, k, (k == 0) ? make_float2(0.f, 0.f) : make_float2(-0.5f * zk.y, 0.5f * zk.x));
+    for (int half = 0; half < 2; ++half) {
+      if (half == 1) {
+#pragma unroll
+        for (int q = 0; q < PH; ++q) {
+          int tg;
+          bool ng;
+          if (target(tile, PH + q, tg, ng)) snk.prefetch(q, tg);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < PH; ++q) {
+        int tg;
+        bool ng;
+        if (target(tile, half * PH + q, tg, ng)) {
+          const int idx = t + (half * PH + q) * kLargeNT;
+          const float2 zk = F[(idx & (TR - 1)) * C::RSQ + pidx(idx >> C::LOG2TR)];
+          const float2 sv = ng ? make_float2(0.5f * zk.y, -0.5f * zk.x) : make_float2(-0.5f * zk.y, 0.5f * zk.x);
+          snk.put(q, tg, (tg == 0) ? make_float2(0.f, 0.f) : sv);
+        }
       }
     }
     __syncthreads();
