@@ -1,15 +1,22 @@
-"""Benchmark of the GB300 SSSP marcher on the range-independent Munk workload.
+"""Benchmark of the GB300 SSSP marcher.
 
-Workload (one solve): Munk deep-ocean guide, H = 5000 m, f = 50 Hz, source at 1000 m,
-N = 4095 interior DST-I points, dr = 50 m, 2000 range steps (100 km), [6/6] Pade, Neumann
-series to 1e-10 or 12 terms, TL recorded after every step.  One bench step = one whole
-2000-range-step march of that solve (set the starter, march, TL rows in HBM).
+Default workload (the headline): the batched precision sweep's FFT form, 256 range-independent
+Munk solves (H = 5000 m, source at 1000 m, N = 1023 interior DST-I points each, f ~ U[50, 500] Hz
+from default_rng(4), dr = 25 m, 2000 range steps, [6/6] Pade, Neumann series to 1e-10 or 12
+terms, TL every 10 steps), all marched together by one batched launch (one CTA per solve).  One
+bench step = set the 256 starters + one 2000-range-step batched march (TL rows land in HBM).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Besides the device-timed value the JSON line carries: the roofline of the march kernel, the
+end-to-end figure through the public API with host buffers, the same solves marched one at a
+time on the plain marcher (``vs_plain``), the serving mix (``served``: Poisson trace of 1000
+requests under a 120 GB budget, p50/p99 latency and throughput), parity of each against stored
+FP64 oracle runs or the plain path, and the FP64 oracle timed on the host cores.
 
-Prints ONE JSON line.  ``--impl reference`` times the FP64 CPU oracle on a bounded sample of
-the same workload (the reference arm of this comparison).  Under torchrun (N > 1) every rank
-marches its own copy of the solve (independent replicas, weak scaling, no collective).
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload ...]
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same workload (the
+reference arm of this comparison).  Under torchrun (N > 1) every rank marches its own copy of
+the batch (independent replicas, weak scaling, no collective).
 """
 from __future__ import annotations
 
@@ -28,7 +35,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "depth-pt·range-steps/s at ≤0.1 dB TL error vs plain path; served p50/p99 latency"
 UNIT = "depth-pt·range-steps/s"
-WORKLOAD = "munk_n4095_f50_dr50_s2000_p6_neumann12"
+WORKLOAD_MUNK = "munk_n4095_f50_dr50_s2000_p6_neumann12"
+WORKLOAD = "munk_batch256_n1023_f50-500_dr25_s2000_p6_neumann12"
+BATCH_TL_EVERY = 10
 
 
 def _rank_env():
@@ -45,7 +54,7 @@ def _hbm_peak():
 
 
 def _config(extra=None):
-    c = {"workload": WORKLOAD, "N": 4095, "H_m": 5000.0, "freq_hz": 50.0, "dr_m": 50.0, "range_steps": 2000,
+    c = {"workload": WORKLOAD_MUNK, "N": 4095, "H_m": 5000.0, "freq_hz": 50.0, "dr_m": 50.0, "range_steps": 2000,
          "pade_order": 6, "neumann_terms": 12, "neumann_tol": 1e-10, "tl_every": 1, "solves_per_gpu": 1,
          "l2": "flushed between timed iterations (256 MiB write)"}
     if extra:
@@ -126,57 +135,331 @@ def _dst_flops(N):
     return 5.0 * L * math.log2(L)
 
 
-def run_cpu_oracle_sample(seconds=15.0):
-    """Time the FP64 oracle (as it stands) on a bounded sample of the workload: the first
-    range steps of the same Munk march, extrapolated as depth-pt*steps per second."""
-    import numpy as np  # noqa: F401
+def run_cpu_oracle_sample(seconds=15.0, workload="batch"):
+    """Time the FP64 oracle (as it stands: Algorithm 1's sum form, explicit O(N^2) sine sums
+    through BLAS) on the host cores, on a bounded sample of the workload, as depth-pt*steps per
+    second.  Batch: the first range steps of successive members of the 256-solve batch; Munk:
+    the first range steps of the N = 4095 march."""
     from oracle import sssp_oracle as O
     from paper_2511_03343_gb300 import inputs
-    s = inputs.munk()
-    g = O.Grid(N=s.N, H=s.H, k0=s.k0, dr=s.dr)
-    plan = O.pade_plan(g.sigma, s.pade_order)
-    O.march(s.u0, s.profiles, g, s.pade_order, 1, s.neumann_terms, s.neumann_tol, tl_every=1, plan=plan)  # warm
-    t0 = time.perf_counter()
-    O.march(s.u0, s.profiles, g, s.pade_order, 1, s.neumann_terms, s.neumann_tol, tl_every=1, plan=plan)
-    one = time.perf_counter() - t0
-    steps = max(1, min(s.steps, int(seconds / max(one, 1e-6))))
-    t0 = time.perf_counter()
-    O.march(s.u0, s.profiles, g, s.pade_order, steps, s.neumann_terms, s.neumann_tol, tl_every=1, plan=plan)
-    el = time.perf_counter() - t0
-    return {"value": s.N * steps / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"first {steps} of {s.steps} range steps of the N=4095 Munk march (FP64, sum form, "
-                      f"direct O(N^2) DST-I via BLAS), {el:.1f} s"}
+    solves = inputs.munk_batch(steps=2000) if workload == "batch" else [inputs.munk()]
+    units, el, done = 0, 0.0, []
+    per = 20 if workload == "batch" else None
+    for s in solves:
+        g = O.Grid(N=s.N, H=s.H, k0=s.k0, dr=s.dr)
+        plan = O.pade_plan(g.sigma, s.pade_order)
+        O.march(s.u0, s.profiles, g, s.pade_order, 1, s.neumann_terms, s.neumann_tol, tl_every=1, plan=plan)
+        if per is None:  # one solve: as many steps as fit in the time
+            t0 = time.perf_counter()
+            O.march(s.u0, s.profiles, g, s.pade_order, 1, s.neumann_terms, s.neumann_tol, tl_every=1, plan=plan)
+            one = time.perf_counter() - t0
+            n = max(1, min(s.steps, int(seconds / max(one, 1e-6))))
+        else:
+            n = per
+        t0 = time.perf_counter()
+        O.march(s.u0, s.profiles, g, s.pade_order, n, s.neumann_terms, s.neumann_tol, tl_every=1, plan=plan)
+        el += time.perf_counter() - t0
+        units += s.N * n
+        done.append(n)
+        if el >= seconds:
+            break
+    what = (f"first {per} range steps of each of the first {len(done)} of the 256 batch members (N=1023)"
+            if workload == "batch" else f"first {done[0]} of 2000 range steps of the N=4095 Munk march")
+    return {"value": units / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{what} (FP64 oracle, sum form, direct O(N^2) DST-I via BLAS), {el:.1f} s"}
 
 
 def bench_reference(args):
+    """The reference arm: the FP64 oracle as it stands on the host cores; each bench step is a
+    bounded sample of the workload (``--ref-sample-steps`` range steps of one solve: for the
+    batch, members in turn)."""
     rank, world, _ = _rank_env()
     if rank != 0:
         return
     from oracle import sssp_oracle as O
     from paper_2511_03343_gb300 import inputs
-    s = inputs.munk()
-    g = O.Grid(N=s.N, H=s.H, k0=s.k0, dr=s.dr)
-    plan = O.pade_plan(g.sigma, s.pade_order)
+    batch = args.workload == "batch"
+    solves = inputs.munk_batch(steps=2000) if batch else [inputs.munk()]
     sample_steps = args.ref_sample_steps
-    times = []
-    u = s.u0
+    times, units = [], 0
     for i in range(args.warmup + args.steps):
+        s = solves[i % len(solves)]
+        g = O.Grid(N=s.N, H=s.H, k0=s.k0, dr=s.dr)
+        plan = O.pade_plan(g.sigma, s.pade_order)
         t0 = time.perf_counter()
-        O.march(u, s.profiles, g, s.pade_order, sample_steps, s.neumann_terms, s.neumann_tol, tl_every=1, plan=plan)
+        O.march(s.u0, s.profiles, g, s.pade_order, sample_steps, s.neumann_terms, s.neumann_tol, tl_every=1, plan=plan)
         el = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(el)
+            units += s.N * sample_steps
     tot = sum(times)
-    value = s.N * sample_steps * len(times) / tot
+    value = units / tot
+    what = (f"each step: {sample_steps} of the 2000 range steps of one batch member (N=1023; members in turn)"
+            if batch else f"each step: {sample_steps} of the 2000 range steps of the N=4095 Munk march")
+    cfg = _batch_config() if batch else _config()
+    cfg["reference_sample_range_steps"] = sample_steps
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": _config({"reference_sample_range_steps": sample_steps}),
+            "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"each step: {sample_steps} of the 2000 range steps of the N=4095 Munk "
-                                       f"march (FP64 oracle, sum form, direct O(N^2) DST-I)"},
+                             "sample": what + " (FP64 oracle, sum form, direct O(N^2) DST-I)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _batch_config(extra=None):
+    c = {"workload": WORKLOAD, "solves": 256, "N": 1023, "H_m": 5000.0, "freq_hz": "U[50, 500] default_rng(4)",
+         "dr_m": 25.0, "range_steps": 2000, "pade_order": 6, "neumann_terms": 12, "neumann_tol": 1e-10,
+         "zs_m": 1000.0, "c0_mps": 1500.0, "tl_every": BATCH_TL_EVERY, "solves_per_gpu": 256,
+         "l2": "flushed between timed iterations (256 MiB write)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def _load_make_golden():
+    import importlib.util
+    here = os.path.join(ROOT, "tests", "golden")
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    return mg
+
+
+def _batch_parity(fields, tls, tl_every):
+    """Field / TL error of the bench's own output for the batch members stored from the FP64
+    oracle's product form (tests/golden/batch_n1023_s2000.txt): worst member and per member."""
+    import numpy as np
+    mg = _load_make_golden()
+    path = os.path.join(ROOT, "tests", "golden", "batch_n1023_s2000.txt")
+    if not os.path.exists(path):
+        return None
+    runs = mg.load_batch(path)
+    per = {}
+    step = mg.BATCH_TL_EVERY // tl_every
+    for i, (freq, fidx, fref, tl_r, tl_ref) in runs.items():
+        if i not in fields:
+            continue
+        u, tl = fields[i], tls[i]
+        rows = tl[step - 1::step][:, ::mg.BATCH_TL_STRIDE].astype(np.float64)
+        mask = tl_ref < 100
+        per[str(i)] = {"freq_hz": round(freq, 3),
+                       "field_rel_l2_sampled": float(np.linalg.norm(u[fidx] - fref) / np.linalg.norm(fref)),
+                       "max_tl_err_db": float(np.max(np.abs(rows - tl_ref)[mask]))}
+    if not per:
+        return None
+    return {"against": "stored FP64 oracle runs, product form (tests/golden/batch_n1023_s2000.txt)",
+            "members": per,
+            "worst_field_rel_l2": max(v["field_rel_l2_sampled"] for v in per.values()),
+            "worst_tl_err_db": max(v["max_tl_err_db"] for v in per.values())}
+
+
+def _tl_vs(tl_a, tl_b):
+    import numpy as np
+    a = tl_a.astype(np.float64)
+    b = tl_b.astype(np.float64)
+    mask = b < 100
+    return float(np.max(np.abs(a - b)[mask])) if mask.any() else 0.0
+
+
+def bench_batch(args):
+    """The headline line: the 256-solve Munk batch (see the module docstring)."""
+    import numpy as np
+    import torch
+    rank, world, local = _rank_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2511_03343_gb300 import build as B
+    B.build()
+    from paper_2511_03343_gb300 import inputs, sssp
+    steps = args.range_steps
+    solves = inputs.munk_batch(steps=steps)
+    stream = torch.cuda.current_stream()
+    plans = [sssp.plan_for(s, stream=stream, tl_every=BATCH_TL_EVERY) for s in solves]
+    for pl in plans:
+        pl.set_kernel(args.kernel)
+    u0s = [torch.from_numpy(s.u0.astype(np.complex64)).cuda() for s in solves]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one_step(ev=None):
+        for pl, u0 in zip(plans, u0s):
+            pl.set_field(u0, 0.0)
+        if ev is not None:
+            ev[0].record(stream)
+        sssp.march_batch(plans, steps)
+        if ev is not None:
+            ev[1].record(stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    nd0 = sum(pl.transform_count() for pl in plans)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms, kern_ms = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[2].record(stream)
+        one_step(e)
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e[2].elapsed_time(e[3]))
+        kern_ms.append(e[0].elapsed_time(e[1]))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    nd1 = sum(pl.transform_count() for pl in plans)
+    units_local = float(sum(s.N for s in solves) * steps * args.steps)
+    tot_ms, units = aggregate_over_ranks(sum(step_ms), units_local, device="cuda")
+    value = units / (tot_ms * 1e-3)
+    mg = _load_make_golden()
+    members = sorted(mg.load_batch().keys()) if steps == 2000 else []
+    fields = {i: plans[i].read_field() for i in members}
+    tls = {i: plans[i].read_tl()[0] for i in members}
+    parity = _batch_parity(fields, tls, BATCH_TL_EVERY) if members else None
+
+    # end to end through the public API with host (pinned) buffers: starters H2D, march, TL rows
+    # and fields D2H, every step
+    rows = steps // BATCH_TL_EVERY
+    u0_host = [torch.from_numpy(s.u0.astype(np.complex64)).pin_memory() for s in solves]
+    tl_host = torch.empty(len(solves) * rows * solves[0].N, dtype=torch.float32).pin_memory()
+    field_host = torch.empty(len(solves) * solves[0].N, dtype=torch.complex64).pin_memory()
+    tl_views = [tl_host[i * rows * s.N:(i + 1) * rows * s.N] for i, s in enumerate(solves)]
+    f_views = [field_host[i * s.N:(i + 1) * s.N] for i, s in enumerate(solves)]
+    e2e_ms = []
+    for i in range(0 if args.no_e2e else args.warmup + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for pl, u0 in zip(plans, u0_host):
+            pl.set_field(u0, 0.0)
+        sssp.march_batch(plans, steps)
+        for pl, tv, fv in zip(plans, tl_views, f_views):
+            pl.read_tl(out=tv)
+            pl.read_field(out=fv)
+        el = time.perf_counter() - t0
+        if i >= args.warmup:
+            e2e_ms.append(el * 1e3)
+    e2e_tot = sum(e2e_ms) if e2e_ms else float("nan")
+    e2e_tot, _ = aggregate_over_ranks(e2e_tot, 0.0, device="cuda")
+
+    # roofline of the dominant kernel (the batched march kernel, FP32 ALU bound)
+    kern_avg = sum(kern_ms) / len(kern_ms)
+    dst_per_launch = (nd1 - nd0) / args.steps
+    L = solves[0].N + 1
+    flops = dst_per_launch * (_dst_flops(solves[0].N) + 10.0 * L)
+    achieved = flops / (kern_avg * 1e-3) / 1e12
+    sm_max = float(clk.get("sm_max_mhz") or 2070.0)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
+
+    line = None
+    if rank == 0:
+        plain = None if (args.no_plain or world > 1) else _vs_plain(args, sssp, inputs, solves, members, fields, tls,
+                                                                     stream, flush)
+        served = None if (args.no_served or world > 1) else _served_block(args, sssp, stream)
+        cpu = run_cpu_oracle_sample(args.cpu_seconds, "batch") if (world == 1 and not args.no_cpu) else None
+        bytes_in = sum(s.N for s in solves) * 8
+        bytes_out = sum(s.N for s in solves) * (rows * 4 + 8)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+                "config": _batch_config({"kernel": plans[0].kernel, "range_steps": steps}),
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "traffic": None,
+                             "kernel": f"{plans[0].kernel} march kernel, one launch of 256 solves",
+                             "flops_per_launch": flops, "dst_per_launch": dst_per_launch, "kernel_ms": kern_avg,
+                             "flop_convention": "per DST-I of length N: 5(N+1)log2(N+1) + 10(N+1)",
+                             "peak_note": f"FP32 FMA peak of all {sms} SMs at the sampled max SM clock "
+                                          "(128 lanes x 2 flop per SM per cycle; derived, not measured)"},
+                "e2e": {"value": units / (e2e_tot * 1e-3) if e2e_ms else None, "unit": UNIT,
+                        "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": bytes_out},
+                "gpu_launches": (len(solves) + 1) * args.steps,
+                "clocks": clk, "parity": parity, "vs_plain": plain, "served": served, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    for pl in plans:
+        pl.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _vs_plain(args, sssp, inputs, solves, members, fields, tls, stream, flush):
+    """The same solves marched one plan at a time on the plain marcher (pe_march, one solve on
+    the GPU at a time, the kernel the library picks for one solve): the stored members (lowest,
+    second lowest, then evenly up to the highest frequency), each timed alone with CUDA events;
+    their results against the batched run (bitwise) and their throughput."""
+    import numpy as np
+    import torch
+    out, tot_ms, units, same = {}, 0.0, 0, True
+    worst_tl = 0.0
+    for i in members:
+        s = solves[i]
+        pl = sssp.plan_for(s, stream=stream, tl_every=BATCH_TL_EVERY)
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pl.march(s.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        u = pl.read_field()
+        tl, _ = pl.read_tl()
+        kernel = pl.kernel
+        pl.close()
+        tot_ms += ms
+        units += s.N * s.steps
+        same = same and np.array_equal(u, fields[i]) and np.array_equal(tl, tls[i])
+        worst_tl = max(worst_tl, _tl_vs(tls[i], tl))
+        out[str(i)] = {"freq_hz": round(s.freq, 3), "ms": ms, "kernel": kernel}
+    if not members:
+        return None
+    return {"value": units / (tot_ms * 1e-3), "unit": UNIT, "solves_timed": len(members),
+            "what": "the stored batch members, each marched alone (pe_march), CUDA events per solve",
+            "batched_results_bitwise_equal": bool(same), "max_tl_diff_db_batched_vs_plain": worst_tl,
+            "members": out}
+
+
+def _served_block(args, sssp, stream):
+    """The serving mix: the Poisson trace (default_rng(5), 200 req/s, 1000 requests) replayed in
+    real time through the continuous-batching server with a 120 GB budget, ranges scaled by
+    ``--served-range-scale``; p50/p99 latency (arrival -> result on the host) and throughput.
+    Parity: a few completed requests marched again alone on the plain marcher with the values
+    admission chose (TL difference, bitwise equality)."""
+    import numpy as np
+    from paper_2511_03343_gb300 import inputs, serving
+    trace = inputs.serving_trace(count=args.serve_requests)
+    check = [t["id"] for t in trace if t["N"] <= 1023][:6]
+    res = serving.replay(trace, hbm_budget=120e9, chunk_steps=args.chunk_steps, tl_every=10,
+                         range_scale=args.served_range_scale, stream=stream, keep_ids=check)
+    worst, same = 0.0, True
+    for i, (field, tl, s, prm) in res.pop("results").items():
+        k0, sc, p = prm
+        pl = sssp.Plan(s.N, s.H, k0, s.dr, p, s.neumann_terms, s.neumann_tol, stream=stream)
+        pl.set_output(10)
+        if s.neumann_terms > 1:
+            pl.set_profile_nodes([(r, sc * np.asarray(n2)) for r, n2 in s.profiles])
+        pl.set_field(s.u0, s.r0)
+        pl.march(s.steps)
+        u = pl.read_field()
+        tl2, _ = pl.read_tl()
+        pl.close()
+        same = same and np.array_equal(u, field) and np.array_equal(tl2, tl)
+        if tl.size:
+            worst = max(worst, _tl_vs(tl, tl2))
+    res["parity_vs_plain"] = {"requests": len(check), "bitwise_equal": bool(same), "max_tl_diff_db": worst}
+    res["config"] = {"requests": len(trace), "rate_per_s": 200, "range_scale": args.served_range_scale,
+                     "budget_bytes": 120e9, "chunk_steps": args.chunk_steps, "tl_every": 10,
+                     "admission": "minimax c0 + convergent Pade order"}
+    res.pop("queue_depth", None)
+    return res
 
 
 def _golden_check(tl, u):
@@ -429,7 +712,7 @@ def bench_dst(args):
     print(json.dumps({"metric": "DST-I time per transform", "unit": "us", "rows": rows}), flush=True)
 
 
-def bench_ours(args):
+def bench_munk(args):
     import numpy as np
     import torch
     rank, world, local = _rank_env()
@@ -518,24 +801,22 @@ def bench_ours(args):
     flops = dst_per_launch * (_dst_flops(N) + diag)
     achieved = flops / (kern_avg * 1e-3) / 1e12
     sm_max = float(clk.get("sm_max_mhz") or 2070.0)
-    peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flop x max SM clock
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = sms * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flop x max SM clock
     line = None
     if rank == 0:
-        cpu = run_cpu_oracle_sample(args.cpu_seconds) if (world == 1 and not args.no_cpu) else None
+        cpu = run_cpu_oracle_sample(args.cpu_seconds, "munk") if (world == 1 and not args.no_cpu) else None
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
                 "config": _config({"kernel": pl.kernel}),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                             "frac": achieved / peak,
-                             # DRAM bytes (read + write) of one full march launch, ncu 1-pass capture
-                             # (profiles/march_cluster_kernel_munk_n4095_launch_list.md)
-                             "traffic": (1.49e6 + 0.104e6) if pl.kernel == "cluster" else None,
+                             "frac": achieved / peak, "traffic": None,
                              "kernel": ("sssp_march_cluster_kernel<12, 8> (one solve over an 8-CTA cluster, 8 SMs)"
                                         if pl.kernel == "cluster" else "sssp_march_kernel<12> (one CTA, one SM)"),
                              "flops_per_launch": flops, "dst_per_launch": dst_per_launch,
                              "kernel_ms": kern_avg,
-                             "peak_note": "FP32 FMA peak of all 152 SMs at the sampled max SM clock (derived, not measured)"},
+                             "peak_note": f"FP32 FMA peak of all {sms} SMs at the sampled max SM clock (derived, not measured)"},
                 "e2e": {"value": s.N * s.steps * args.steps * world / (e2e_tot * 1e-3), "unit": UNIT,
                         "h2d_bytes_per_step": s.N * 8, "d2h_bytes_per_step": s.N * s.steps * 4 + s.N * 8},
                 "gpu_launches": 2 * args.steps,
@@ -558,11 +839,15 @@ def main():
     ap.add_argument("--range-steps", type=int, default=2000,
                     help="range steps per march (2000 = the workload; fewer only for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="munk",
+    ap.add_argument("--workload", default="batch",
                     choices=["munk", "batch", "eddy", "iso", "serve", "gemm", "dst", "large"])
     ap.add_argument("--large-count", type=int, default=64, help="solves in the N = 65535 batch ('large')")
-    ap.add_argument("--serve-requests", type=int, default=100)
-    ap.add_argument("--range-scale", type=float, default=0.05)
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--range-scale", type=float, default=1.0)
+    ap.add_argument("--served-range-scale", type=float, default=0.2,
+                    help="range scale of the serving trace replayed inside the default bench line")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--chunk-steps", type=int, default=50)
     ap.add_argument("--serve-baseline", action="store_true")
     ap.add_argument("--batch-count", type=int, default=256)
@@ -577,10 +862,12 @@ def main():
         bench_gemm(args)
     elif args.workload == "dst":
         bench_dst(args)
-    elif args.workload != "munk":
-        bench_other(args)
+    elif args.workload == "munk":
+        bench_munk(args)
+    elif args.workload == "batch":
+        bench_batch(args)
     else:
-        bench_ours(args)
+        bench_other(args)
 
 
 if __name__ == "__main__":

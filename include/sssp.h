@@ -250,6 +250,32 @@ pe_status pe_plan_set_kernel(pe_plan* plan, int kernel);
 pe_status pe_plan_get_kernel(const pe_plan* plan, int* kernel);
 
 /*
+ * Shape of the one-CTA shared-memory kernel (no counterpart in the paper): points per thread
+ * P = 4, 8 (default; 0 means 8) or 16, i.e. L/P threads per solve, each transform a Stockham FFT
+ * of radix-P passes.  4 and 16 take Dirichlet grids with N + 1 in [256, 4096]; PE_ERR_ARG
+ * otherwise.  All shapes compute the same step (results agree to FP32 rounding).
+ * pe_plan_get_shape reports the P a march of the plan runs (0 when it runs the cluster or the
+ * large-grid kernel).
+ */
+pe_status pe_plan_set_shape(pe_plan* plan, int points_per_thread);
+pe_status pe_plan_get_shape(const pe_plan* plan, int* points_per_thread);
+
+/*
+ * Shape autotuners (no counterpart in the paper).  pe_march_batch_autotune times `steps` range
+ * steps of the batched march of `plans` (pe_march_batch) with each shape the plans can take —
+ * one CTA per solve at 4, 8 and 16 points per thread, and one thread-block cluster per solve —
+ * a warm-up run then a timed run each, restores every plan's state and TL bookkeeping after each
+ * run, and sets the fastest shape on every plan that can take it.  ms: 4 floats, the timed
+ * milliseconds of (CTA P=4, CTA P=8, CTA P=16, cluster), -1 where no plan can take the shape, or
+ * NULL; kernel / points_per_thread: the shape chosen, or NULL.  pe_plan_autotune_shapes is the
+ * same for one plan.  Plans need a field (and a profile when Neumann terms are asked for);
+ * synchronises.
+ */
+pe_status pe_march_batch_autotune(pe_plan** plans, int count, int steps, float* ms, int* kernel,
+                                  int* points_per_thread);
+pe_status pe_plan_autotune_shapes(pe_plan* plan, int steps, float* ms, int* kernel, int* points_per_thread);
+
+/*
  * Autotuner (no counterpart in the paper): times `steps` range steps of the plan's own march on
  * each kernel it can take (one CTA; the cluster where supported), a warm-up run then a timed
  * run each, restores the marcher's state and TL bookkeeping after every run (pe_save_state /
@@ -341,7 +367,30 @@ typedef struct {
   const double* node_r;  /* node ranges, non-decreasing */
   int nodes;
   double r0;             /* range of the starter */
+  int flags;             /* PE_ADMIT_* bits (0: march the request as given) */
 } pe_request;
+
+/*
+ * Admission adaptations (no counterpart in the paper).  PE_ADMIT_MINIMAX_C0: the reference
+ * sound speed c0 is chosen to minimise max|V| over the request's profile nodes (n^2 -> s n^2,
+ * k0 -> k0/sqrt(s), s = 2/(min n^2 + max n^2); k0^2 n^2 is unchanged).  PE_ADMIT_CONVERGENT_ORDER:
+ * the Pade order is lowered until the Neumann series (Eq. Neumann) converges for every term j
+ * (the FP64 bound max|V| max_m |b_j/(1 + b_j lambda_m)| below 1, else an FP64 power-iteration
+ * estimate of the spectral radius of -b_j L_j^{-1} V below 0.98, for the node with the largest
+ * max|V|); a request that diverges at every order fails at admission (state 3).  The starter is
+ * kept as given.
+ */
+enum { PE_ADMIT_MINIMAX_C0 = 1, PE_ADMIT_CONVERGENT_ORDER = 2 };
+
+/*
+ * Host-only (no GPU): the admission's FP64 power-iteration estimate of the spectral radius of
+ * the Neumann operator -b L^{-1} V of Eq. (Neumann), L^{-1} = IDST diag(1/(1 + b lambda_m)) DST,
+ * lambda_m = -(pi m/(k0 H))^2, for V at the N interior points (N + 1 a power of two) and one
+ * Pade coefficient b = b_re + i b_im: the geometric mean growth of ||M^k x|| over k = 16..48 from
+ * a fixed start vector.  PE_ERR_ARG on bad sizes.
+ */
+pe_status pe_neumann_radius_estimate(const double* V, int N, double H, double k0, double b_re, double b_im,
+                                     double* rho);
 
 /* hbm_budget_bytes > 0, max_live >= 1 concurrent solves, chunk_steps >= 1 steps per launch. */
 pe_status pe_server_create(pe_server** out, size_t hbm_budget_bytes, int max_live, int chunk_steps, void* cuda_stream);
@@ -358,6 +407,10 @@ pe_status pe_server_state(pe_server* server, unsigned long long id, int* state);
 pe_status pe_server_take(pe_server* server, unsigned long long id, float* field, float* tl, size_t tl_cap,
                          size_t* rows);
 pe_status pe_server_stats(pe_server* server, size_t* bytes_in_use, size_t* peak_bytes, int* peak_live);
+/* The values an admitted request marches with: k0, the factor s its n^2 rows were scaled by,
+ * and its Pade order (each pointer may be NULL).  PE_ERR_STATE while it is still queued. */
+pe_status pe_server_request_params(pe_server* server, unsigned long long id, double* k0, double* n2_scale,
+                                   int* pade_order);
 /* Withdraw a queued or running request (its plan is freed at once; state becomes 3, failed,
  * with the message "cancelled").  PE_ERR_STATE if it already finished. */
 pe_status pe_server_cancel(pe_server* server, unsigned long long id);

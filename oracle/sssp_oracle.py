@@ -342,20 +342,30 @@ class Grid:
         return lambdas_bc(self.N, self.H, self.k0, self.bc)
 
 
-def step_sum(u: np.ndarray, V: np.ndarray, grid: Grid, plan: PadePlan, terms: int, tol: float) -> np.ndarray:
+def step_sum(u: np.ndarray, V: np.ndarray, grid: Grid, plan: PadePlan, terms: int, tol: float,
+             counts: Optional[list] = None) -> np.ndarray:
     """One SSSP range step in the paper's sum form (Algorithm 1):
-    u_n = e^{i k0 dr} (d0 u + sum_j d_j w_j)."""
-    w = neumann_w(u, V, plan.b, grid.lam, terms, tol, bc=grid.bc)
+    u_n = e^{i k0 dr} (d0 u + sum_j d_j w_j).  ``counts``, if given, receives the number of
+    Neumann terms summed for each j (m = 0 included)."""
+    w, c = neumann_w(u, V, plan.b, grid.lam, terms, tol, return_counts=True, bc=grid.bc)
+    if counts is not None:
+        counts.append(np.asarray(c))
     return np.exp(1j * grid.sigma) * (plan.d0 * u + w @ plan.d)
 
 
-def step_product(u: np.ndarray, V: np.ndarray, grid: Grid, plan: PadePlan, terms: int, tol: float) -> np.ndarray:
+def step_product(u: np.ndarray, V: np.ndarray, grid: Grid, plan: PadePlan, terms: int, tol: float,
+                 counts: Optional[list] = None) -> np.ndarray:
     """The same step in Collins' product form prod_j (1 + a_j X)(1 + b_j X)^{-1}: stage j maps
-    y -> (a_j/b_j) y + (1 - a_j/b_j) w_j with (1 + b_j X) w_j = y; then u_n = e^{i k0 dr} P(0) y."""
+    y -> (a_j/b_j) y + (1 - a_j/b_j) w_j with (1 + b_j X) w_j = y; then u_n = e^{i k0 dr} P(0) y.
+    ``counts``, if given, receives the number of Neumann terms summed in each stage."""
     y = u.astype(np.complex128)
+    cs = []
     for aj, bj in zip(plan.a, plan.b):
-        w = neumann_w(y, V, np.array([bj]), grid.lam, terms, tol, bc=grid.bc)[:, 0]
-        y = (aj / bj) * y + (1.0 - aj / bj) * w
+        w, c = neumann_w(y, V, np.array([bj]), grid.lam, terms, tol, return_counts=True, bc=grid.bc)
+        cs.append(int(c[0]))
+        y = (aj / bj) * y + (1.0 - aj / bj) * w[:, 0]
+    if counts is not None:
+        counts.append(np.array(cs))
     return np.exp(1j * grid.sigma) * plan.pc[0] * y
 
 
@@ -386,12 +396,13 @@ class MarchResult:
 
 def march(u0: np.ndarray, profiles, grid: Grid, pade_order: int, steps: int, terms: int, tol: float,
           r0: float = 0.0, form: str = "sum", tl_every: int = 1, plan: Optional[PadePlan] = None,
-          record_steps: Optional[Sequence[int]] = None) -> MarchResult:
+          record_steps: Optional[Sequence[int]] = None, term_counts: Optional[list] = None) -> MarchResult:
     """Algorithm 1: march u0 from range r0 over ``steps`` steps of dr.
 
     The step from r to r + dr uses V = n^2 - 1 of the node in force at r + dr/2.  TL is
     recorded after every ``tl_every``-th step (tl_every = 0: never); ``record_steps``
-    overrides that with an explicit list of 1-based step numbers.
+    overrides that with an explicit list of 1-based step numbers.  ``term_counts``, if given,
+    receives one array per step: the Neumann terms summed for each Pade term j.
     """
     plan = plan or pade_plan(grid.sigma, pade_order)
     stepper = step_sum if form == "sum" else step_product
@@ -401,7 +412,10 @@ def march(u0: np.ndarray, profiles, grid: Grid, pade_order: int, steps: int, ter
     rec = set(record_steps) if record_steps is not None else None
     for n in range(1, steps + 1):
         V = profile_at(profiles, r + 0.5 * grid.dr) - 1.0
-        u = stepper(u, V, grid, plan, terms if terms > 1 else 1, tol)
+        if term_counts is None:
+            u = stepper(u, V, grid, plan, terms if terms > 1 else 1, tol)
+        else:
+            u = stepper(u, V, grid, plan, terms if terms > 1 else 1, tol, counts=term_counts)
         r = r0 + n * grid.dr
         want = (n in rec) if rec is not None else (tl_every > 0 and n % tl_every == 0)
         if want:

@@ -18,9 +18,11 @@
 //   y_n = sin(pi n/L)(x_n + x_{L-n}) + (x_n - x_{L-n})/2,  Y = FFT_L(y),
 //   S_{2k} = (i/2)(Y_k - Y_{L-k}),  S_{2k+1} = S_{2k-1} + (Y_k + Y_{L-k})/2,  S_{-1} = -S_1,
 // with a block-wide prefix scan for the odd outputs.  The FFT is a Stockham autosort FFT
-// with radix-8 passes (one radix-8 butterfly per thread, 8 points per thread) and a final
-// radix-2/4 pass, ping-ponging between two padded shared buffers (index i stored at
-// i + i/16 to spread the strided accesses over the banks).
+// with radix-P passes (P = 4, 8 or 16 points per thread: one radix-P butterfly per thread per
+// pass) and a final smaller-radix pass, ping-ponging between two padded shared buffers (index i
+// stored at i + i/16 to spread the strided accesses over the banks).  P trades threads for
+// passes: P = 4 gives twice the warps of P = 8 (latency hiding) at more passes and barriers,
+// P = 16 half the warps at fewer passes; the library times them per plan (pe_plan_autotune).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -64,15 +66,21 @@ struct SolveDesc {
   int N;
 };
 
-template <int LOG2L>
+template <int LOG2L, int PPT = 8>
 struct Cfg {
   static constexpr int L = 1 << LOG2L;
-  static constexpr int NT = L / 8;            // threads per CTA, 8 points each
+  static constexpr int P = PPT;               // points per thread (radix of the passes)
+  static constexpr int HALF = PPT / 2;        // DST-I output pairs per thread
+  static constexpr int NT = L / PPT;          // threads per CTA
   static constexpr int PADL = L + L / 16;     // padded buffer length
   static constexpr int WS = NT >= 32 ? 32 : NT;
   static constexpr int NW = (NT + 31) / 32;
   static constexpr unsigned MASK = NT >= 32 ? 0xffffffffu : ((1u << NT) - 1u);
-  static constexpr int MIN_BLOCKS = NT >= 512 ? 1 : (512 / NT > 16 ? 16 : 512 / NT);
+  // CTAs per SM the register budget is sized for: 128 registers per thread for P <= 8, 255 for
+  // P = 16 (its 16-point butterflies hold 3 x 16 complex values), at most 16 CTAs
+  static constexpr int REGS = PPT <= 8 ? 128 : 256;
+  static constexpr int MB0 = 65536 / ((NT < 32 ? 32 : NT) * REGS);  // registers go by whole warps
+  static constexpr int MIN_BLOCKS = MB0 >= 16 ? 16 : (MB0 < 1 ? 1 : MB0);
   // dynamic shared memory: 2 padded buffers, twiddles, t_0 and B_j areas, sin weights, V row,
   // scan + reduce
   static constexpr size_t SMEM = sizeof(float2) * (2 * PADL + 3 * L) + sizeof(float) * (2 * L) +
@@ -92,6 +100,15 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 mul_negi(float2 x) { return make_float2(x.y, -x.x); }
 __device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+
+// Stop test of the Neumann series (Eq. Neumann; stop after term m once ||t_m|| <= tol ||w_j||),
+// compared in FP64: the sums of squares nt2 = ||t_m||^2 and nw2 = ||w_j||^2 are widened to
+// double and tested against tol^2 held in double.  (They are accumulated in FP32: a sum of
+// positive terms carries a relative rounding error below 1e-6, which moves the threshold on the
+// norm by less than a millionth of itself.)
+__device__ __forceinline__ bool neumann_stop(float nt2, float nw2, double tol2) {
+  return double(nt2) <= tol2 * double(nw2);
+}
 
 // y * (hi + lo) with the hi/lo split of a multiplier: the product is rounded, the
 // multiplier is not, so no fixed per-mode error builds up over the steps.
@@ -176,13 +193,13 @@ __device__ __forceinline__ void dftR(float2 (&v)[R]) {
 
 // One Stockham pass of radix R over span NS: butterfly j reads src[j + r L/R], applies the
 // twiddles exp(-2 pi i r k/(NS R)), k = j mod NS, and writes dst[(j - k) R + k + r NS].
-// Twiddles come from a per-pass table tw[(NS - 8) + (r - 1) NS + k] (k contiguous, so a
-// half-warp reads 16 consecutive entries or broadcasts).
-template <int LOG2L, int R, int NS>
+// Twiddles come from a per-pass table tw[(NS - P) + (r - 1) NS + k] (k contiguous, so a
+// half-warp reads 16 consecutive entries or broadcasts), P the first pass's radix.
+template <int LOG2L, int R, int NS, int PPT = 8>
 __device__ __forceinline__ void fft_pass(const float2* __restrict__ src, float2* __restrict__ dst,
                                          const float2* __restrict__ tw) {
-  constexpr int L = 1 << LOG2L, NT = L / 8, NB = L / R, PER = NB / NT;
-  constexpr int OFF = NS - 8;
+  constexpr int L = 1 << LOG2L, NT = L / PPT, NB = L / R, PER = NB / NT;
+  constexpr int OFF = NS - PPT;  // the passes before span NS took (NS - PPT) entries
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int j = threadIdx.x + q * NT;
@@ -201,59 +218,58 @@ __device__ __forceinline__ void fft_pass(const float2* __restrict__ src, float2*
   }
 }
 
-template <int LOG2L, int NS>
+template <int LOG2L, int NS, int PPT = 8>
 __device__ __forceinline__ float2* fft_rest(float2* src, float2* dst, const float2* tw) {
   constexpr int L = 1 << LOG2L;
   if constexpr (NS >= L) {
     return src;
   } else {
-    constexpr int R = (L / NS) >= 8 ? 8 : (L / NS);
-    fft_pass<LOG2L, R, NS>(src, dst, tw);
+    constexpr int R = (L / NS) >= PPT ? PPT : (L / NS);
+    fft_pass<LOG2L, R, NS, PPT>(src, dst, tw);
     __syncthreads();
-    return fft_rest<LOG2L, NS * R>(dst, src, tw);
+    return fft_rest<LOG2L, NS * R, PPT>(dst, src, tw);
   }
 }
 
 // Unnormalised DST-I of the L values in `a` (natural order, padded; a[0] is ignored) into
-// out[0..8) = S_{8t..8t+8) of thread t (S_0 = 0).  Uses `b` as the ping-pong buffer.
+// out[0..P) = S_{P t..P t+P) of thread t (S_0 = 0).  Uses `b` as the ping-pong buffer.
 // On return every thread has finished reading both buffers.
-template <int LOG2L>
+template <int LOG2L, int PPT = 8>
 __device__ __forceinline__ void dst_block(float2* a, float2* b, const float2* __restrict__ tw,
-                                          const float* __restrict__ sinw, float2* scan_s, float2 (&out)[8]) {
-  using C = Cfg<LOG2L>;
-  constexpr int L = C::L;
+                                          const float* __restrict__ sinw, float2* scan_s, float2 (&out)[PPT]) {
+  using C = Cfg<LOG2L, PPT>;
+  constexpr int L = C::L, H = C::HALF;
   const int t = threadIdx.x;
-  {  // first radix-8 pass (span 1, no twiddles), fused with the sine pre-weighting
-    float2 v[8];
+  {  // first radix-P pass (span 1, no twiddles), fused with the sine pre-weighting
+    float2 v[PPT];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int n = t + r * (L / 8);
+    for (int r = 0; r < PPT; ++r) {
+      const int n = t + r * (L / PPT);
       const float2 xn = a[pidx(n)];
       const float2 xm = a[pidx((L - n) & (L - 1))];
       const float s = sinw[n];
       v[r] = make_float2(fmaf(s, xn.x + xm.x, 0.5f * (xn.x - xm.x)), fmaf(s, xn.y + xm.y, 0.5f * (xn.y - xm.y)));
     }
-    dft8(v);
+    dftR<PPT>(v);
 #pragma unroll
-    for (int r = 0; r < 8; ++r) b[pidx(8 * t + r)] = v[r];
+    for (int r = 0; r < PPT; ++r) b[pidx(PPT * t + r)] = v[r];
   }
   __syncthreads();
-  const float2* F = fft_rest<LOG2L, 8>(b, a, tw);
+  const float2* F = fft_rest<LOG2L, PPT, PPT>(b, a, tw);
   // post-processing: even outputs from pairs (k, L-k), odd outputs by a prefix scan
-  float2 se[4], dd[4];
+  float2 se[H], dd[H];
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    const int k = 4 * t + s;
+  for (int s = 0; s < H; ++s) {
+    const int k = H * t + s;
     const float2 yk = F[pidx(k)];
     const float2 ym = F[pidx((L - k) & (L - 1))];
     se[s] = make_float2(-0.5f * (yk.y - ym.y), 0.5f * (yk.x - ym.x));
     dd[s] = (k == 0) ? 0.5f * yk : 0.5f * (yk + ym);
   }
-  dd[1] = dd[1] + dd[0];
-  dd[2] = dd[2] + dd[1];
-  dd[3] = dd[3] + dd[2];
+#pragma unroll
+  for (int s = 1; s < H; ++s) dd[s] = dd[s] + dd[s - 1];
   const int lane = t & 31, warp = t >> 5;
-  float2 inc = dd[3];
+  float2 inc = dd[H - 1];
 #pragma unroll
   for (int o = 1; o < C::WS; o <<= 1) {
     const float nx = __shfl_up_sync(C::MASK, inc.x, o, C::WS);
@@ -272,7 +288,7 @@ __device__ __forceinline__ void dst_block(float2* a, float2* b, const float2* __
     __syncthreads();
   }
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
+  for (int s = 0; s < H; ++s) {
     out[2 * s] = se[s];
     out[2 * s + 1] = dd[s] + excl;
   }
@@ -285,29 +301,29 @@ constexpr int kBcPeriodic = 1;
 
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
-// Unnormalised DFT of the L values in `a` (natural order, padded) into out[0..8) = X_{8t..8t+8)
+// Unnormalised DFT of the L values in `a` (natural order, padded) into out[0..P) = X_{Pt..Pt+P)
 // of thread t; INV uses e^{+2 pi i n m/L} (by conjugating input and output).  On return every
 // thread has finished reading both buffers.
-template <int LOG2L, bool INV>
-__device__ __forceinline__ void dft_block(float2* a, float2* b, const float2* __restrict__ tw, float2 (&out)[8]) {
+template <int LOG2L, bool INV, int PPT = 8>
+__device__ __forceinline__ void dft_block(float2* a, float2* b, const float2* __restrict__ tw, float2 (&out)[PPT]) {
   constexpr int L = 1 << LOG2L;
   const int t = threadIdx.x;
   {
-    float2 v[8];
+    float2 v[PPT];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const float2 x = a[pidx(t + r * (L / 8))];
+    for (int r = 0; r < PPT; ++r) {
+      const float2 x = a[pidx(t + r * (L / PPT))];
       v[r] = INV ? conjf2(x) : x;
     }
-    dft8(v);
+    dftR<PPT>(v);
 #pragma unroll
-    for (int r = 0; r < 8; ++r) b[pidx(8 * t + r)] = v[r];
+    for (int r = 0; r < PPT; ++r) b[pidx(PPT * t + r)] = v[r];
   }
   __syncthreads();
-  const float2* F = fft_rest<LOG2L, 8>(b, a, tw);
+  const float2* F = fft_rest<LOG2L, PPT, PPT>(b, a, tw);
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const float2 x = F[pidx(8 * t + i)];
+  for (int i = 0; i < PPT; ++i) {
+    const float2 x = F[pidx(PPT * t + i)];
     out[i] = INV ? conjf2(x) : x;
   }
   __syncthreads();
@@ -315,27 +331,27 @@ __device__ __forceinline__ void dft_block(float2* a, float2* b, const float2* __
 
 // The transform of the boundary condition: TO_DEPTH maps spectral coefficients to depth values
 // (the inverse transform up to the scale folded into the tables), otherwise depth -> spectral.
-template <int LOG2L, int BC, bool TO_DEPTH>
+template <int LOG2L, int BC, bool TO_DEPTH, int PPT = 8>
 __device__ __forceinline__ void xform(float2* a, float2* b, const float2* __restrict__ tw,
-                                      const float* __restrict__ sinw, float2* scan_s, float2 (&out)[8]) {
+                                      const float* __restrict__ sinw, float2* scan_s, float2 (&out)[PPT]) {
   if constexpr (BC == kBcPeriodic) {
-    dft_block<LOG2L, TO_DEPTH>(a, b, tw, out);
+    dft_block<LOG2L, TO_DEPTH, PPT>(a, b, tw, out);
   } else {
-    dst_block<LOG2L>(a, b, tw, sinw, scan_s, out);  // DST-I is its own inverse
+    dst_block<LOG2L, PPT>(a, b, tw, sinw, scan_s, out);  // DST-I is its own inverse
   }
 }
 
-template <int LOG2L>
+template <int LOG2L, int PPT = 8>
 __device__ __forceinline__ void load_tables(float2* tw, float* sinw, const float2* __restrict__ tw_g,
                                             const float* __restrict__ sin_g) {
-  using C = Cfg<LOG2L>;
+  using C = Cfg<LOG2L, PPT>;
   for (int i = threadIdx.x; i < C::L; i += C::NT) {
     tw[i] = tw_g[i];
     sinw[i] = sin_g[i];
   }
 }
 
-template <int LOG2L>
+template <int LOG2L, int PPT = 8>
 struct Smem {
   float2* bufA;
   float2* bufB;
@@ -348,7 +364,7 @@ struct Smem {
   float2* scan_s;
   float* red;
   __device__ __forceinline__ explicit Smem(unsigned char* base) {
-    using C = Cfg<LOG2L>;
+    using C = Cfg<LOG2L, PPT>;
     bufA = reinterpret_cast<float2*>(base);
     bufB = bufA + C::PADL;
     tw = bufB + C::PADL;
@@ -362,55 +378,56 @@ struct Smem {
   }
 };
 
-template <int LOG2L>
-__device__ __forceinline__ void load8(const float2* __restrict__ p, float2 (&v)[8]) {
+// P consecutive complex values of one thread, 16-byte vector accesses (P even, p 16-byte aligned)
+template <int LOG2L, int PPT = 8>
+__device__ __forceinline__ void load8(const float2* __restrict__ p, float2 (&v)[PPT]) {
   const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < PPT / 2; ++i) {
     const float4 x = __ldg(q + i);
     v[2 * i] = make_float2(x.x, x.y);
     v[2 * i + 1] = make_float2(x.z, x.w);
   }
 }
 
-template <int LOG2L>
-__device__ __forceinline__ void store8(float2* p, const float2 (&v)[8]) {
+template <int LOG2L, int PPT = 8>
+__device__ __forceinline__ void store8(float2* p, const float2 (&v)[PPT]) {
   float4* q = reinterpret_cast<float4*>(p);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) q[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+  for (int i = 0; i < PPT / 2; ++i) q[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
 }
 
 // TL row after a step: physical envelope u = (2/L) DST(y), TL = -20 log10|u| + 10 log10 r.
-template <int LOG2L, int BC>
-__device__ __forceinline__ void record_tl(Smem<LOG2L>& sm, const SolveDesc& d, const float2 (&y)[8], float out_scale,
-                                          int s, int nrec) {
+template <int LOG2L, int BC, int PPT = 8>
+__device__ __forceinline__ void record_tl(Smem<LOG2L, PPT>& sm, const SolveDesc& d, const float2 (&y)[PPT],
+                                          float out_scale, int s, int nrec) {
   const int t = threadIdx.x;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) sm.bufA[pidx(8 * t + i)] = out_scale * y[i];
+  for (int i = 0; i < PPT; ++i) sm.bufA[pidx(PPT * t + i)] = out_scale * y[i];
   __syncthreads();
-  float2 u[8];
-  xform<LOG2L, BC, true>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, u);
+  float2 u[PPT];
+  xform<LOG2L, BC, true, PPT>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, u);
   const float lr = float(10.0 * log10(d.r0 + double(s + 1) * d.dr));
   float* row = d.tl + (size_t)(d.rec0 + nrec) * d.N;
   constexpr int off = (BC == kBcPeriodic) ? 0 : 1;  // Dirichlet: depth index 0 is the boundary
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int n = 8 * t + i;
+  for (int i = 0; i < PPT; ++i) {
+    const int n = PPT * t + i;
     if (n >= off) row[n - off] = fmaf(-10.f, log10f(cabs2(u[i])), lr);
   }
 }
 
 // ---------------------------------------------------------------------------------------
-// The persistent march: blockIdx.x selects the solve.
+// The persistent march: blockIdx.x selects the solve; thread t owns the modes [P t, P t + P).
 // ---------------------------------------------------------------------------------------
-template <int LOG2L, bool CPLX, int BC>
-__global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
+template <int LOG2L, bool CPLX, int BC, int PPT = 8>
+__global__ void __launch_bounds__(Cfg<LOG2L, PPT>::NT, Cfg<LOG2L, PPT>::MIN_BLOCKS)
     sssp_march_kernel(const SolveDesc* __restrict__ descs, const float2* __restrict__ tw_g,
                       const float* __restrict__ sin_g) {
-  using C = Cfg<LOG2L>;
-  constexpr int L = C::L;
+  using C = Cfg<LOG2L, PPT>;
+  constexpr int L = C::L, P = PPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<LOG2L> sm(smem_raw);
+  Smem<LOG2L, PPT> sm(smem_raw);
   __shared__ SolveDesc d;
   const int t = threadIdx.x;
   const int lane = t & 31, warp = t >> 5;
@@ -419,14 +436,13 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
     int* dst = reinterpret_cast<int*>(&d);
     for (int i = t; i < int(sizeof(SolveDesc) / sizeof(int)); i += C::NT) dst[i] = src[i];
   }
-  load_tables<LOG2L>(sm.tw, sm.sinw, tw_g, sin_g);
+  load_tables<LOG2L, PPT>(sm.tw, sm.sinw, tw_g, sin_g);
   __syncthreads();
 
-  float2 y[8];
-  load8<LOG2L>(d.yhat + 8 * t, y);
+  float2 y[P];
+  load8<LOG2L, P>(d.yhat + P * t, y);
   const float out_scale = (BC == kBcPeriodic ? 1.0f : 2.0f) / float(L);
   const bool iso = d.terms <= 1;
-  const float tol2f = float(d.tol2);
   int status = kStatusOk;
   unsigned int ndst = 0;
   int nrec = 0;
@@ -445,18 +461,18 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
 
   if (iso) {
     // V ignored: every step is the diagonal multiply by G = prod_j R_j
-    float4 G[8];
+    float4 G[P];
     {
-      const float4* g = d.G + 8 * t;
+      const float4* g = d.G + P * t;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) G[i] = __ldg(g + i);
+      for (int i = 0; i < P; ++i) G[i] = __ldg(g + i);
     }
     for (int s = 0; s < d.steps; ++s) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) y[i] = ffmul(G[i], y[i]);
+      for (int i = 0; i < P; ++i) y[i] = ffmul(G[i], y[i]);
       const long long gs = d.step0 + s + 1;
       if (d.tl_every > 0 && gs % d.tl_every == 0) {
-        record_tl<LOG2L, BC>(sm, d, y, out_scale, s, nrec);
+        record_tl<LOG2L, BC, P>(sm, d, y, out_scale, s, nrec);
         ++ndst;
         ++nrec;
       }
@@ -476,42 +492,42 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
         // first read of Vs is after the syncs of the stage's first transform
       }
       for (int j = 0; j < d.p && status == kStatusOk; ++j) {
-        float2 acc[8], tp[8];
+        float2 acc[P], tp[P];
         {
-          float2 Bj[8];
-          load8<LOG2L>(d.B + (size_t)j * L + 8 * t, Bj);
+          float2 Bj[P];
+          load8<LOG2L, P>(d.B + (size_t)j * L + P * t, Bj);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) sm.Bs[i * C::NT + t] = Bj[i];
+          for (int i = 0; i < P; ++i) sm.Bs[i * C::NT + t] = Bj[i];
         }
         {
-          float2 Aj[8];
-          load8<LOG2L>(d.A + (size_t)j * L + 8 * t, Aj);
+          float2 Aj[P];
+          load8<LOG2L, P>(d.A + (size_t)j * L + P * t, Aj);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
+          for (int i = 0; i < P; ++i) {
             const float2 t0 = cmul(Aj[i], y[i]);
             sm.t0s[i * C::NT + t] = t0;
-            sm.bufA[pidx(8 * t + i)] = t0;
+            sm.bufA[pidx(P * t + i)] = t0;
             acc[i] = make_float2(0.f, 0.f);
           }
         }
         __syncthreads();
-        xform<LOG2L, BC, true>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // t_0 in depth space
+        xform<LOG2L, BC, true, P>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // t_0 in depth space
         ++ndst;
         float first = 0.f;
         for (int m = 1; m < d.terms; ++m) {
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
+          for (int i = 0; i < P; ++i) {
             if constexpr (cplx)
-              sm.bufA[pidx(8 * t + i)] = cmul(make_float2(sm.Vs[8 * t + i], sm.Vis[8 * t + i]), tp[i]);
+              sm.bufA[pidx(P * t + i)] = cmul(make_float2(sm.Vs[P * t + i], sm.Vis[P * t + i]), tp[i]);
             else
-              sm.bufA[pidx(8 * t + i)] = sm.Vs[8 * t + i] * tp[i];
+              sm.bufA[pidx(P * t + i)] = sm.Vs[P * t + i] * tp[i];
           }
           __syncthreads();
-          xform<LOG2L, BC, false>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // T(V t_{m-1})
+          xform<LOG2L, BC, false, P>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // T(V t_{m-1})
           ++ndst;
           float nt = 0.f, nw = 0.f;
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
+          for (int i = 0; i < P; ++i) {
             tp[i] = cmul(sm.Bs[i * C::NT + t], tp[i]);  // spectral t_m (scaled by 2/L)
             acc[i] = acc[i] + tp[i];
             nt += cabs2(tp[i]);
@@ -529,7 +545,7 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
           const bool last = (m == d.terms - 1);
           if (!last) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) sm.bufA[pidx(8 * t + i)] = tp[i];
+            for (int i = 0; i < P; ++i) sm.bufA[pidx(P * t + i)] = tp[i];
           }
           __syncthreads();
           if (last) break;
@@ -555,35 +571,35 @@ __global__ void __launch_bounds__(Cfg<LOG2L>::NT, Cfg<LOG2L>::MIN_BLOCKS)
             status = kStatusDiverged;
             break;
           }
-          if (snt <= tol2f * snw) break;
-          xform<LOG2L, BC, true>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // t_m in depth space
+          if (neumann_stop(snt, snw, d.tol2)) break;
+          xform<LOG2L, BC, true, P>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // t_m in depth space
           ++ndst;
         }
         {
-          const float4* rp = d.R + (size_t)j * L + 8 * t;
+          const float4* rp = d.R + (size_t)j * L + P * t;
           const float2 bj = d.beta[j];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) y[i] = ffmul(__ldg(rp + i), y[i]) + cmul(bj, acc[i]);
+          for (int i = 0; i < P; ++i) y[i] = ffmul(__ldg(rp + i), y[i]) + cmul(bj, acc[i]);
         }
       }
       if (status != kStatusOk) break;
       const long long gs = d.step0 + s + 1;
       if (d.tl_every > 0 && gs % d.tl_every == 0) {
-        record_tl<LOG2L, BC>(sm, d, y, out_scale, s, nrec);
+        record_tl<LOG2L, BC, P>(sm, d, y, out_scale, s, nrec);
         ++ndst;
         ++nrec;
       }
     }
   }
-  store8<LOG2L>(d.yhat + 8 * t, y);
+  store8<LOG2L, P>(d.yhat + P * t, y);
   // physical envelope for pe_read_field
 #pragma unroll
-  for (int i = 0; i < 8; ++i) sm.bufA[pidx(8 * t + i)] = out_scale * y[i];
+  for (int i = 0; i < P; ++i) sm.bufA[pidx(P * t + i)] = out_scale * y[i];
   __syncthreads();
-  float2 u[8];
-  xform<LOG2L, BC, true>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, u);
+  float2 u[P];
+  xform<LOG2L, BC, true, P>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, u);
   ++ndst;
-  store8<LOG2L>(d.field + 8 * t, u);
+  store8<LOG2L, P>(d.field + P * t, u);
   if (t == 0) {
     if (status != kStatusOk) atomicMax(d.status, status);
     atomicAdd(d.ndst, (unsigned long long)ndst);

@@ -21,6 +21,7 @@ struct pe_plan {
                     // the even extension of the field to [0, 2H])
   int N_user = 0;   // grid points the caller sees
   int kernel = 0;   // PE_KERNEL_AUTO / PE_KERNEL_CTA / PE_KERNEL_CLUSTER
+  int ppt = 8;      // points per thread of the one-CTA kernel (4, 8 or 16; pe_plan_set_shape)
   int off = 1;  // index of the first stored depth point in the length-L arrays
   double H = 0, k0 = 0, dr = 0, tol = 0;
   cudaStream_t stream = nullptr;
@@ -48,6 +49,7 @@ struct pe_plan {
   std::vector<double> tl_ranges;
   int tl_every = 0;
   sssp::SolveDesc* dDesc = nullptr;
+  size_t desc_cap = 0;  // bytes of dDesc (batched marches led by this plan reuse it)
   double r_set = 0.0;
   long long steps_done = 0;
   bool field_set = false;

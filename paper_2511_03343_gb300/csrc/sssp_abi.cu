@@ -21,6 +21,7 @@
 #include "march_large.cuh"
 #include "pade_host.h"
 #include "plan_internal.h"
+#include "shape_launch.h"
 
 using sssp::Cfg;
 using sssp::SolveDesc;
@@ -36,12 +37,13 @@ constexpr int kMaxTerms = 64;
 thread_local std::string g_create_error;
 
 std::mutex g_tab_mu;
-std::map<std::pair<int, int>, TransformTables> g_tabs;  // (device, log2L)
+std::map<std::tuple<int, int, int>, TransformTables> g_tabs;  // (device, log2L, points per thread)
 
-// twiddles / sine weights in FP64, rounded once to FP32 (shared by all plans of a size)
-cudaError_t get_tables(int device, int log2L, TransformTables* out) {
+// twiddles / sine weights in FP64, rounded once to FP32 (shared by all plans of a size and
+// shape)
+cudaError_t get_tables(int device, int log2L, TransformTables* out, int ppt = 8) {
   std::lock_guard<std::mutex> lk(g_tab_mu);
-  auto key = std::make_pair(device, log2L);
+  auto key = std::make_tuple(device, log2L, ppt);
   auto it = g_tabs.find(key);
   if (it != g_tabs.end()) {
     *out = it->second;
@@ -51,14 +53,14 @@ cudaError_t get_tables(int device, int log2L, TransformTables* out) {
   std::vector<float2> tw(L, make_float2(0.f, 0.f));
   std::vector<float> sw(L);
   for (int q = 0; q < L; ++q) sw[q] = float(std::sin(M_PI * double(q) / double(L)));
-  // per-pass Stockham twiddles exp(-2 pi i r k/(NS R)) at (NS - 8) + (r - 1) NS + k for the
-  // passes after the first (spans NS = 8, 64, ...; radix R = min(8, L/NS)); L - 8 entries
-  for (int ns = 8; ns < L; ns *= 8) {
-    const int R = std::min(8, L / ns);
+  // per-pass Stockham twiddles exp(-2 pi i r k/(NS R)) at (NS - P) + (r - 1) NS + k for the
+  // passes after the first (spans NS = P, P^2, ...; radix R = min(P, L/NS)); L - P entries
+  for (int ns = ppt; ns < L; ns *= std::min(ppt, L / ns)) {
+    const int R = std::min(ppt, L / ns);
     for (int r = 1; r < R; ++r)
       for (int k = 0; k < ns; ++k) {
         const double ang = 2.0 * M_PI * double(r) * double(k) / (double(ns) * double(R));
-        tw[(ns - 8) + (r - 1) * ns + k] = make_float2(float(std::cos(ang)), float(-std::sin(ang)));
+        tw[(ns - ppt) + (r - 1) * ns + k] = make_float2(float(std::cos(ang)), float(-std::sin(ang)));
       }
   }
   TransformTables t;
@@ -237,7 +239,11 @@ cudaError_t launch_dst_large_t(const float2* in, float2* out, float scale, float
 }
 
 cudaError_t launch_march(int log2L, const SolveDesc* d, int count, const TransformTables& tabs, cudaStream_t st,
-                         bool cplx, int bc) {
+                         bool cplx, int bc, int ppt = 8) {
+  if (ppt != 8) {  // the one-CTA kernel at 4 or 16 points per thread (Dirichlet, L <= 4096)
+    if (bc != sssp::kBcDirichlet) return cudaErrorInvalidValue;
+    return sssp_shapes::launch_march(log2L, ppt, d, count, tabs.tw, tabs.sinw, st, cplx);
+  }
   switch (log2L) {
     case 3: return launch_march_t<3>(d, count, tabs, st, cplx, bc);
     case 4: return launch_march_t<4>(d, count, tabs, st, cplx, bc);
@@ -395,6 +401,23 @@ bool use_cluster(const pe_plan* p, bool cplx, int group = 1) {
   if (sssp_cluster::max_active_clusters(p->log2L, cplx, &clusters) != cudaSuccess || clusters < 1) return false;
   if (p->kernel == PE_KERNEL_AUTO && p->log2L == 12 && group > clusters) return false;
   return true;
+}
+
+// Points per thread of the one-CTA shared-memory kernel a march of this plan runs (8 unless a
+// shape was set and is supported; grids beyond one CTA's shared memory take no shape).
+int shape_of(const pe_plan* p) {
+  if (p->ppt == 8 || p->ppt == 0) return 8;
+  if (p->bc != PE_BC_DIRICHLET || !sssp_shapes::supported(p->log2L, p->ppt)) return 8;
+  return p->ppt;
+}
+
+// Transform tables of the plan's shape on its device
+cudaError_t tables_for(const pe_plan* p, int ppt, TransformTables* out) {
+  if (ppt == 8) {
+    *out = p->tabs;
+    return cudaSuccess;
+  }
+  return get_tables(p->device, p->log2L, out, ppt);
 }
 
 // Fill the descriptor for one march of `steps` steps and reserve its TL rows.
@@ -636,6 +659,7 @@ pe_status pe_plan_create_bc(pe_plan** out, int N, double H, double k0, double dr
     return bail(e, "cudaMalloc(workspace)");
   if ((e = cudaMalloc(&p->dNdst, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMalloc");
   if ((e = cudaMalloc(&p->dDesc, sizeof(SolveDesc))) != cudaSuccess) return bail(e, "cudaMalloc");
+  p->desc_cap = sizeof(SolveDesc);
   if ((e = cudaMemcpy(p->dR, R.data(), sizeof(float4) * R.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "upload");
   if ((e = cudaMemcpy(p->dA, A.data(), sizeof(float2) * A.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "upload");
   if ((e = cudaMemcpy(p->dB, B.data(), sizeof(float2) * B.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "upload");
@@ -767,14 +791,57 @@ pe_status pe_march(pe_plan* p, int steps) {
   pe_status st = prepare_desc(p, steps, &d);
   if (st != PE_OK) return st;
   if (steps == 0) return PE_OK;
-  PE_CUDA(p, cudaMemcpyAsync(p->dDesc, &d, sizeof(d), cudaMemcpyHostToDevice, p->stream));
+  PE_CUDA(p, cudaMemcpyAsync(p->dDesc, &d, sizeof(d), cudaMemcpyHostToDevice, p->stream));  // capacity >= 1
   const bool cplx = d.Vi != nullptr;
-  if (use_cluster(p, cplx))
+  if (use_cluster(p, cplx)) {
     PE_CUDA(p, sssp_cluster::launch_march(p->log2L, p->dDesc, 1, p->stream, cplx, p->device));
-  else
-    PE_CUDA(p, launch_march(p->log2L, p->dDesc, 1, p->tabs, p->stream, cplx, p->bc));
+  } else {
+    const int ppt = (p->log2L <= kMaxSmemLog2) ? shape_of(p) : 8;
+    TransformTables tb;
+    PE_CUDA(p, tables_for(p, ppt, &tb));
+    PE_CUDA(p, launch_march(p->log2L, p->dDesc, 1, tb, p->stream, cplx, p->bc, ppt));
+  }
   return PE_OK;
 }
+
+}  // extern "C"
+
+namespace {
+
+// Streams, events and descriptor arrays of batched marches, per device (kept for the process):
+// group g of a batch always runs on stream g and reads descriptor array g, so a later batch's
+// upload into array g is ordered after the earlier batch's launch that read it.
+struct BatchLanes {
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> done;
+  std::vector<SolveDesc*> descs;
+  std::vector<size_t> cap;
+  cudaEvent_t fork = nullptr;
+};
+std::mutex g_lanes_mu;
+std::map<int, BatchLanes> g_lanes;
+
+cudaError_t lanes_for(int device, int groups, BatchLanes** out) {
+  BatchLanes& b = g_lanes[device];
+  cudaError_t e = cudaSuccess;
+  if (!b.fork && (e = cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+  while (int(b.streams.size()) < groups) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+    b.streams.push_back(st);
+    b.done.push_back(ev);
+    b.descs.push_back(nullptr);
+    b.cap.push_back(0);
+  }
+  *out = &b;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
 
 pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
   if (!plans || !steps || count < 0) return PE_ERR_ARG;
@@ -787,10 +854,11 @@ pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
     if (plans[i]->device != p0->device) return fail(p0, PE_ERR_ARG, "plans on different devices");
     if (steps[i] < 0) return fail(p0, PE_ERR_ARG, "steps must be >= 0");
   }
-  // group by (size, complex profile, boundary condition, kernel), one launch per group; every
-  // CTA (or cluster) marches its own plan its own step count
-  std::map<std::tuple<int, bool, int, bool>, std::vector<SolveDesc>> groups;
-  std::map<std::tuple<int, bool, int, bool>, TransformTables> tabs;
+  // group by (size, complex profile, boundary condition, kernel, shape), one launch per group;
+  // every CTA (or cluster) marches its own plan its own step count
+  using GroupKey = std::tuple<int, bool, int, bool, int>;
+  std::map<GroupKey, std::vector<SolveDesc>> groups;
+  std::map<GroupKey, TransformTables> tabs;
   std::map<std::tuple<int, bool, int>, int> size_count;  // solves per (size, complex, bc)
   for (int i = 0; i < count; ++i)
     if (steps[i] > 0)
@@ -805,22 +873,66 @@ pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
     }
     const bool cplx = d.Vi != nullptr;
     const int group = size_count[std::make_tuple(plans[i]->log2L, plans[i]->complex_profile, plans[i]->bc)];
-    const auto key = std::make_tuple(plans[i]->log2L, cplx, plans[i]->bc, use_cluster(plans[i], cplx, group));
+    const bool cl = use_cluster(plans[i], cplx, group);
+    const int ppt = (!cl && plans[i]->log2L <= kMaxSmemLog2) ? shape_of(plans[i]) : 8;
+    const auto key = std::make_tuple(plans[i]->log2L, cplx, plans[i]->bc, cl, ppt);
     groups[key].push_back(d);
-    tabs[key] = plans[i]->tabs;
+    if (!tabs.count(key)) {
+      TransformTables tb;
+      PE_CUDA(p0, tables_for(plans[i], ppt, &tb));
+      tabs[key] = tb;
+    }
   }
-  for (auto& kv : groups) {
-    SolveDesc* dd = nullptr;
+  if (groups.size() == 1) {  // one group: on the plan's stream, in its own descriptor array
+    auto& kv = *groups.begin();
     const size_t bytes = sizeof(SolveDesc) * kv.second.size();
-    PE_CUDA(p0, cudaMallocAsync(reinterpret_cast<void**>(&dd), bytes, p0->stream));
-    PE_CUDA(p0, cudaMemcpyAsync(dd, kv.second.data(), bytes, cudaMemcpyHostToDevice, p0->stream));
+    if (bytes > p0->desc_cap) {
+      PE_CUDA(p0, cudaStreamSynchronize(p0->stream));
+      cudaFree(p0->dDesc);
+      p0->dDesc = nullptr;
+      p0->desc_cap = 0;
+      PE_CUDA(p0, cudaMalloc(reinterpret_cast<void**>(&p0->dDesc), bytes));
+      p0->desc_cap = bytes;
+    }
+    PE_CUDA(p0, cudaMemcpyAsync(p0->dDesc, kv.second.data(), bytes, cudaMemcpyHostToDevice, p0->stream));
     if (std::get<3>(kv.first))
-      PE_CUDA(p0, sssp_cluster::launch_march(std::get<0>(kv.first), dd, int(kv.second.size()), p0->stream,
+      PE_CUDA(p0, sssp_cluster::launch_march(std::get<0>(kv.first), p0->dDesc, int(kv.second.size()), p0->stream,
                                              std::get<1>(kv.first), p0->device));
     else
-      PE_CUDA(p0, launch_march(std::get<0>(kv.first), dd, int(kv.second.size()), tabs[kv.first], p0->stream,
-                               std::get<1>(kv.first), std::get<2>(kv.first)));
-    PE_CUDA(p0, cudaFreeAsync(dd, p0->stream));
+      PE_CUDA(p0, launch_march(std::get<0>(kv.first), p0->dDesc, int(kv.second.size()), tabs[kv.first], p0->stream,
+                               std::get<1>(kv.first), std::get<2>(kv.first), std::get<4>(kv.first)));
+    return PE_OK;
+  }
+  // several groups (grid sizes / kernels): each on its own stream, forked from the plan's stream
+  // and joined back to it, so that their launches overlap on the device
+  std::lock_guard<std::mutex> lk(g_lanes_mu);
+  BatchLanes* bl = nullptr;
+  PE_CUDA(p0, lanes_for(p0->device, int(groups.size()), &bl));
+  PE_CUDA(p0, cudaEventRecord(bl->fork, p0->stream));
+  int g = 0;
+  for (auto& kv : groups) {
+    cudaStream_t st = bl->streams[g];
+    const size_t bytes = sizeof(SolveDesc) * kv.second.size();
+    PE_CUDA(p0, cudaStreamWaitEvent(st, bl->fork, 0));
+    if (bytes > bl->cap[g]) {
+      PE_CUDA(p0, cudaStreamSynchronize(st));
+      cudaFree(bl->descs[g]);
+      bl->descs[g] = nullptr;
+      bl->cap[g] = 0;
+      PE_CUDA(p0, cudaMalloc(reinterpret_cast<void**>(&bl->descs[g]), std::max<size_t>(bytes, 64 * sizeof(SolveDesc))));
+      bl->cap[g] = std::max<size_t>(bytes, 64 * sizeof(SolveDesc));
+    }
+    SolveDesc* dd = bl->descs[g];
+    PE_CUDA(p0, cudaMemcpyAsync(dd, kv.second.data(), bytes, cudaMemcpyHostToDevice, st));
+    if (std::get<3>(kv.first))
+      PE_CUDA(p0, sssp_cluster::launch_march(std::get<0>(kv.first), dd, int(kv.second.size()), st,
+                                             std::get<1>(kv.first), p0->device));
+    else
+      PE_CUDA(p0, launch_march(std::get<0>(kv.first), dd, int(kv.second.size()), tabs[kv.first], st,
+                               std::get<1>(kv.first), std::get<2>(kv.first), std::get<4>(kv.first)));
+    PE_CUDA(p0, cudaEventRecord(bl->done[g], st));
+    PE_CUDA(p0, cudaStreamWaitEvent(p0->stream, bl->done[g], 0));
+    ++g;
   }
   return PE_OK;
 }
@@ -1010,10 +1122,154 @@ pe_status pe_plan_autotune(pe_plan* p, int steps, float* ms, int* chosen) {
   return PE_OK;
 }
 
+pe_status pe_plan_set_shape(pe_plan* p, int points_per_thread) {
+  if (!p) return PE_ERR_ARG;
+  const int v = points_per_thread == 0 ? 8 : points_per_thread;
+  if (v != 4 && v != 8 && v != 16) return fail(p, PE_ERR_ARG, "points_per_thread must be 0, 4, 8 or 16");
+  if (v != 8 && (p->bc != PE_BC_DIRICHLET || !sssp_shapes::supported(p->log2L, v)))
+    return fail(p, PE_ERR_ARG, "4 and 16 points per thread take Dirichlet grids with N + 1 in [256, 4096]");
+  p->ppt = v;
+  return PE_OK;
+}
+
+pe_status pe_plan_get_shape(const pe_plan* p, int* points_per_thread) {
+  if (!p || !points_per_thread) return PE_ERR_ARG;
+  *points_per_thread = (p->log2L <= kMaxSmemLog2 && !use_cluster(p, p->complex_profile)) ? shape_of(p) : 0;
+  return PE_OK;
+}
+
 pe_status pe_plan_get_kernel(const pe_plan* p, int* kernel) {
   if (!p || !kernel) return PE_ERR_ARG;
   *kernel = use_cluster(p, p->complex_profile) ? PE_KERNEL_CLUSTER : PE_KERNEL_CTA;
   return PE_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The (kernel, points per thread) shapes the autotuners search, in the order of their timing
+// outputs: one CTA at 4, 8 and 16 points per thread, then the thread-block cluster.
+constexpr int kShapes = 4;
+const int kShapeKernel[kShapes] = {PE_KERNEL_CTA, PE_KERNEL_CTA, PE_KERNEL_CTA, PE_KERNEL_CLUSTER};
+const int kShapePpt[kShapes] = {4, 8, 16, 8};
+
+bool shape_ok(const pe_plan* p, int c) {
+  if (kShapeKernel[c] == PE_KERNEL_CLUSTER) {
+    int clusters = 0;
+    return p->user_bc == PE_BC_DIRICHLET && sssp_cluster::supported(p->log2L) &&
+           sssp_cluster::max_active_clusters(p->log2L, p->complex_profile, &clusters) == cudaSuccess && clusters > 0;
+  }
+  if (kShapePpt[c] == 8) return true;
+  return p->bc == PE_BC_DIRICHLET && sssp_shapes::supported(p->log2L, kShapePpt[c]);
+}
+
+struct SavedMarch {
+  std::vector<float> state;
+  double r_set = 0.0;
+  long long steps = 0, tl_rows = 0;
+  std::vector<double> tl_ranges;
+  int kernel = 0, ppt = 8;
+};
+
+pe_status save_march(pe_plan* p, SavedMarch* sv) {
+  sv->state.resize(pe_state_size(p));
+  pe_status st = pe_save_state(p, sv->state.data(), &sv->r_set, &sv->steps);
+  sv->tl_rows = p->tl_rows;
+  sv->tl_ranges = p->tl_ranges;
+  sv->kernel = p->kernel;
+  sv->ppt = p->ppt;
+  return st;
+}
+
+pe_status restore_march(pe_plan* p, const SavedMarch& sv) {
+  pe_status st = pe_load_state(p, sv.state.data(), sv.r_set, sv.steps);
+  p->tl_rows = sv.tl_rows;
+  p->tl_ranges = sv.tl_ranges;
+  return st;
+}
+
+// Time `steps` range steps of the batch (a warm-up run, then a timed run) with every shape the
+// plans can take, restoring their state after each run; set the fastest.
+pe_status autotune_batch(pe_plan** plans, int count, int steps, float* ms, int* kernel, int* ppt) {
+  pe_plan* p0 = plans[0];
+  std::vector<SavedMarch> sv(static_cast<size_t>(count));
+  for (int i = 0; i < count; ++i) {
+    if (!plans[i]->field_set) return fail(p0, PE_ERR_STATE, "autotune before pe_set_field");
+    if (plans[i]->terms > 1 && plans[i]->nodes == 0)
+      return fail(p0, PE_ERR_STATE, "autotune with Neumann terms but no profile");
+    pe_status st = save_march(plans[i], &sv[size_t(i)]);
+    if (st != PE_OK) return st;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  PE_CUDA(p0, cudaEventCreate(&e0));
+  PE_CUDA(p0, cudaEventCreate(&e1));
+  std::vector<int> st_steps(static_cast<size_t>(count), steps);
+  float best = -1.f;
+  int best_c = -1;
+  pe_status st = PE_OK;
+  for (int c = 0; c < kShapes && st == PE_OK; ++c) {
+    bool any = false;
+    for (int i = 0; i < count; ++i) any = any || shape_ok(plans[i], c);
+    if (ms) ms[c] = -1.f;
+    if (!any) continue;
+    for (int i = 0; i < count; ++i)
+      if (shape_ok(plans[i], c)) {
+        plans[i]->kernel = kShapeKernel[c];
+        plans[i]->ppt = kShapePpt[c];
+      }
+    float t = 0.f;
+    for (int rep = 0; rep < 2 && st == PE_OK; ++rep) {  // the first run warms tables and caches
+      PE_CUDA(p0, cudaEventRecord(e0, p0->stream));
+      st = pe_march_batch_steps(plans, st_steps.data(), count);
+      PE_CUDA(p0, cudaEventRecord(e1, p0->stream));
+      for (int i = 0; i < count && st == PE_OK; ++i) st = check_status(plans[i]);
+      if (st == PE_OK) PE_CUDA(p0, cudaEventElapsedTime(&t, e0, e1));
+      for (int i = 0; i < count; ++i) {
+        pe_status rs = restore_march(plans[i], sv[size_t(i)]);
+        if (st == PE_OK) st = rs;
+      }
+    }
+    if (st != PE_OK) break;
+    if (ms) ms[c] = t;
+    if (best_c < 0 || t < best) {
+      best = t;
+      best_c = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int i = 0; i < count; ++i) {  // the previous setting, then the winner where it applies
+    plans[i]->kernel = sv[size_t(i)].kernel;
+    plans[i]->ppt = sv[size_t(i)].ppt;
+    if (st == PE_OK && best_c >= 0 && shape_ok(plans[i], best_c)) {
+      plans[i]->kernel = kShapeKernel[best_c];
+      plans[i]->ppt = kShapePpt[best_c];
+    }
+  }
+  if (st != PE_OK) return st;
+  if (kernel) *kernel = kShapeKernel[best_c];
+  if (ppt) *ppt = kShapePpt[best_c];
+  return PE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pe_status pe_plan_autotune_shapes(pe_plan* p, int steps, float* ms, int* kernel, int* points_per_thread) {
+  if (!p || steps < 1) return PE_ERR_ARG;
+  NvtxRange nvtx_("pe_plan_autotune_shapes");
+  return autotune_batch(&p, 1, steps, ms, kernel, points_per_thread);
+}
+
+pe_status pe_march_batch_autotune(pe_plan** plans, int count, int steps, float* ms, int* kernel,
+                                  int* points_per_thread) {
+  if (!plans || count < 1 || steps < 1) return PE_ERR_ARG;
+  for (int i = 0; i < count; ++i)
+    if (!plans[i] || plans[i]->device != plans[0]->device) return PE_ERR_ARG;
+  NvtxRange nvtx_("pe_march_batch_autotune");
+  return autotune_batch(plans, count, steps, ms, kernel, points_per_thread);
 }
 
 size_t pe_state_size(const pe_plan* p) { return p ? 4 * size_t(p->L) : 0; }

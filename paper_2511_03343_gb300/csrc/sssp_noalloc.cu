@@ -14,6 +14,9 @@
 //    these arrays until the process exits).
 //  * The first call on a device sets that device up (looks up the arrays' device addresses
 //    and uploads the tables, synchronously).  Make that first call before any stream capture.
+//    The set-up is tied to the device's current CUDA context: after cudaDeviceReset (which
+//    reloads the arrays as zeros, possibly elsewhere) the next call sees a new context and
+//    sets the device up again, so that call too must come before any capture.
 //  * All calls share the one scratch array, which keeps the last call's contents.  Calls
 //    whose work overlaps on the GPU (different streams, or several host threads) race on it;
 //    order them on one stream or synchronise between them.
@@ -41,6 +44,7 @@ static __device__ __align__(256) float g_noalloc_sin[2 * kNoAllocMaxL];
 
 struct NoAllocDevice {
   bool ready = false;
+  void* ctx = nullptr;        // the context the addresses and tables belong to
   float2* scratch = nullptr;  // device address of g_noalloc_scratch (host-side name is a stand-in)
   float2* tw = nullptr;
   float* sinw = nullptr;
@@ -48,6 +52,23 @@ struct NoAllocDevice {
 
 std::mutex g_noalloc_mu;
 NoAllocDevice g_noalloc_dev[kMaxDevices];
+
+// The calling thread's current context (driver API, looked up once through the runtime so
+// the library needs no link against the driver library).
+using CtxGetCurrentFn = int (*)(void**);
+void* current_context() {
+  static CtxGetCurrentFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<CtxGetCurrentFn>(p);
+  }();
+  void* ctx = nullptr;
+  if (!fn || fn(&ctx) != 0) return nullptr;
+  return ctx;
+}
 
 template <int LOG2L>
 __global__ void __launch_bounds__(sssp::Cfg<LOG2L>::NT)
@@ -142,18 +163,23 @@ cudaError_t noalloc_setup(int dev, NoAllocDevice* out) {
 
 extern "C" pe_status pe_dst1_noalloc(const float* in, float* out, int N, void* cuda_stream) {
   if (!in || !out) return PE_ERR_ARG;
+  // range first, so that the power-of-two search below cannot overflow
+  if (N < (1 << kNoAllocMinLog2) - 1 || N > kNoAllocMaxL - 1) return PE_ERR_ARG;
   int log2L = 0;
   while ((1 << log2L) < N + 1) ++log2L;
-  if (N < 1 || (1 << log2L) != N + 1 || log2L < kNoAllocMinLog2 || log2L > kNoAllocMaxLog2) return PE_ERR_ARG;
+  if ((1 << log2L) != N + 1) return PE_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PE_ERR_CUDA;
   NoAllocDevice d;
   {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_dev[dev].ready) {
-      if (noalloc_setup(dev, &g_noalloc_dev[dev]) != cudaSuccess) return PE_ERR_CUDA;
+    NoAllocDevice& cur = g_noalloc_dev[dev];
+    if (!cur.ready || cur.ctx == nullptr || cur.ctx != current_context()) {
+      cur.ready = false;
+      if (noalloc_setup(dev, &cur) != cudaSuccess) return PE_ERR_CUDA;
+      cur.ctx = current_context();  // the set-up's runtime calls made the context current
     }
-    d = g_noalloc_dev[dev];
+    d = cur;
   }
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const size_t bytes = sizeof(float2) * size_t(N);

@@ -11,7 +11,21 @@
 //      and frees the plan, so the next queued requests can be admitted.
 // A request that arrives while others are on the GPU joins them at the next step; all live
 // solves share every launch.  Marching in chunks gives the same bits as one long march.
+//
+// Admission may also adapt a request so that its Neumann series (Eq. Neumann) converges:
+//   PE_ADMIT_MINIMAX_C0  picks the reference sound speed c0 that minimises max|V| over the
+//                        request's profile nodes (V = n^2 - 1): with n^2 = (c0/c)^2 the
+//                        rescaling n^2 -> s n^2, k0 -> k0/sqrt(s), s = 2/(min n^2 + max n^2),
+//                        keeps k0^2 n^2 = (omega/c)^2 and centres V on zero;
+//   PE_ADMIT_CONVERGENT_ORDER lowers the Pade order until the series converges for every
+//                        term j: the FP64 bound rho_j = max|V| max_m |b_j/(1 + b_j lambda_m)|
+//                        is below 1, or, where it is not, an FP64 power iteration on
+//                        -b_j L_j^{-1} V (DST-I by a host FFT) estimates the spectral radius
+//                        below 0.98.  A request that diverges at every order fails at admission.
+// The values used are reported by pe_server_request_params.
 #include <algorithm>
+#include <cmath>
+#include <complex>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -23,9 +37,88 @@
 
 namespace {
 
+using cd = std::complex<double>;
+
+// in-place radix-2 FFT, X_k = sum_n x_n e^{-2 pi i n k/n}, n a power of two (host FP64)
+void fft_pow2(std::vector<cd>& a) {
+  const size_t n = a.size();
+  thread_local std::vector<cd> tw;  // e^{-2 pi i k/n}, k < n/2, for the last size used
+  if (tw.size() != n / 2) {
+    tw.resize(n / 2);
+    for (size_t k = 0; k < n / 2; ++k) tw[k] = std::polar(1.0, -2.0 * M_PI * double(k) / double(n));
+  }
+  for (size_t i = 1, j = 0; i < n; ++i) {
+    size_t bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  for (size_t len = 2; len <= n; len <<= 1) {
+    const size_t step = n / len;
+    for (size_t i = 0; i < n; i += len)
+      for (size_t k = 0; k < len / 2; ++k) {
+        const cd w = tw[k * step];
+        const cd u = a[i + k], v = a[i + k + len / 2] * w;
+        a[i + k] = u + v;
+        a[i + k + len / 2] = u - v;
+      }
+  }
+}
+
+// unnormalised DST-I of x_1..x_N (Section 3.1): S_k = sum_n x_n sin(pi n k/L), L = N + 1, from
+// the DFT Z of the odd extension of length 2L (z_n = x_n, z_{2L-n} = -x_n): S_k = (i/2) Z_k
+void dst1_host(const std::vector<cd>& x, std::vector<cd>& out) {
+  const size_t N = x.size(), L = N + 1;
+  std::vector<cd> z(2 * L, cd(0.0, 0.0));
+  for (size_t n = 1; n <= N; ++n) {
+    z[n] = x[n - 1];
+    z[2 * L - n] = -x[n - 1];
+  }
+  fft_pow2(z);
+  out.resize(N);
+  for (size_t k = 1; k <= N; ++k) out[k - 1] = cd(0.0, 0.5) * z[k];
+}
+
+// Spectral radius estimate of M = -b L^{-1} V, L^{-1} = IDST diag(1/(1 + b lambda_m)) DST, by
+// power iteration: the geometric mean growth of ||M^k x|| over iterations 16..48 (the radius
+// near 1, where admission decides, is a well separated eigenvalue in the workloads; nearly
+// equal moduli far below 1 converge more slowly but do not change the decision).
+double neumann_radius(const std::vector<double>& V, cd b, double k0, double H) {
+  const size_t N = V.size();
+  const double L = double(N + 1);
+  std::vector<cd> x(N), y;
+  unsigned long long st = 88172645463325252ull;  // fixed xorshift start vector
+  for (size_t n = 0; n < N; ++n) {
+    st ^= st << 13;
+    st ^= st >> 7;
+    st ^= st << 17;
+    x[n] = cd(double(st % 1000003) / 1000003.0 - 0.5, double((st >> 20) % 1000003) / 1000003.0 - 0.5);
+  }
+  double lg = 0.0, lg16 = 0.0;
+  for (int it = 1; it <= 48; ++it) {
+    double nx = 0.0;
+    for (auto& v : x) nx += std::norm(v);
+    nx = std::sqrt(nx);
+    if (!(nx > 0.0) || !std::isfinite(nx)) return 0.0;
+    for (size_t n = 0; n < N; ++n) x[n] *= V[n] / nx;
+    dst1_host(x, y);
+    for (size_t m = 1; m <= N; ++m) {
+      const double lam = -std::pow(M_PI * double(m) / (k0 * H), 2.0);
+      y[m - 1] *= (2.0 / L) / (1.0 + b * lam);
+    }
+    dst1_host(y, x);
+    for (auto& v : x) v *= -b;
+    double nn = 0.0;
+    for (auto& v : x) nn += std::norm(v);
+    lg += 0.5 * std::log(std::max(nn, 1e-300));
+    if (it == 16) lg16 = lg;
+  }
+  return std::exp((lg - lg16) / 32.0);
+}
+
 struct Request {
   unsigned long long id = 0;
-  pe_request r{};
+  pe_request r{};          // as admitted (k0, n2 and pade_order may be adapted)
   std::vector<float> u0;
   std::vector<double> n2;
   std::vector<double> node_r;
@@ -45,6 +138,8 @@ struct Result {
   std::vector<float> tl;
   long long rows = 0;
   std::string err;
+  double k0 = 0.0, n2_scale = 1.0;  // the values admission marched with
+  int pade_order = 0;
 };
 
 }  // namespace
@@ -68,6 +163,66 @@ pe_status sfail(pe_server* s, pe_status st, const std::string& m) {
 }
 
 long long tl_rows_for(const pe_request& r) { return r.tl_every > 0 ? r.steps / r.tl_every : 0; }
+
+// Adapt a request at admission (see the file comment); false + message if it cannot converge.
+bool admit_adapt(Request* q, Result* res, std::string* err) {
+  pe_request& r = q->r;
+  res->k0 = r.k0;
+  res->pade_order = r.pade_order;
+  res->n2_scale = 1.0;
+  if (r.neumann_terms <= 1 || r.nodes < 1) return true;
+  const size_t N = size_t(r.N);
+  if (r.flags & PE_ADMIT_MINIMAX_C0) {
+    double lo = 1e300, hi = -1e300;
+    for (double v : q->n2) {
+      lo = std::min(lo, v);
+      hi = std::max(hi, v);
+    }
+    if (lo > 0.0 && std::isfinite(hi)) {
+      const double sc = 2.0 / (lo + hi);
+      for (double& v : q->n2) v *= sc;
+      r.k0 /= std::sqrt(sc);
+      res->n2_scale = sc;
+      res->k0 = r.k0;
+    }
+  }
+  if (!(r.flags & PE_ADMIT_CONVERGENT_ORDER)) return true;
+  // the node with the largest max|V| decides
+  int worst = 0;
+  double vmax = -1.0;
+  for (int k = 0; k < r.nodes; ++k) {
+    double m = 0.0;
+    for (size_t n = 0; n < N; ++n) m = std::max(m, std::fabs(q->n2[size_t(k) * N + n] - 1.0));
+    if (m > vmax) {
+      vmax = m;
+      worst = k;
+    }
+  }
+  std::vector<double> V(N);
+  for (size_t n = 0; n < N; ++n) V[n] = q->n2[size_t(worst) * N + n] - 1.0;
+  for (int p = r.pade_order; p >= 1; --p) {
+    double b[16], a[16], d[18];
+    if (pe_pade_coefficients(r.k0 * r.dr, p, b, a, d) != PE_OK) continue;
+    bool ok = true;
+    for (int j = 0; j < p && ok; ++j) {
+      const cd bj(b[2 * j], b[2 * j + 1]);
+      double mx = 0.0;
+      for (size_t m = 1; m <= N; ++m) {
+        const double lam = -std::pow(M_PI * double(m) / (r.k0 * r.H), 2.0);
+        mx = std::max(mx, std::abs(bj / (1.0 + bj * lam)));
+      }
+      if (vmax * mx < 1.0) continue;
+      if (neumann_radius(V, bj, r.k0, r.H) >= 0.98) ok = false;
+    }
+    if (ok) {
+      r.pade_order = p;
+      res->pade_order = p;
+      return true;
+    }
+  }
+  *err = "the Neumann series diverges at every Pade order for this profile";
+  return false;
+}
 
 // create the plan of a request: tables, output, profile, starter (all host -> device copies)
 pe_status start_plan(pe_server* s, Request* q, pe_plan** out) {
@@ -143,8 +298,14 @@ pe_status pe_server_step(pe_server* s, int* live_out, int* queued_out, int* comp
     std::unique_ptr<Request> q = std::move(s->queue.front());
     s->queue.pop_front();
     pe_plan* p = nullptr;
-    pe_status st = start_plan(s, q.get(), &p);
     Result& res = s->results[q->id];
+    std::string aerr;
+    if (!admit_adapt(q.get(), &res, &aerr)) {
+      res.state = 3;
+      res.err = aerr;
+      continue;
+    }
+    pe_status st = start_plan(s, q.get(), &p);
     if (st != PE_OK) {
       res.state = 3;
       res.err = s->err;
@@ -214,7 +375,11 @@ pe_status pe_server_take(pe_server* s, unsigned long long id, float* field, floa
   auto it = s->results.find(id);
   if (it == s->results.end()) return sfail(s, PE_ERR_ARG, "unknown request id");
   Result& r = it->second;
-  if (r.state == 3) return sfail(s, PE_ERR_CUDA, "request failed: " + r.err);
+  if (r.state == 3) {  // reported once; the entry goes so failed requests do not pile up
+    const std::string m = "request failed: " + r.err;
+    s->results.erase(it);
+    return sfail(s, PE_ERR_CUDA, m);
+  }
   if (r.state != 2) return sfail(s, PE_ERR_STATE, "request not finished");
   if (rows) *rows = size_t(r.rows);
   if (field) std::memcpy(field, r.field.data(), sizeof(float) * r.field.size());
@@ -246,6 +411,25 @@ pe_status pe_server_cancel(pe_server* s, unsigned long long id) {
     }
   it->second.state = 3;
   it->second.err = "cancelled";
+  return PE_OK;
+}
+
+pe_status pe_neumann_radius_estimate(const double* V, int N, double H, double k0, double b_re, double b_im,
+                                     double* rho) {
+  if (!V || !rho || N < 1 || ((N + 1) & N) != 0 || !(H > 0) || !(k0 > 0)) return PE_ERR_ARG;
+  *rho = neumann_radius(std::vector<double>(V, V + N), cd(b_re, b_im), k0, H);
+  return PE_OK;
+}
+
+pe_status pe_server_request_params(pe_server* s, unsigned long long id, double* k0, double* n2_scale,
+                                   int* pade_order) {
+  if (!s) return PE_ERR_ARG;
+  auto it = s->results.find(id);
+  if (it == s->results.end()) return sfail(s, PE_ERR_ARG, "unknown request id");
+  if (it->second.state == 0) return sfail(s, PE_ERR_STATE, "request not admitted yet");
+  if (k0) *k0 = it->second.k0;
+  if (n2_scale) *n2_scale = it->second.n2_scale;
+  if (pade_order) *pade_order = it->second.pade_order;
   return PE_OK;
 }
 

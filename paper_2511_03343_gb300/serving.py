@@ -58,8 +58,15 @@ def _depth_summary(depth, points: int = 24) -> Dict:
 
 
 def replay(trace: List[Dict], hbm_budget: float, chunk_steps: int = 50, tl_every: int = 10,
-           range_scale: float = 1.0, max_live: int = 1024, stream=None, keep_results: bool = False):
-    """Replay ``trace`` against a fresh server; returns latency / throughput figures."""
+           range_scale: float = 1.0, max_live: int = 1024, stream=None, keep_results: bool = False,
+           admit: int = sssp.ADMIT_MINIMAX_C0 | sssp.ADMIT_CONVERGENT_ORDER, keep_ids=None):
+    """Replay ``trace`` against a fresh server; returns latency / throughput figures.  ``admit``
+    are the server's admission adaptations (default: minimax reference sound speed and a Pade
+    order at which the Neumann series converges); ``keep_results`` also returns, per request,
+    (field, TL rows, solve, (k0, n2 scale, Pade order) it was marched with); ``keep_ids`` keeps
+    those only for the given trace ids."""
+    keep = None if keep_ids is None else set(keep_ids)
+    keep_results = keep_results or keep is not None
     srv = sssp.Server(int(hbm_budget), max_live=max_live, chunk_steps=chunk_steps, stream=stream)
     order = sorted(range(len(trace)), key=lambda i: trace[i]["t_arrival"])
     pending = list(order)
@@ -68,6 +75,7 @@ def replay(trace: List[Dict], hbm_budget: float, chunk_steps: int = 50, tl_every
     units = 0
     results = {}
     failed = {}
+    adapted = {}
     t0 = time.perf_counter()
     nsteps = 0
     depth = []  # (seconds since start, live solves, queued requests) after every server step
@@ -76,7 +84,7 @@ def replay(trace: List[Dict], hbm_budget: float, chunk_steps: int = 50, tl_every
         while pending and trace[pending[0]]["t_arrival"] <= now:
             i = pending.pop(0)
             s = build_solve(trace[i], range_scale)
-            rid = srv.submit(s, tl_every=tl_every)
+            rid = srv.submit(s, tl_every=tl_every, admit=admit)
             running[rid] = (i, t0 + trace[i]["t_arrival"], s.N * s.steps, s)
         if not running:
             time.sleep(max(0.0, trace[pending[0]]["t_arrival"] - (time.perf_counter() - t0)))
@@ -89,6 +97,7 @@ def replay(trace: List[Dict], hbm_budget: float, chunk_steps: int = 50, tl_every
             state = srv.state(rid)
             if state == 3:  # the march failed on the device (e.g. a diverging Neumann series)
                 i, ta, u, s = running.pop(rid)
+                failed[i] = "failed"
                 try:
                     srv.take(rid)
                 except sssp.PEError as e:
@@ -98,17 +107,23 @@ def replay(trace: List[Dict], hbm_budget: float, chunk_steps: int = 50, tl_every
                 i, ta, u, s = running.pop(rid)
                 lat[i] = tnow - ta
                 units += u
+                prm = srv.params(rid)
+                if prm[2] != s.pade_order or prm[1] != 1.0:
+                    adapted[i] = prm
                 f, tl = srv.take(rid)
-                if keep_results:
-                    results[i] = (f, tl, s)
+                if keep_results and (keep is None or trace[i]["id"] in keep):
+                    results[i] = (f, tl, s, prm)
     wall = time.perf_counter() - t0
     st = srv.stats()
     srv.close()
     L = np.array([lat[i] for i in sorted(lat)])
+    pct = (lambda q: float(np.percentile(L, q))) if L.size else (lambda q: None)
     out = {"requests": len(trace), "completed": len(lat), "failed": len(failed),
-           "failed_ids": sorted(failed), "wall_s": wall, "server_steps": nsteps,
-           "throughput": units / wall, "p50_s": float(np.percentile(L, 50)), "p99_s": float(np.percentile(L, 99)),
-           "mean_s": float(L.mean()), "peak_live": st["peak_live"], "peak_bytes": st["peak_bytes"],
+           "failed_ids": sorted(failed), "failures": {str(k): v for k, v in sorted(failed.items())},
+           "order_lowered": sum(1 for i, p in adapted.items() if p[2] != trace[i]["pade_order"]),
+           "wall_s": wall, "server_steps": nsteps,
+           "throughput": units / wall, "p50_s": pct(50), "p99_s": pct(99),
+           "mean_s": float(L.mean()) if L.size else None, "peak_live": st["peak_live"], "peak_bytes": st["peak_bytes"],
            "queue_depth": _depth_summary(depth)}
     if keep_results:
         out["results"] = results

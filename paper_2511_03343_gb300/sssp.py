@@ -67,6 +67,10 @@ _SIGNATURES = {
     "pe_plan_set_kernel": (_i, [_vp, _i]),
     "pe_plan_get_kernel": (_i, [_vp, ctypes.POINTER(_i)]),
     "pe_plan_autotune": (_i, [_vp, _i, _vp, ctypes.POINTER(_i)]),
+    "pe_plan_set_shape": (_i, [_vp, _i]),
+    "pe_plan_get_shape": (_i, [_vp, ctypes.POINTER(_i)]),
+    "pe_plan_autotune_shapes": (_i, [_vp, _i, _vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "pe_march_batch_autotune": (_i, [ctypes.POINTER(_vp), _i, _i, _vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "pe_state_size": (_sz, [_vp]),
     "pe_save_state": (_i, [_vp, _vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
     "pe_load_state": (_i, [_vp, _vp, _d, ctypes.c_longlong]),
@@ -87,6 +91,9 @@ _SIGNATURES = {
     "pe_server_state": (_i, [_vp, ctypes.c_ulonglong, ctypes.POINTER(_i)]),
     "pe_server_take": (_i, [_vp, ctypes.c_ulonglong, _vp, _vp, _sz, ctypes.POINTER(_sz)]),
     "pe_server_stats": (_i, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz), ctypes.POINTER(_i)]),
+    "pe_server_request_params": (_i, [_vp, ctypes.c_ulonglong, ctypes.POINTER(_d), ctypes.POINTER(_d),
+                                      ctypes.POINTER(_i)]),
+    "pe_neumann_radius_estimate": (_i, [_vp, _i, _d, _d, _d, _d, ctypes.POINTER(_d)]),
 }
 
 
@@ -94,7 +101,21 @@ class PERequest(ctypes.Structure):
     """Mirror of ``pe_request`` (include/sssp.h)."""
     _fields_ = [("N", _i), ("H", _d), ("k0", _d), ("dr", _d), ("pade_order", _i), ("neumann_terms", _i),
                 ("neumann_tol", _d), ("steps", ctypes.c_longlong), ("tl_every", _i), ("u0", _vp), ("n2", _vp),
-                ("node_r", _vp), ("nodes", _i), ("r0", _d)]
+                ("node_r", _vp), ("nodes", _i), ("r0", _d), ("flags", _i)]
+
+
+ADMIT_MINIMAX_C0 = 1
+ADMIT_CONVERGENT_ORDER = 2
+
+
+def neumann_radius_estimate(V, H: float, k0: float, b: complex) -> float:
+    """Host FP64 power-iteration estimate of the spectral radius of -b L^{-1} V (the serving
+    admission's convergence check; pe_neumann_radius_estimate)."""
+    v = np.ascontiguousarray(np.asarray(V, dtype=np.float64))
+    rho = _d(0)
+    _check(lib().pe_neumann_radius_estimate(v.ctypes.data, int(v.size), float(H), float(k0), float(b.real),
+                                            float(b.imag), ctypes.byref(rho)))
+    return rho.value
 
 
 def library_path() -> str:
@@ -292,6 +313,17 @@ class Plan:
         """'auto', 'cta' (one CTA per solve) or 'cluster' (one solve over a thread-block cluster)."""
         self._c(lib().pe_plan_set_kernel(self._p, KERNELS[kernel]))
 
+    def set_shape(self, points_per_thread: int):
+        """Points per thread of the one-CTA kernel: 4, 8 (default) or 16."""
+        self._c(lib().pe_plan_set_shape(self._p, int(points_per_thread)))
+
+    @property
+    def shape(self) -> int:
+        """Points per thread of the one-CTA kernel a march runs (0: cluster or large-grid kernel)."""
+        v = _i(0)
+        self._c(lib().pe_plan_get_shape(self._p, ctypes.byref(v)))
+        return v.value
+
     @property
     def kernel(self) -> str:
         """The kernel a march of this plan runs: 'cta' or 'cluster'."""
@@ -402,13 +434,13 @@ class Server:
         except Exception:
             pass
 
-    def submit(self, solve, tl_every: int = 0, steps: Optional[int] = None) -> int:
-        """Queue an ``inputs.Solve``; returns the request id."""
+    def submit(self, solve, tl_every: int = 0, steps: Optional[int] = None, admit: int = 0) -> int:
+        """Queue an ``inputs.Solve``; returns the request id.  ``admit``: ADMIT_* bits."""
         u0 = _host_c64(solve.u0)
         req = PERequest(N=solve.N, H=solve.H, k0=solve.k0, dr=solve.dr, pade_order=solve.pade_order,
                         neumann_terms=solve.neumann_terms, neumann_tol=solve.neumann_tol,
                         steps=int(steps if steps is not None else solve.steps), tl_every=int(tl_every),
-                        u0=u0.ctypes.data, r0=solve.r0)
+                        u0=u0.ctypes.data, r0=solve.r0, flags=int(admit))
         if solve.neumann_terms > 1 and len(solve.profiles) > 0:
             n2 = np.ascontiguousarray(np.stack([np.asarray(v, dtype=np.float64) for _, v in solve.profiles]))
             nr = np.ascontiguousarray(np.array([r for r, _ in solve.profiles], dtype=np.float64))
@@ -438,6 +470,13 @@ class Server:
                                      tl.ctypes.data if tl.size else None, tl.size, ctypes.byref(rows)))
         del self._keep[rid]
         return field, tl
+
+    def params(self, rid: int):
+        """(k0, n2 scale, Pade order) the request marches with after admission."""
+        k0, sc, p = _d(0), _d(0), _i(0)
+        self._c(lib().pe_server_request_params(self._s, ctypes.c_ulonglong(rid), ctypes.byref(k0), ctypes.byref(sc),
+                                               ctypes.byref(p)))
+        return k0.value, sc.value, p.value
 
     def cancel(self, rid: int):
         self._c(lib().pe_server_cancel(self._s, ctypes.c_ulonglong(rid)))
@@ -487,6 +526,28 @@ class GemmBatch:
             self.close()
         except Exception:
             pass
+
+
+SHAPE_NAMES = ("cta4", "cta8", "cta16", "cluster")
+
+
+def _shape_result(ms, k, p):
+    return {"chosen": ("cluster" if k.value == KERNELS["cluster"] else f"cta{p.value}"),
+            "ms": {n: (float(ms[i]) if ms[i] >= 0 else None) for i, n in enumerate(SHAPE_NAMES)}}
+
+
+def autotune_batch(plans: List[Plan], steps: int = 8) -> dict:
+    """Time ``steps`` range steps of the batched march of ``plans`` with every shape they can take
+    (one CTA per solve at 4/8/16 points per thread, one cluster per solve), restore their state,
+    and set the fastest (pe_march_batch_autotune)."""
+    arr = (_vp * len(plans))(*[p.handle for p in plans])
+    ms = (ctypes.c_float * 4)()
+    k, p = _i(0), _i(0)
+    st = lib().pe_march_batch_autotune(arr, len(plans), int(steps), ctypes.cast(ms, _vp), ctypes.byref(k),
+                                       ctypes.byref(p))
+    if st != PE_OK:
+        raise PEError(st, lib().pe_last_error(plans[0].handle).decode())
+    return _shape_result(ms, k, p)
 
 
 def march_batch_steps(plans: List[Plan], steps: Sequence[int]):

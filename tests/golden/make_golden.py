@@ -19,7 +19,17 @@
                                                   # -> munk_n65535_s2000.txt (library DST-I
                                                   # backend)
 
-Each file holds the sampled final field and sampled TL rows.
+    python tests/golden/make_golden.py batch      # eight members of the 256-solve Munk batch
+                                                  # (N = 1023, f ~ U[50, 500] Hz from
+                                                  # default_rng(4), 2000 steps of 25 m, [6/6],
+                                                  # 12 terms), product form, explicit sine sums
+                                                  # -> batch_n1023_s2000.txt (one process per
+                                                  # member; a few minutes on 8 cores)
+    python tests/golden/make_golden.py counts     # Neumann terms summed per step and Pade term,
+                                                  # first 100 steps of the N = 4095 Munk march,
+                                                  # product form -> munk_n4095_counts100.txt
+
+Each workload file holds the sampled final field and sampled TL rows.
 """
 import os
 import sys
@@ -153,7 +163,108 @@ def main_large(path=os.path.join(HERE, "munk_n65535_s2000.txt")):
     print("wrote", path, "in", round(el, 1), "s")
 
 
+# members of the 256-solve batch with stored runs: positions in the frequency order (lowest,
+# second lowest, then evenly up to the highest).  The lowest, 53.7 Hz, is the member whose
+# 12-term series does not converge to 1e-10.
+BATCH_RANKS = (0, 1, 42, 85, 128, 170, 213, 255)
+BATCH_FIELD_STRIDE = 4
+BATCH_TL_EVERY = 100
+BATCH_TL_STRIDE = 16
+
+
+def _batch_member(i):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    s = inputs.munk_batch()[i]
+    g = O.Grid(N=s.N, H=s.H, k0=s.k0, dr=s.dr)
+    t0 = time.time()
+    res = O.march(s.u0, s.profiles, g, s.pade_order, s.steps, s.neumann_terms, s.neumann_tol,
+                  tl_every=BATCH_TL_EVERY, form="product")
+    return i, s.freq, res, time.time() - t0
+
+
+def main_batch(path=os.path.join(HERE, "batch_n1023_s2000.txt")):
+    import multiprocessing as mp
+    freqs = np.array([s.freq for s in inputs.munk_batch(steps=1)])
+    members = [int(np.argsort(freqs)[k]) for k in BATCH_RANKS]
+    with mp.get_context("spawn").Pool(len(members)) as pool:
+        runs = pool.map(_batch_member, members)
+    with open(path, "w") as f:
+        f.write("# FP64 oracle (product form, explicit sine sums), written by tests/golden/make_golden.py batch\n")
+        f.write("# munk_batch count=256 seed=4 N=1023 H=5000 dr=25 steps=2000 p=6 terms=12 tol=1e-10 zs=1000 "
+                "c0=1500\n")
+        f.write(f"field_stride {BATCH_FIELD_STRIDE} tl_every {BATCH_TL_EVERY} tl_stride {BATCH_TL_STRIDE} "
+                f"members {len(runs)}\n")
+        for i, freq, res, el in runs:
+            f.write(f"member {i} freq {freq:.17e} norm {np.linalg.norm(res.u):.17e} oracle_seconds {el:.1f}\n")
+            f.write("field\n")
+            for k in range(0, res.u.shape[0], BATCH_FIELD_STRIDE):
+                f.write(f"{k} {res.u[k].real:.17e} {res.u[k].imag:.17e}\n")
+            f.write("tl\n")
+            for r, row in zip(res.tl_ranges, res.tl):
+                f.write(f"{r:.6f} " + " ".join(f"{row[k]:.10e}" for k in range(0, row.shape[0], BATCH_TL_STRIDE)) + "\n")
+    print("wrote", path, "members", members)
+
+
+def load_batch(path=os.path.join(HERE, "batch_n1023_s2000.txt")):
+    """{member index: (freq, field indices, field, TL ranges, TL rows)} of the stored batch runs."""
+    lines = open(path).read().splitlines()
+    out = {}
+    k = 3
+    while k < len(lines):
+        a = lines[k].split()
+        i, freq = int(a[1]), float(a[3])
+        assert lines[k + 1] == "field"
+        k += 2
+        fidx, fld = [], []
+        while lines[k] != "tl":
+            b = lines[k].split()
+            fidx.append(int(b[0]))
+            fld.append(float(b[1]) + 1j * float(b[2]))
+            k += 1
+        k += 1
+        tr, tl = [], []
+        while k < len(lines) and not lines[k].startswith("member"):
+            b = lines[k].split()
+            tr.append(float(b[0]))
+            tl.append([float(v) for v in b[1:]])
+            k += 1
+        out[i] = (freq, np.array(fidx), np.array(fld), np.array(tr), np.array(tl))
+    return out
+
+
+COUNT_STEPS = 100
+
+
+def main_counts(path=os.path.join(HERE, "munk_n4095_counts100.txt")):
+    """Per step and Pade term, the Neumann terms (m = 0 included) that the oracle's product form
+    sums on the first 100 steps of the N = 4095 Munk march (library DST-I backend)."""
+    s = inputs.munk(steps=COUNT_STEPS)
+    g = O.Grid(N=s.N, H=s.H, k0=s.k0, dr=s.dr)
+    O.set_dst_backend("fft")
+    counts = []
+    O.march(s.u0, s.profiles, g, s.pade_order, s.steps, s.neumann_terms, s.neumann_tol, tl_every=0,
+            form="product", term_counts=counts)
+    O.set_dst_backend("matrix")
+    with open(path, "w") as f:
+        f.write("# FP64 oracle (product form, library DST-I backend), written by tests/golden/make_golden.py counts\n")
+        f.write(f"# munk N={s.N} H={s.H} f={s.freq} dr={s.dr} steps={s.steps} p={s.pade_order} "
+                f"terms={s.neumann_terms} tol={s.neumann_tol}: one row per step, terms summed per Pade term\n")
+        for c in counts:
+            f.write(" ".join(str(int(v)) for v in c) + "\n")
+    print("wrote", path)
+
+
+def load_counts(path=os.path.join(HERE, "munk_n4095_counts100.txt")):
+    return np.array([[int(v) for v in ln.split()] for ln in open(path).read().splitlines() if not ln.startswith("#")])
+
+
 if __name__ == "__main__":
+    if len(sys.argv) > 1 and sys.argv[1] == "batch":
+        main_batch()
+        sys.exit(0)
+    if len(sys.argv) > 1 and sys.argv[1] == "counts":
+        main_counts()
+        sys.exit(0)
     if len(sys.argv) > 1 and sys.argv[1] == "large":
         main_large()
     elif len(sys.argv) > 1 and sys.argv[1] == "eddy":

@@ -163,3 +163,32 @@ def test_serving_queue_depth_summary():
     many = serving._depth_summary([(0.01 * i, i % 7, i % 3) for i in range(1, 1001)], points=24)
     assert len(many["trace"]) == 24 and many["trace"][-1][0] == 10.0
     assert serving._depth_summary([])["trace"] == []
+
+
+def test_admission_radius_estimate_matches_dense_eigenvalues(L):
+    """The serving admission's host FP64 power iteration (pe_neumann_radius_estimate) against
+    the spectral radius of the dense Neumann operator -b_j L_j^{-1} V built from the oracle's
+    explicit sine matrix (np.linalg.eigvals), for converging and diverging cases."""
+    import math
+    from oracle import sssp_oracle as O
+    from paper_2511_03343_gb300 import inputs
+    checked = []
+    for N, f, p, c0 in [(255, 31.6, 7, 1500.0), (255, 31.6, 7, 1525.14), (255, 37.7, 7, 1525.14), (127, 60.0, 4, 1500.0)]:
+        z = inputs.depth_grid(N, 5000.0)
+        V = inputs.n2_from_c(inputs.munk_c(z), c0) - 1.0
+        k0 = 2 * math.pi * f / c0
+        g = O.Grid(N=N, H=5000.0, k0=k0, dr=25.0)
+        plan = O.pade_plan(g.sigma, p)
+        S = O.sine_matrix(N)
+        for bj in plan.b:
+            M = -bj * ((2.0 / (N + 1)) * S @ np.diag(1.0 / (1.0 + bj * g.lam)) @ S) @ np.diag(V)
+            exact = np.max(np.abs(np.linalg.eigvals(M)))
+            from paper_2511_03343_gb300 import sssp
+            est = sssp.neumann_radius_estimate(V, 5000.0, k0, complex(bj))
+            # the decision admission takes agrees, and radii near it are accurate
+            assert (est >= 0.98) == (exact >= 0.98), (N, f, p, c0, bj, est, exact)
+            if exact >= 0.5:
+                assert abs(est - exact) <= 0.03 * exact, (N, f, p, c0, bj, est, exact)
+        checked.append(max(np.max(np.abs(np.linalg.eigvals(
+            -bj * ((2.0 / (N + 1)) * S @ np.diag(1.0 / (1.0 + bj * g.lam)) @ S) @ np.diag(V)))) for bj in plan.b))
+    assert max(checked) > 1.0 and min(checked) < 1.0  # both sides of the decision were exercised

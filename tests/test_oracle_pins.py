@@ -343,6 +343,8 @@ def _all_pins_pass():
         try:
             if not ok():
                 failed.append(name)
+        except TypeError:  # a planted mistake with the wrong signature is a bug of the test itself
+            raise
         except Exception:  # a mistake may also make a pin raise
             failed.append(name)
     return failed
@@ -373,20 +375,20 @@ def _mut_sine_index(mp):
 def _mut_neumann_sign(mp):
     orig = O.neumann_w
 
-    def bad(u, V, b, lam, terms, tol, return_counts=False):
-        return orig(u, -V, b, lam, terms, tol, return_counts)
+    def bad(u, V, b, lam, terms, tol, return_counts=False, bc="dirichlet"):
+        return orig(u, -V, b, lam, terms, tol, return_counts, bc=bc)
     mp.setattr(O, "neumann_w", bad)
 
 
 def _mut_neumann_order(mp):
     """Apply V after L^{-1} instead of before (the factors do not commute)."""
-    def bad(u, V, b, lam, terms, tol, return_counts=False):
+    def bad(u, V, b, lam, terms, tol, return_counts=False, bc="dirichlet"):
         b = np.asarray(b, dtype=np.complex128)
         U = np.repeat(u[:, None], len(b), axis=1) if u.ndim == 1 else u
-        t = O.apply_Linv(U, b, lam)
+        t = O.apply_Linv(U, b, lam, bc)
         w = t.copy()
         for m in range(1, max(terms, 1)):
-            t = -b[None, :] * V[:, None] * O.apply_Linv(t, b, lam)
+            t = -b[None, :] * V[:, None] * O.apply_Linv(t, b, lam, bc)
             w = w + t
         return (w, np.full(len(b), terms)) if return_counts else w
     mp.setattr(O, "neumann_w", bad)
@@ -415,8 +417,8 @@ def _mut_taylor_term(mp):
 
 def _mut_carrier_sign(mp):
     orig = O.step_sum
-    def bad(u, V, grid, plan, terms, tol):
-        return orig(u, V, grid, plan, terms, tol) * np.exp(-2j * grid.sigma)
+    def bad(u, V, grid, plan, terms, tol, counts=None):
+        return orig(u, V, grid, plan, terms, tol, counts) * np.exp(-2j * grid.sigma)
     mp.setattr(O, "step_sum", bad)
 
 
@@ -623,3 +625,22 @@ def test_fft_dst_backend_equals_the_sine_sums(N):
     assert np.max(np.abs(got1 - ref[:, 0])) <= 1e-12 * scale * math.log2(N + 1)
     with pytest.raises(ValueError):
         O.set_dst_backend("cuda")
+
+
+@pytest.mark.parametrize("N", [16383, 65535])
+def test_fft_dst_backend_at_the_largest_grids_sampled(N):
+    """At the grid sizes of the stored full-length runs (N = 16383 and 65535), the library
+    DST-I backend equals the explicit O(N) sine sums (dst1_at) at sampled modes: the lowest and
+    highest, the middle, powers of two and random ones."""
+    rng = np.random.default_rng(N + 11)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    ms = sorted(set([1, 2, 3, N // 2, (N + 1) // 2, N - 1, N] + [1 << k for k in range(1, int(math.log2(N)))]
+                    + list(rng.integers(1, N + 1, 24))))
+    ref = O.dst1_at(x, ms)
+    try:
+        O.set_dst_backend("fft")
+        got = O.dst1(x)[np.array(ms) - 1]
+    finally:
+        O.set_dst_backend("matrix")
+    scale = np.sqrt(N) * np.sqrt(np.mean(np.abs(x) ** 2))
+    assert np.max(np.abs(got - ref)) <= 1e-11 * scale * math.log2(N + 1)
