@@ -281,6 +281,8 @@ def bench_batch(args):
     plans = [sssp.plan_for(s, stream=stream, tl_every=BATCH_TL_EVERY) for s in solves]
     for pl in plans:
         pl.set_kernel(args.kernel)
+    # the batch shape (points per thread of the one-CTA kernel) chosen by the library's autotuner
+    tune = None if args.no_autotune else sssp.autotune_batch(plans, steps=8)
     u0s = [torch.from_numpy(s.u0.astype(np.complex64)).cuda() for s in solves]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -364,7 +366,7 @@ def bench_batch(args):
     line = None
     if rank == 0:
         plain = None if (args.no_plain or world > 1) else _vs_plain(args, sssp, inputs, solves, members, fields, tls,
-                                                                     stream, flush)
+                                                                     stream, flush, f"cta{plans[0].shape}")
         served = None if (args.no_served or world > 1) else _served_block(args, sssp, stream)
         cpu = run_cpu_oracle_sample(args.cpu_seconds, "batch") if (world == 1 and not args.no_cpu) else None
         bytes_in = sum(s.N for s in solves) * 8
@@ -372,7 +374,8 @@ def bench_batch(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-                "config": _batch_config({"kernel": plans[0].kernel, "range_steps": steps}),
+                "config": _batch_config({"kernel": plans[0].kernel, "points_per_thread": plans[0].shape,
+                                         "range_steps": steps, "autotune": tune}),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak, "traffic": None,
                              "kernel": f"{plans[0].kernel} march kernel, one launch of 256 solves",
@@ -391,7 +394,7 @@ def bench_batch(args):
         torch.distributed.destroy_process_group()
 
 
-def _vs_plain(args, sssp, inputs, solves, members, fields, tls, stream, flush):
+def _vs_plain(args, sssp, inputs, solves, members, fields, tls, stream, flush, batch_shape):
     """The same solves marched one plan at a time on the plain marcher (pe_march, one solve on
     the GPU at a time, the kernel the library picks for one solve): the stored members (lowest,
     second lowest, then evenly up to the highest frequency), each timed alone with CUDA events;
@@ -403,6 +406,7 @@ def _vs_plain(args, sssp, inputs, solves, members, fields, tls, stream, flush):
     for i in members:
         s = solves[i]
         pl = sssp.plan_for(s, stream=stream, tl_every=BATCH_TL_EVERY)
+        tune = sssp.autotune_batch([pl], steps=8)  # the plain path at its own best shape
         flush.fill_(1.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -412,18 +416,20 @@ def _vs_plain(args, sssp, inputs, solves, members, fields, tls, stream, flush):
         ms = e0.elapsed_time(e1)
         u = pl.read_field()
         tl, _ = pl.read_tl()
-        kernel = pl.kernel
+        kernel = pl.kernel if pl.kernel == "cluster" else f"cta{pl.shape}"
         pl.close()
         tot_ms += ms
         units += s.N * s.steps
-        same = same and np.array_equal(u, fields[i]) and np.array_equal(tl, tls[i])
+        if kernel == batch_shape:
+            same = same and np.array_equal(u, fields[i]) and np.array_equal(tl, tls[i])
         worst_tl = max(worst_tl, _tl_vs(tls[i], tl))
-        out[str(i)] = {"freq_hz": round(s.freq, 3), "ms": ms, "kernel": kernel}
+        out[str(i)] = {"freq_hz": round(s.freq, 3), "ms": ms, "shape": kernel, "autotune_ms": tune["ms"]}
     if not members:
         return None
     return {"value": units / (tot_ms * 1e-3), "unit": UNIT, "solves_timed": len(members),
-            "what": "the stored batch members, each marched alone (pe_march), CUDA events per solve",
-            "batched_results_bitwise_equal": bool(same), "max_tl_diff_db_batched_vs_plain": worst_tl,
+            "what": "the stored batch members, each marched alone (pe_march) at the shape the autotuner picks "
+                    "for one solve, CUDA events per solve",
+            "batched_results_bitwise_equal_where_same_shape": bool(same), "max_tl_diff_db_batched_vs_plain": worst_tl,
             "members": out}
 
 
@@ -628,35 +634,73 @@ def bench_serve(args):
 
 
 def bench_gemm(args):
-    """The 256-solve Munk batch (N = 1023) with the DST-I as a dense tensor-core GEMM, per
-    precision: throughput of the lockstep march (one captured graph per range step)."""
+    """The 256-solve Munk batch (N = 1023, [6/6], 12 terms) with the DST-I as the library's own
+    tensor-core GEMM (tcgen05.mma, TMA-fed, fused epilogues), per precision: throughput of the
+    lockstep march (one captured graph per range step), the tensor work rate, and the sampled final
+    field of the stored members against the FP64 oracle runs.  FP32 (CUDA cores, the reference)
+    runs fewer steps (``--gemm-fp32-steps``) and its parity is not checked."""
     import numpy as np
     import torch
     torch.cuda.set_device(0)
     from paper_2511_03343_gb300 import build as B
     B.build()
+    from oracle import sssp_oracle as O
     from paper_2511_03343_gb300 import inputs, sssp
     stream = torch.cuda.current_stream()
     steps = args.range_steps
     solves = inputs.munk_batch(count=args.batch_count, steps=steps)
+    mg = _load_make_golden()
+    runs = mg.load_batch() if (steps == 2000 and args.batch_count == 256) else {}
+    L = solves[0].N + 1
+    C = 2 * len(solves)
     out = {}
-    for mode in ["fp32", "tf32", "3xtf32", "bf16x3"]:
+    for mode in ["bf16x3", "3xtf32", "tf32", "fp32"]:
+        n_steps = steps if mode != "fp32" else min(steps, args.gemm_fp32_steps)
         plans = [sssp.plan_for(s, stream=stream) for s in solves]
         gb = sssp.GemmBatch(plans, mode)
         gb.march(2)
         torch.cuda.synchronize()
+        gb.close()
+        gb = sssp.GemmBatch(plans, mode)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        gb.march(steps)
+        gb.march(n_steps)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        out[mode] = {"ms": ms, "throughput": sum(s.N for s in solves) * steps / (ms * 1e-3)}
+        gemms = solves[0].pade_order * (2 * solves[0].neumann_terms - 2) * n_steps
+        products = 3 if mode in ("bf16x3", "3xtf32") else 1
+        tflops = 2.0 * L * L * C * products * gemms / (ms * 1e-3) / 1e12
+        rec = {"ms": ms, "range_steps": n_steps, "throughput": sum(s.N for s in solves) * n_steps / (ms * 1e-3),
+               "gemms": gemms, "us_per_gemm": 1e3 * ms / gemms, "tensor_tflops": tflops if mode != "fp32" else None,
+               "fp32_tflops": tflops if mode == "fp32" else None}
+        if runs and n_steps == 2000:
+            worst = (0.0, 0.0)
+            for i, (freq, fidx, fref, tl_r, tl_ref) in runs.items():
+                u = gb.read_field(i).astype(np.complex128)
+                rel = float(np.linalg.norm(u[fidx] - fref) / np.linalg.norm(fref))
+                tl = O.transmission_loss(u, tl_r[-1])[::mg.BATCH_TL_STRIDE]
+                mask = tl_ref[-1] < 100
+                worst = (max(worst[0], rel), max(worst[1], float(np.max(np.abs(tl - tl_ref[-1])[mask]))))
+            rec["parity"] = {"worst_field_rel_l2_sampled": worst[0], "worst_final_tl_err_db": worst[1],
+                             "against": "stored FP64 oracle runs of 8 members (tests/golden/batch_n1023_s2000.txt)"}
+        out[mode] = rec
         gb.close()
         for pl in plans:
             pl.close()
+    peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        peak = 1900.0
+    for mode in ("bf16x3",):
+        if out[mode]["tensor_tflops"]:
+            out[mode]["frac_of_bf16_peak"] = out[mode]["tensor_tflops"] / peak
     print(json.dumps({"metric": METRIC, "unit": UNIT, "config": {"workload": "batch_gemm_dst", "solves": len(solves),
-                      "N": 1023, "range_steps": steps}, "modes": out}), flush=True)
+                      "N": solves[0].N, "range_steps": steps, "gemm": f"{L} x {C} x {L} per transform, "
+                      "128 x 32 tiles, tcgen05.mma kind::f16 / kind::tf32"}, "bf16_peak_tflops": peak,
+                      "modes": out}), flush=True)
 
 
 def bench_dst(args):
@@ -848,6 +892,8 @@ def main():
                     help="range scale of the serving trace replayed inside the default bench line")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--gemm-fp32-steps", type=int, default=100)
     ap.add_argument("--chunk-steps", type=int, default=50)
     ap.add_argument("--serve-baseline", action="store_true")
     ap.add_argument("--batch-count", type=int, default=256)

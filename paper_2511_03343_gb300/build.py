@@ -78,7 +78,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         logs = list(ex.map(_run, jobs))
     tmp = LIB + ".tmp"
     cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
-    logs.append(_run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcublas",
+    logs.append(_run([nvcc, *ARCH, "-shared", "-o", tmp, *objs,
                       "-Xlinker", "-rpath", "-Xlinker", cuda_lib]))
     os.replace(tmp, LIB)
     if verbose:

@@ -1,36 +1,57 @@
 // Batched march with the DST-I as a dense GEMM on the tensor cores (a precision variant).
 //
-// For a batch of B solves of one grid size, every transform of the march is applied to all B
-// fields at once as Y = S X, S[m][n] = sin(pi n m/(N+1)) (N x N, real, symmetric) and X the
-// N x 2B real matrix of the fields' real and imaginary parts.  The GEMM is a plain library
-// contraction (cuBLAS) in one of four precisions:
-//   PE_GEMM_FP32    FP32 on the CUDA cores (reference for the others),
-//   PE_GEMM_TF32    one TF32 tensor-core GEMM,
-//   PE_GEMM_3XTF32  S = S_hi + S_lo, X = X_hi + X_lo (TF32 hi parts): S_hi X_hi + S_hi X_lo + S_lo X_hi,
-//   PE_GEMM_BF16X3  the same split with BF16 parts,
-// all accumulating in FP32.  Everything else of the step (Pade multipliers, V multiply,
-// Neumann accumulation, stage update with hi/lo multipliers) runs in this file's element-wise
-// kernels, with the same tables and arithmetic as the FFT marcher.  The series takes a fixed
-// number of terms (the plans' neumann_terms) for every solve, so all solves stay in lockstep;
-// one range step is captured once in a CUDA graph and replayed.
+// For a batch of B solves of one grid size (L = N + 1 a power of two, L >= 128), every
+// transform of the march is applied to all B fields at once as Y = S X with
+// S[m][n] = sin(pi n m/L) (L x L with the zero row and column m = 0 / n = 0 of the index
+// convention of the FFT marcher, real, symmetric) and X the L x C real matrix of the fields'
+// components, column 2b the real and 2b + 1 the imaginary part of field b (C = 2B rounded up to
+// the tile width, extra columns zero).  The contraction is this file's own kernel:
+//   PE_GEMM_BF16X3  S = S_hi + S_lo, X = X_hi + X_lo with BF16 parts, three tcgen05.mma
+//                   products (hi hi + hi lo + lo hi) into one FP32 accumulator in tensor memory;
+//   PE_GEMM_TF32    one tcgen05.mma kind::tf32 product of the TF32-rounded operands;
+//   PE_GEMM_3XTF32  the hi/lo split with TF32 parts, three kind::tf32 products;
+//   PE_GEMM_FP32    a CUDA-core FP32 GEMM (the reference the others are measured against).
+// A CTA owns a 128 x 32 output tile: one thread issues TMA loads of 128-byte swizzled K slices
+// of S and X into a multi-stage shared-memory ring, another issues the MMAs (K-major operands,
+// the accumulator in 32 tensor-memory columns), and after the last product all four warps read
+// their 32 rows back with tcgen05.ld and run the step's element-wise work in the epilogue,
+// writing the next GEMM's operand (already split) directly:
+//   after a transform to depth space:    X' = V .* Y                 (the Neumann term's V t)
+//   after a transform to spectral space: t_m = B_j .* Y, acc += t_m, X' = t_m.
+// So one Neumann term is two GEMM launches and nothing else; the stage start (t_0 = A_j y) and
+// end (y = R_j y + beta_j acc, hi/lo multiplier) are small element-wise kernels.  The tables and
+// the arithmetic are the FFT marcher's.  The series takes a fixed number of terms (the plans'
+// neumann_terms) for every solve, so the batch stays in lockstep; one range step is captured in
+// a CUDA graph and replayed.
 //
-// The dense transform costs 4 N^2 flop per complex vector against ~5 (N+1) log2(N+1) for the
-// FFT (about 80x more at N = 1023), so this form is measured for its accuracy per precision,
-// not offered as the fast path.
-#include <cublas_v2.h>
+// The dense transform costs 2 L^2 flop per real column against ~5 L log2 L for the FFT, so this
+// form is measured for its accuracy per precision and for the tensor pipe, not offered as the
+// fast path.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "../../include/sssp.h"
 #include "plan_internal.h"
+#include "umma.cuh"
 
 namespace {
 
-struct GemmSolve {  // per-solve table pointers (device)
+constexpr int kBM = 128;        // output rows per tile (modes or depths): the MMA's M, one TMEM lane each
+constexpr int kBN = 32;         // output columns per tile (16 complex fields): the MMA's N, 32 TMEM columns
+constexpr int kRowBytes = 128;  // one swizzled K slice row: 64 BF16 or 32 FP32 values
+constexpr int kThreads = 128;
+constexpr uint64_t kWaitNs = 500000000ull;  // every barrier wait gives up after 0.5 s
+constexpr int kStatusTimeout = 5;
+
+enum Epi { kEpiTimesV = 0, kEpiTerm = 1, kEpiTermLast = 2, kEpiOut = 3 };
+
+struct GemmSolve {  // per-solve tables (device, L-indexed, index 0 the zero pad)
   const float2* A;
   const float2* B;
   const float4* R;
@@ -38,153 +59,358 @@ struct GemmSolve {  // per-solve table pointers (device)
   float2 beta[sssp::kMaxStages];
 };
 
-__device__ __forceinline__ float tf32_hi(float x) {
-  // round to the nearest value with a 10-bit mantissa (TF32), ties away
+struct EpiArgs {
+  const GemmSolve* solves;
+  float2* ACC;   // B x L Neumann sums (spectral)
+  void* Xhi;     // next GEMM operand, C x L (BF16 for BF16X3, FP32 otherwise)
+  void* Xlo;     // its low part (split modes)
+  float* Gout;   // C x L FP32 output (read-out)
+  int* status;   // error word: a barrier wait that ran out
+  int L, B, j;
+};
+
+__device__ __forceinline__ float tf32_round(float x) {
+  // to the nearest value with a 10-bit mantissa (TF32), ties away from zero
   unsigned u = __float_as_uint(x);
   u = (u + 0x1000u) & 0xffffe000u;
   return __uint_as_float(u);
 }
 
-// writes the GEMM input columns (re in column b, im in column B + b) in the chosen precision
-__device__ __forceinline__ void put_x(float* xf, __nv_bfloat16* xh, __nv_bfloat16* xl, float* xlo, int mode, size_t ir,
-                                      size_t ii, float2 v) {
-  if (mode == PE_GEMM_BF16X3) {
-    const __nv_bfloat16 hr = __float2bfloat16(v.x), hi = __float2bfloat16(v.y);
-    xh[ir] = hr;
-    xh[ii] = hi;
-    xl[ir] = __float2bfloat16(v.x - __bfloat162float(hr));
-    xl[ii] = __float2bfloat16(v.y - __bfloat162float(hi));
-  } else if (mode == PE_GEMM_3XTF32) {
-    const float hr = tf32_hi(v.x), hi = tf32_hi(v.y);
-    xf[ir] = hr;
-    xf[ii] = hi;
-    xlo[ir] = v.x - hr;
-    xlo[ii] = v.y - hi;
+// X operand element (column col, row m) in the mode's representation
+template <int MODE>
+__device__ __forceinline__ void put_x(void* hi, void* lo, size_t idx, float v) {
+  if constexpr (MODE == PE_GEMM_BF16X3) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    static_cast<__nv_bfloat16*>(hi)[idx] = h;
+    static_cast<__nv_bfloat16*>(lo)[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+  } else if constexpr (MODE == PE_GEMM_3XTF32) {
+    const float h = tf32_round(v);
+    static_cast<float*>(hi)[idx] = h;
+    static_cast<float*>(lo)[idx] = v - h;
+  } else if constexpr (MODE == PE_GEMM_TF32) {
+    static_cast<float*>(hi)[idx] = tf32_round(v);
   } else {
-    xf[ir] = v.x;
-    xf[ii] = v.y;
+    static_cast<float*>(hi)[idx] = v;
   }
 }
 
-struct Args {
-  const GemmSolve* solves;
-  float2* Y;      // N x B spectral state (complex, row n = mode n+1, column b)
-  float2* T0;     // N x B
-  float2* ACC;    // N x B
-  const float* G; // N x 2B GEMM output (real columns)
-  float* XF;      // GEMM input, FP32 / TF32 hi
-  float* XLO;     // TF32 lo
-  __nv_bfloat16* XH;
-  __nv_bfloat16* XL;
-  int N, B, mode, j;
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// the epilogue of one output pair (row m; columns col = 2b and 2b + 1 of field b)
+template <int MODE, int EPI>
+__device__ __forceinline__ void epi_pair(const EpiArgs& a, int m, int col, float re, float im) {
+  const int b = col >> 1;
+  if (b >= a.B) return;  // padding columns stay zero
+  const size_t L = size_t(a.L), ir = size_t(col) * L + m, ii = ir + L;
+  if constexpr (EPI == kEpiOut) {
+    a.Gout[ir] = re;
+    a.Gout[ii] = im;
+  } else if constexpr (EPI == kEpiTimesV) {
+    const float v = a.solves[b].V[m];
+    put_x<MODE>(a.Xhi, a.Xlo, ir, v * re);
+    put_x<MODE>(a.Xhi, a.Xlo, ii, v * im);
+  } else {
+    const float2 t = cmulf(a.solves[b].B[size_t(a.j) * L + m], make_float2(re, im));
+    float2* acc = a.ACC + size_t(b) * L + m;
+    const float2 s = *acc;
+    *acc = make_float2(s.x + t.x, s.y + t.y);
+    if constexpr (EPI == kEpiTerm) {
+      put_x<MODE>(a.Xhi, a.Xlo, ir, t.x);
+      put_x<MODE>(a.Xhi, a.Xlo, ii, t.y);
+    }
+  }
+}
+
+template <int MODE>
+struct Traits {
+  static constexpr bool SPLIT = MODE != PE_GEMM_TF32;  // hi/lo operands, three products
+  static constexpr bool BF16 = MODE == PE_GEMM_BF16X3;
+  static constexpr int EL = BF16 ? 2 : 4;              // operand bytes
+  static constexpr int BK = kRowBytes / EL;            // K values per pipeline stage
+  static constexpr int A_BYTES = kBM * kRowBytes;      // one S slice (128 rows x 128 B)
+  static constexpr int B_BYTES = kBN * kRowBytes;      // one X slice (32 columns x 128 B)
+  static constexpr int STAGE_BYTES = (SPLIT ? 2 : 1) * (A_BYTES + B_BYTES);
+  static constexpr int STAGES = SPLIT ? 4 : 6;
+  static constexpr size_t SMEM = size_t(STAGES) * STAGE_BYTES + 1024;  // + alignment slack
+  static constexpr uint32_t IDESC = umma::instr_desc(kBM, kBN, BF16 ? umma::kFmtBF16 : umma::kFmtTF32);
 };
 
-// stage start: t0 = A_j y (spectral), acc = 0, X <- t0
-__global__ void k_stage_start(Args a) {
+// Y = S X for one 128 x 32 output tile with the fused epilogue (see the file comment).
+// Shared memory per stage: [S_hi slice | X_hi slice | S_lo slice | X_lo slice], 1024-byte aligned.
+template <int MODE, int EPI>
+__global__ void __launch_bounds__(kThreads, 1)
+    sssp_gemm_dst_kernel(const __grid_constant__ CUtensorMap mSh, const __grid_constant__ CUtensorMap mSl,
+                         const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
+                         EpiArgs ea) {
+  using T = Traits<MODE>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full[T::STAGES];
+  __shared__ __align__(8) uint64_t empty[T::STAGES];
+  __shared__ __align__(8) uint64_t done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM, c0 = blockIdx.y * kBN;
+  const int KB = ea.L / T::BK;
+  if (threadIdx.x == 0) abort_flag = *reinterpret_cast<volatile int*>(ea.status);
+  __syncthreads();
+  if (abort_flag) return;  // an earlier launch of the batch gave up: do nothing more
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < T::STAGES; ++s) {
+      umma::mbar_init(&full[s], 1);
+      umma::mbar_init(&empty[s], 1);
+    }
+    umma::mbar_init(&done, 1);
+    abort_flag = 0;
+    umma::fence_barrier_init();
+    umma::prefetch_tensormap(&mSh);
+    umma::prefetch_tensormap(&mXh);
+    if constexpr (T::SPLIT) {
+      umma::prefetch_tensormap(&mSl);
+      umma::prefetch_tensormap(&mXl);
+    }
+  }
+  if (warp == 0) {
+    umma::tmem_alloc(&tmem_base, kBN);
+    umma::tmem_relinquish();
+  }
+  umma::tc_fence_before();
+  __syncthreads();
+  umma::tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0) {  // TMA producer
+    int issued = 0;
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % T::STAGES;
+      if (kb >= T::STAGES && !umma::mbar_wait(&empty[s], ((kb / T::STAGES) - 1) & 1, kWaitNs)) {
+        abort_flag = 1;
+        break;
+      }
+      uint8_t* st = smem + size_t(s) * T::STAGE_BYTES;
+      umma::mbar_expect_tx(&full[s], T::STAGE_BYTES);
+      umma::tma_load_2d(st, &mSh, &full[s], kb * T::BK, m0);
+      umma::tma_load_2d(st + T::A_BYTES, &mXh, &full[s], kb * T::BK, c0);
+      if constexpr (T::SPLIT) {
+        umma::tma_load_2d(st + T::A_BYTES + T::B_BYTES, &mSl, &full[s], kb * T::BK, m0);
+        umma::tma_load_2d(st + 2 * T::A_BYTES + T::B_BYTES, &mXl, &full[s], kb * T::BK, c0);
+      }
+      issued = kb + 1;
+    }
+    // every load issued has landed before the CTA may leave (bounded)
+    for (int kb = (issued > T::STAGES ? issued - T::STAGES : 0); kb < issued; ++kb)
+      if (!umma::mbar_wait(&full[kb % T::STAGES], (kb / T::STAGES) & 1, kWaitNs)) abort_flag = 1;
+  } else if (warp == 1 && lane == 0) {  // MMA issuer
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % T::STAGES;
+      if (!umma::mbar_wait(&full[s], (kb / T::STAGES) & 1, kWaitNs)) {
+        abort_flag = 1;
+        break;
+      }
+      umma::tc_fence_after();
+      const uint8_t* st = smem + size_t(s) * T::STAGE_BYTES;
+      const uint64_t ah = umma::desc_sw128(st), bh = umma::desc_sw128(st + T::A_BYTES);
+      const uint64_t al = umma::desc_sw128(st + T::A_BYTES + T::B_BYTES);
+      const uint64_t bl = umma::desc_sw128(st + 2 * T::A_BYTES + T::B_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < kRowBytes / 32; ++kk) {  // MMA K steps of 32 bytes (16 BF16 / 8 TF32)
+        const uint64_t o = uint64_t(kk * 32) >> 4;
+        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+        if constexpr (T::BF16) {
+          umma::mma_bf16(tmem, ah + o, bh + o, T::IDESC, acc);
+          umma::mma_bf16(tmem, ah + o, bl + o, T::IDESC, 1u);
+          umma::mma_bf16(tmem, al + o, bh + o, T::IDESC, 1u);
+        } else {
+          umma::mma_tf32(tmem, ah + o, bh + o, T::IDESC, acc);
+          if constexpr (T::SPLIT) {
+            umma::mma_tf32(tmem, ah + o, bl + o, T::IDESC, 1u);
+            umma::mma_tf32(tmem, al + o, bh + o, T::IDESC, 1u);
+          }
+        }
+      }
+      umma::mma_commit(&empty[s]);  // the stage is free once these products have read it
+    }
+    umma::mma_commit(&done);  // arrives when every product issued has completed
+  }
+  __syncwarp();
+  // epilogue: every warp reads its 32 accumulator lanes (rows m0 + 32 w + lane)
+  const bool ok = umma::mbar_wait(&done, 0, kWaitNs);
+  umma::tc_fence_after();
+  __syncthreads();  // abort_flag is final
+  if (ok && !abort_flag) {
+    float v[32];
+    umma::tmem_ld32(tmem + (uint32_t(32 * warp) << 16), v);
+    const int m = m0 + 32 * warp + lane;
+#pragma unroll
+    for (int i = 0; i < kBN / 2; ++i) epi_pair<MODE, EPI>(ea, m, c0 + 2 * i, v[2 * i], v[2 * i + 1]);
+  } else if (threadIdx.x == 0) {
+    atomicExch(ea.status, kStatusTimeout);
+  }
+  umma::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tmem, kBN);
+}
+
+// FP32 reference contraction on the CUDA cores with the same epilogue: 64 x 32 output tiles,
+// 256 threads, each 4 rows x one complex column pair.
+template <int EPI>
+__global__ void __launch_bounds__(256)
+    sssp_gemm_dst_fp32_kernel(const float* __restrict__ S, const float* __restrict__ X, EpiArgs ea) {
+  constexpr int TM = 64, TN = 32, TK = 32;
+  __shared__ float As[TM][TK + 1];
+  __shared__ float Bs[TN][TK + 1];
+  const int L = ea.L;
+  const int m0 = blockIdx.x * TM, c0 = blockIdx.y * TN;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // column pair tx, rows ty + 16 r
+  float acc[4][2] = {};
+  for (int k0 = 0; k0 < L; k0 += TK) {
+    for (int i = threadIdx.x; i < TM * TK; i += 256) {
+      const int r = i / TK, k = i % TK;
+      As[r][k] = S[size_t(m0 + r) * L + k0 + k];
+    }
+    for (int i = threadIdx.x; i < TN * TK; i += 256) {
+      const int c = i / TK, k = i % TK;
+      Bs[c][k] = X[size_t(c0 + c) * L + k0 + k];
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < TK; ++k) {
+      const float b0 = Bs[2 * tx][k], b1 = Bs[2 * tx + 1][k];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float a = As[ty + 16 * r][k];
+        acc[r][0] = fmaf(a, b0, acc[r][0]);
+        acc[r][1] = fmaf(a, b1, acc[r][1]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) epi_pair<PE_GEMM_FP32, EPI>(ea, m0 + ty + 16 * r, c0 + 2 * tx, acc[r][0], acc[r][1]);
+}
+
+// element-wise parts of the step, one thread per (field b, mode m)
+struct ElemArgs {
+  const GemmSolve* solves;
+  float2* Y;    // B x L spectral state
+  float2* ACC;  // B x L
+  void* Xhi;
+  void* Xlo;
+  int L, B, j;
+  float scale;
+};
+
+// stage start: t_0 = A_j y (spectral), acc = 0, X <- t_0
+template <int MODE>
+__global__ void k_stage_start(ElemArgs a) {
   const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= size_t(a.N) * a.B) return;
-  const int n = int(idx % a.N), b = int(idx / a.N);
-  const GemmSolve& s = a.solves[b];
-  const size_t L = size_t(a.N) + 1;
-  const float2 Av = s.A[size_t(a.j) * L + n + 1], y = a.Y[idx];
-  const float2 t0 = make_float2(fmaf(Av.x, y.x, -Av.y * y.y), fmaf(Av.x, y.y, Av.y * y.x));
-  a.T0[idx] = t0;
+  const size_t L = size_t(a.L);
+  if (idx >= L * a.B) return;
+  const int m = int(idx % L), b = int(idx / L);
+  const float2 t0 = cmulf(a.solves[b].A[size_t(a.j) * L + m], a.Y[idx]);
   a.ACC[idx] = make_float2(0.f, 0.f);
-  put_x(a.XF, a.XH, a.XL, a.XLO, a.mode, size_t(b) * a.N + n, size_t(a.B + b) * a.N + n, t0);
-}
-
-// depth space: X <- V .* (GEMM output)
-__global__ void k_times_v(Args a) {
-  const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= size_t(a.N) * a.B) return;
-  const int n = int(idx % a.N), b = int(idx / a.N);
-  const float v = a.solves[b].V[n + 1];
-  const size_t ir = size_t(b) * a.N + n, ii = size_t(a.B + b) * a.N + n;
-  put_x(a.XF, a.XH, a.XL, a.XLO, a.mode, ir, ii, make_float2(v * a.G[ir], v * a.G[ii]));
-}
-
-// spectral: t_m = B_j .* (GEMM output); acc += t_m; X <- t_m
-__global__ void k_term(Args a, int write_x) {
-  const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= size_t(a.N) * a.B) return;
-  const int n = int(idx % a.N), b = int(idx / a.N);
-  const size_t L = size_t(a.N) + 1;
-  const float2 Bv = a.solves[b].B[size_t(a.j) * L + n + 1];
-  const size_t ir = size_t(b) * a.N + n, ii = size_t(a.B + b) * a.N + n;
-  const float2 u = make_float2(a.G[ir], a.G[ii]);
-  const float2 th = make_float2(fmaf(Bv.x, u.x, -Bv.y * u.y), fmaf(Bv.x, u.y, Bv.y * u.x));
-  const float2 acc = a.ACC[idx];
-  a.ACC[idx] = make_float2(acc.x + th.x, acc.y + th.y);
-  if (write_x) put_x(a.XF, a.XH, a.XL, a.XLO, a.mode, ir, ii, th);
+  put_x<MODE>(a.Xhi, a.Xlo, size_t(2 * b) * L + m, t0.x);
+  put_x<MODE>(a.Xhi, a.Xlo, size_t(2 * b + 1) * L + m, t0.y);
 }
 
 // stage end: y = R_j y (hi/lo multiplier) + beta_j acc
-__global__ void k_stage_end(Args a) {
+__global__ void k_stage_end(ElemArgs a) {
   const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= size_t(a.N) * a.B) return;
-  const int n = int(idx % a.N), b = int(idx / a.N);
+  const size_t L = size_t(a.L);
+  if (idx >= L * a.B) return;
+  const int m = int(idx % L), b = int(idx / L);
   const GemmSolve& s = a.solves[b];
-  const size_t L = size_t(a.N) + 1;
-  const float4 g = s.R[size_t(a.j) * L + n + 1];
+  const float4 g = s.R[size_t(a.j) * L + m];
   const float2 y = a.Y[idx], acc = a.ACC[idx], bj = s.beta[a.j];
   const float re_lo = fmaf(g.z, y.x, -g.w * y.y), im_lo = fmaf(g.z, y.y, g.w * y.x);
   const float re = fmaf(g.x, y.x, fmaf(-g.y, y.y, re_lo)), im = fmaf(g.x, y.y, fmaf(g.y, y.x, im_lo));
   a.Y[idx] = make_float2(re + fmaf(bj.x, acc.x, -bj.y * acc.y), im + fmaf(bj.x, acc.y, bj.y * acc.x));
 }
 
-// X <- scale * Y (for the final depth-space field)
-__global__ void k_out(Args a, float scale) {
+// X <- scale y (for the depth-space read-out)
+template <int MODE>
+__global__ void k_out(ElemArgs a) {
   const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= size_t(a.N) * a.B) return;
-  const int n = int(idx % a.N), b = int(idx / a.N);
+  const size_t L = size_t(a.L);
+  if (idx >= L * a.B) return;
+  const int m = int(idx % L), b = int(idx / L);
   const float2 y = a.Y[idx];
-  put_x(a.XF, a.XH, a.XL, a.XLO, a.mode, size_t(b) * a.N + n, size_t(a.B + b) * a.N + n,
-        make_float2(scale * y.x, scale * y.y));
+  put_x<MODE>(a.Xhi, a.Xlo, size_t(2 * b) * L + m, a.scale * y.x);
+  put_x<MODE>(a.Xhi, a.Xlo, size_t(2 * b + 1) * L + m, a.scale * y.y);
 }
 
-__global__ void k_split_s(const float* S, float* shi, float* slo, __nv_bfloat16* bh, __nv_bfloat16* bl, size_t n,
-                          int mode) {
+// S in the mode's representation (from the FP32 matrix rounded once from FP64)
+__global__ void k_split_s(const float* S, void* hi, void* lo, size_t n, int mode) {
   const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const float v = S[i];
-  if (mode == PE_GEMM_BF16X3) {
-    const __nv_bfloat16 h = __float2bfloat16(v);
-    bh[i] = h;
-    bl[i] = __float2bfloat16(v - __bfloat162float(h));
-  } else if (mode == PE_GEMM_3XTF32) {
-    const float h = tf32_hi(v);
-    shi[i] = h;
-    slo[i] = v - h;
+  switch (mode) {
+    case PE_GEMM_BF16X3: put_x<PE_GEMM_BF16X3>(hi, lo, i, S[i]); break;
+    case PE_GEMM_3XTF32: put_x<PE_GEMM_3XTF32>(hi, lo, i, S[i]); break;
+    case PE_GEMM_TF32: put_x<PE_GEMM_TF32>(hi, lo, i, S[i]); break;
+    default: put_x<PE_GEMM_FP32>(hi, lo, i, S[i]); break;
   }
 }
 
-// gather the spectral states of the plans (mode index 1..N) into Y
-__global__ void k_gather(const float2* const* yhats, float2* Y, int N, int B) {
+// the plans' spectral states (L-indexed) into Y
+__global__ void k_gather(const float2* const* yhats, float2* Y, int L, int B) {
   const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= size_t(N) * B) return;
-  const int n = int(idx % N), b = int(idx / N);
-  Y[idx] = yhats[b][n + 1];
+  if (idx >= size_t(L) * B) return;
+  Y[idx] = yhats[idx / L][idx % L];
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+  static EncodeTiled fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
+
+// 2D tensor map of a row-major matrix rows x inner (inner contiguous), tiles of box_rows rows x
+// one 128-byte slice, 128-byte swizzle
+bool make_map(CUtensorMap* m, void* base, bool bf16, size_t inner, size_t rows, int box_rows) {
+  EncodeTiled enc = encode_fn();
+  if (!enc) return false;
+  const size_t el = bf16 ? 2 : 4;
+  const cuuint64_t dims[2] = {cuuint64_t(inner), cuuint64_t(rows)};
+  const cuuint64_t strides[1] = {cuuint64_t(inner * el)};
+  const cuuint32_t box[2] = {cuuint32_t(kRowBytes / el), cuuint32_t(box_rows)};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
 
 struct pe_gemm_batch {
-  int N = 0, B = 0, p = 0, terms = 0, mode = 0;
+  int N = 0, L = 0, B = 0, C = 0, p = 0, terms = 0, mode = 0;
   std::vector<double> sigma;  // k0 dr of every member (the carrier phase per step)
   long long steps_done = 0;
   cudaStream_t stream = nullptr;
-  cublasHandle_t h = nullptr;
-  void* ws = nullptr;
   GemmSolve* dSolves = nullptr;
-  float* S = nullptr;  // N x N FP32
-  float* Shi = nullptr;
-  float* Slo = nullptr;
-  __nv_bfloat16* Sbh = nullptr;
-  __nv_bfloat16* Sbl = nullptr;
-  float2 *Y = nullptr, *T0 = nullptr, *ACC = nullptr;
-  float *G = nullptr, *XF = nullptr, *XLO = nullptr;
-  __nv_bfloat16 *XH = nullptr, *XL = nullptr;
+  void* Shi = nullptr;  // L x L operand (BF16 or FP32); FP32 mode: the FP32 matrix
+  void* Slo = nullptr;
+  void* Xhi[2] = {nullptr, nullptr};  // ping-pong operands C x L
+  void* Xlo[2] = {nullptr, nullptr};
+  float2* Y = nullptr;
+  float2* ACC = nullptr;
+  float* G = nullptr;  // C x L read-out
+  int* status = nullptr;
+  CUtensorMap mS[2], mX[2][2];  // [hi, lo]; [buffer][hi, lo]
   cudaGraphExec_t step_graph = nullptr;
+  unsigned long long gemms_per_step = 0;
   std::string err;
 };
 
@@ -195,77 +421,126 @@ pe_status gfail(pe_gemm_batch* g, pe_status s, const std::string& m) {
   return s;
 }
 
-// G = S X in the batch's precision
-cublasStatus_t gemm(pe_gemm_batch* g) {
-  const int m = g->N, n = 2 * g->B, k = g->N;
-  const float one = 1.f, zero = 0.f;
-  switch (g->mode) {
-    case PE_GEMM_FP32:
-      return cublasGemmEx(g->h, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, g->S, CUDA_R_32F, m, g->XF, CUDA_R_32F, k,
-                          &zero, g->G, CUDA_R_32F, m, CUBLAS_COMPUTE_32F_PEDANTIC, CUBLAS_GEMM_DEFAULT);
-    case PE_GEMM_TF32:
-      return cublasGemmEx(g->h, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, g->S, CUDA_R_32F, m, g->XF, CUDA_R_32F, k,
-                          &zero, g->G, CUDA_R_32F, m, CUBLAS_COMPUTE_32F_FAST_TF32, CUBLAS_GEMM_DEFAULT);
-    case PE_GEMM_3XTF32: {
-      cublasStatus_t s = cublasGemmEx(g->h, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, g->Shi, CUDA_R_32F, m, g->XF,
-                                      CUDA_R_32F, k, &zero, g->G, CUDA_R_32F, m, CUBLAS_COMPUTE_32F_FAST_TF32,
-                                      CUBLAS_GEMM_DEFAULT);
-      if (s != CUBLAS_STATUS_SUCCESS) return s;
-      s = cublasGemmEx(g->h, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, g->Shi, CUDA_R_32F, m, g->XLO, CUDA_R_32F, k,
-                       &one, g->G, CUDA_R_32F, m, CUBLAS_COMPUTE_32F_FAST_TF32, CUBLAS_GEMM_DEFAULT);
-      if (s != CUBLAS_STATUS_SUCCESS) return s;
-      return cublasGemmEx(g->h, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, g->Slo, CUDA_R_32F, m, g->XF, CUDA_R_32F, k,
-                          &one, g->G, CUDA_R_32F, m, CUBLAS_COMPUTE_32F_FAST_TF32, CUBLAS_GEMM_DEFAULT);
-    }
-    case PE_GEMM_BF16X3: {
-      cublasStatus_t s = cublasGemmEx(g->h, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, g->Sbh, CUDA_R_16BF, m, g->XH,
-                                      CUDA_R_16BF, k, &zero, g->G, CUDA_R_32F, m, CUBLAS_COMPUTE_32F,
-                                      CUBLAS_GEMM_DEFAULT);
-      if (s != CUBLAS_STATUS_SUCCESS) return s;
-      s = cublasGemmEx(g->h, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, g->Sbh, CUDA_R_16BF, m, g->XL, CUDA_R_16BF, k,
-                       &one, g->G, CUDA_R_32F, m, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
-      if (s != CUBLAS_STATUS_SUCCESS) return s;
-      return cublasGemmEx(g->h, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, g->Sbl, CUDA_R_16BF, m, g->XH, CUDA_R_16BF,
-                          k, &one, g->G, CUDA_R_32F, m, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
-    }
-  }
-  return CUBLAS_STATUS_INVALID_VALUE;
-}
-
-Args args_of(pe_gemm_batch* g, int j) {
-  Args a;
+EpiArgs epi_args(pe_gemm_batch* g, int j, int out_buf) {
+  EpiArgs a;
   a.solves = g->dSolves;
-  a.Y = g->Y;
-  a.T0 = g->T0;
   a.ACC = g->ACC;
-  a.G = g->G;
-  a.XF = g->XF;
-  a.XLO = g->XLO;
-  a.XH = g->XH;
-  a.XL = g->XL;
-  a.N = g->N;
+  a.Xhi = g->Xhi[out_buf];
+  a.Xlo = g->Xlo[out_buf];
+  a.Gout = g->G;
+  a.status = g->status;
+  a.L = g->L;
   a.B = g->B;
-  a.mode = g->mode;
   a.j = j;
   return a;
 }
 
-// enqueue one range step (all stages, fixed term count) on g->stream
-pe_status enqueue_step(pe_gemm_batch* g) {
-  const size_t tot = size_t(g->N) * g->B;
-  const int th = 256, bl = int((tot + th - 1) / th);
-  for (int j = 0; j < g->p; ++j) {
-    Args a = args_of(g, j);
-    k_stage_start<<<bl, th, 0, g->stream>>>(a);
-    if (gemm(g) != CUBLAS_STATUS_SUCCESS) return gfail(g, PE_ERR_CUDA, "cuBLAS GEMM failed");  // t_0 in depth space
-    for (int m = 1; m < g->terms; ++m) {
-      k_times_v<<<bl, th, 0, g->stream>>>(a);
-      if (gemm(g) != CUBLAS_STATUS_SUCCESS) return gfail(g, PE_ERR_CUDA, "cuBLAS GEMM failed");  // DST(V t)
-      const int last = (m == g->terms - 1);
-      k_term<<<bl, th, 0, g->stream>>>(a, last ? 0 : 1);
-      if (!last && gemm(g) != CUBLAS_STATUS_SUCCESS) return gfail(g, PE_ERR_CUDA, "cuBLAS GEMM failed");
+template <int MODE, int EPI>
+cudaError_t launch_gemm_t(pe_gemm_batch* g, int in_buf, const EpiArgs& a) {
+  if constexpr (MODE == PE_GEMM_FP32) {
+    const dim3 grid(g->L / 64, g->C / 32);
+    sssp_gemm_dst_fp32_kernel<EPI><<<grid, 256, 0, g->stream>>>(static_cast<const float*>(g->Shi),
+                                                                static_cast<const float*>(g->Xhi[in_buf]), a);
+  } else {
+    using T = Traits<MODE>;
+    static std::mutex mu;
+    static int attr_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      if (attr_dev != dev) {
+        cudaError_t e = cudaFuncSetAttribute(sssp_gemm_dst_kernel<MODE, EPI>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(T::SMEM));
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
+      }
     }
-    k_stage_end<<<bl, th, 0, g->stream>>>(a);
+    const dim3 grid(g->L / kBM, g->C / kBN);
+    sssp_gemm_dst_kernel<MODE, EPI><<<grid, kThreads, T::SMEM, g->stream>>>(g->mS[0], g->mS[1], g->mX[in_buf][0],
+                                                                            g->mX[in_buf][1], a);
+  }
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_gemm_m(pe_gemm_batch* g, int epi, int in_buf, const EpiArgs& a) {
+  switch (epi) {
+    case kEpiTimesV: return launch_gemm_t<MODE, kEpiTimesV>(g, in_buf, a);
+    case kEpiTerm: return launch_gemm_t<MODE, kEpiTerm>(g, in_buf, a);
+    case kEpiTermLast: return launch_gemm_t<MODE, kEpiTermLast>(g, in_buf, a);
+    default: return launch_gemm_t<MODE, kEpiOut>(g, in_buf, a);
+  }
+}
+
+// one GEMM of the operand in buffer in_buf, epilogue writing buffer 1 - in_buf
+cudaError_t launch_gemm(pe_gemm_batch* g, int epi, int in_buf, int j) {
+  const EpiArgs a = epi_args(g, j, 1 - in_buf);
+  ++g->gemms_per_step;
+  switch (g->mode) {
+    case PE_GEMM_BF16X3: return launch_gemm_m<PE_GEMM_BF16X3>(g, epi, in_buf, a);
+    case PE_GEMM_TF32: return launch_gemm_m<PE_GEMM_TF32>(g, epi, in_buf, a);
+    case PE_GEMM_3XTF32: return launch_gemm_m<PE_GEMM_3XTF32>(g, epi, in_buf, a);
+    default: return launch_gemm_m<PE_GEMM_FP32>(g, epi, in_buf, a);
+  }
+}
+
+ElemArgs elem_args(pe_gemm_batch* g, int j, int buf) {
+  ElemArgs a;
+  a.solves = g->dSolves;
+  a.Y = g->Y;
+  a.ACC = g->ACC;
+  a.Xhi = g->Xhi[buf];
+  a.Xlo = g->Xlo[buf];
+  a.L = g->L;
+  a.B = g->B;
+  a.j = j;
+  a.scale = 1.f;
+  return a;
+}
+
+template <int MODE>
+void launch_start(pe_gemm_batch* g, const ElemArgs& a, int bl) {
+  k_stage_start<MODE><<<bl, 256, 0, g->stream>>>(a);
+}
+
+void stage_start(pe_gemm_batch* g, const ElemArgs& a, int bl) {
+  switch (g->mode) {
+    case PE_GEMM_BF16X3: launch_start<PE_GEMM_BF16X3>(g, a, bl); break;
+    case PE_GEMM_TF32: launch_start<PE_GEMM_TF32>(g, a, bl); break;
+    case PE_GEMM_3XTF32: launch_start<PE_GEMM_3XTF32>(g, a, bl); break;
+    default: launch_start<PE_GEMM_FP32>(g, a, bl); break;
+  }
+}
+
+void stage_out(pe_gemm_batch* g, const ElemArgs& a, int bl) {
+  switch (g->mode) {
+    case PE_GEMM_BF16X3: k_out<PE_GEMM_BF16X3><<<bl, 256, 0, g->stream>>>(a); break;
+    case PE_GEMM_TF32: k_out<PE_GEMM_TF32><<<bl, 256, 0, g->stream>>>(a); break;
+    case PE_GEMM_3XTF32: k_out<PE_GEMM_3XTF32><<<bl, 256, 0, g->stream>>>(a); break;
+    default: k_out<PE_GEMM_FP32><<<bl, 256, 0, g->stream>>>(a); break;
+  }
+}
+
+// enqueue one range step (all stages, the fixed term count) on g->stream:
+//   t_0 = A_j y -> X0;  GEMM X0 (depth t_0) epilogue V.*  -> X1
+//   m = 1 .. terms-1:   GEMM X1 (spectral)  epilogue t_m = B_j.*, acc += t_m -> X0
+//                       GEMM X0 (depth t_m) epilogue V.*  -> X1        (not after the last term)
+//   y = R_j y + beta_j acc
+pe_status enqueue_step(pe_gemm_batch* g) {
+  const size_t tot = size_t(g->L) * g->B;
+  const int bl = int((tot + 255) / 256);
+  g->gemms_per_step = 0;
+  for (int j = 0; j < g->p; ++j) {
+    stage_start(g, elem_args(g, j, 0), bl);
+    cudaError_t e = launch_gemm(g, kEpiTimesV, 0, j);
+    for (int m = 1; m < g->terms && e == cudaSuccess; ++m) {
+      const bool last = (m == g->terms - 1);
+      e = launch_gemm(g, last ? kEpiTermLast : kEpiTerm, 1, j);
+      if (!last && e == cudaSuccess) e = launch_gemm(g, kEpiTimesV, 0, j);
+    }
+    if (e != cudaSuccess) return gfail(g, PE_ERR_CUDA, std::string("GEMM launch: ") + cudaGetErrorString(e));
+    k_stage_end<<<bl, 256, 0, g->stream>>>(elem_args(g, j, 0));
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return gfail(g, PE_ERR_CUDA, cudaGetErrorString(e));
@@ -280,10 +555,11 @@ pe_status pe_gemm_batch_create(pe_gemm_batch** out, pe_plan** plans, int count, 
   if (!out || !plans || count < 1 || mode < PE_GEMM_FP32 || mode > PE_GEMM_BF16X3) return PE_ERR_ARG;
   *out = nullptr;
   pe_plan* p0 = plans[0];
+  if (!p0) return PE_ERR_ARG;
   for (int i = 0; i < count; ++i) {
     pe_plan* p = plans[i];
     if (!p || p->N != p0->N || p->p != p0->p || p->terms != p0->terms || p->dr != p0->dr) {
-      if (p0) p0->err = "GEMM batch: plans must share N, Pade order, term count and dr";
+      p0->err = "GEMM batch: plans must share N, Pade order, term count and dr";
       return PE_ERR_ARG;
     }
     if (!p->field_set || p->terms < 2 || p->nodes != 1 || p->complex_profile || p->bc != PE_BC_DIRICHLET) {
@@ -291,51 +567,69 @@ pe_status pe_gemm_batch_create(pe_gemm_batch** out, pe_plan** plans, int count, 
       return PE_ERR_STATE;
     }
   }
+  if (p0->L < kBM || p0->L > 16384) {
+    p0->err = "GEMM batch: N + 1 must be a power of two in [128, 16384]";
+    return PE_ERR_ARG;
+  }
   pe_gemm_batch* g = new pe_gemm_batch();
   g->N = p0->N;
+  g->L = p0->L;
   g->B = count;
+  g->C = ((2 * count + kBN - 1) / kBN) * kBN;
   g->p = p0->p;
   g->terms = p0->terms;
   g->mode = mode;
   g->stream = p0->stream;
-  const size_t N = size_t(g->N), NB = N * count, NN = N * N;
+  const size_t L = size_t(g->L), LB = L * count, LL = L * L, LC = L * size_t(g->C);
+  const bool bf16 = (mode == PE_GEMM_BF16X3), split = (mode == PE_GEMM_BF16X3 || mode == PE_GEMM_3XTF32);
+  const size_t el = bf16 ? 2 : 4;
   auto bail = [&](const char* what) {
     p0->err = std::string("GEMM batch: ") + what;
     pe_gemm_batch_destroy(g);
     return PE_ERR_CUDA;
   };
-  if (cublasCreate(&g->h) != CUBLAS_STATUS_SUCCESS) return bail("cublasCreate");
-  cublasSetStream(g->h, g->stream);
-  const size_t ws_bytes = size_t(32) << 20;
-  if (cudaMalloc(&g->ws, ws_bytes) != cudaSuccess) return bail("workspace");
-  cublasSetWorkspace(g->h, g->ws, ws_bytes);
-  if (cudaMalloc(&g->S, sizeof(float) * NN) != cudaSuccess || cudaMalloc(&g->Y, sizeof(float2) * NB) != cudaSuccess ||
-      cudaMalloc(&g->T0, sizeof(float2) * NB) != cudaSuccess || cudaMalloc(&g->ACC, sizeof(float2) * NB) != cudaSuccess ||
-      cudaMalloc(&g->G, sizeof(float) * 2 * NB) != cudaSuccess || cudaMalloc(&g->XF, sizeof(float) * 2 * NB) != cudaSuccess ||
-      cudaMalloc(&g->dSolves, sizeof(GemmSolve) * count) != cudaSuccess)
+  float* S32 = nullptr;
+  if (cudaMalloc(&S32, sizeof(float) * LL) != cudaSuccess) return bail("cudaMalloc");
+  bool okm = cudaMalloc(&g->Shi, el * LL) == cudaSuccess && cudaMalloc(&g->Y, sizeof(float2) * LB) == cudaSuccess &&
+             cudaMalloc(&g->ACC, sizeof(float2) * LB) == cudaSuccess &&
+             cudaMalloc(&g->G, sizeof(float) * LC) == cudaSuccess &&
+             cudaMalloc(&g->dSolves, sizeof(GemmSolve) * count) == cudaSuccess &&
+             cudaMalloc(&g->status, sizeof(int)) == cudaSuccess;
+  for (int b = 0; b < 2 && okm; ++b) okm = cudaMalloc(&g->Xhi[b], el * LC) == cudaSuccess;
+  if (okm && split) {
+    okm = cudaMalloc(&g->Slo, el * LL) == cudaSuccess;
+    for (int b = 0; b < 2 && okm; ++b) okm = cudaMalloc(&g->Xlo[b], el * LC) == cudaSuccess;
+  }
+  if (!okm) {
+    cudaFree(S32);
     return bail("cudaMalloc");
-  if (mode == PE_GEMM_3XTF32 &&
-      (cudaMalloc(&g->Shi, sizeof(float) * NN) != cudaSuccess || cudaMalloc(&g->Slo, sizeof(float) * NN) != cudaSuccess ||
-       cudaMalloc(&g->XLO, sizeof(float) * 2 * NB) != cudaSuccess))
-    return bail("cudaMalloc");
-  if (mode == PE_GEMM_BF16X3 &&
-      (cudaMalloc(&g->Sbh, sizeof(__nv_bfloat16) * NN) != cudaSuccess ||
-       cudaMalloc(&g->Sbl, sizeof(__nv_bfloat16) * NN) != cudaSuccess ||
-       cudaMalloc(&g->XH, sizeof(__nv_bfloat16) * 2 * NB) != cudaSuccess ||
-       cudaMalloc(&g->XL, sizeof(__nv_bfloat16) * 2 * NB) != cudaSuccess))
-    return bail("cudaMalloc");
-  // the DST-I matrix in FP64, rounded once (symmetric, so row/column order does not matter)
-  std::vector<float> S(NN);
-  const long long L = (long long)N + 1;
-  for (size_t m = 1; m <= N; ++m)
-    for (size_t n = 1; n <= N; ++n) {
-      const long long q = (long long)((m * n) % size_t(2 * L));
-      S[(m - 1) * N + (n - 1)] = float(std::sin(M_PI * double(q) / double(L)));
+  }
+  for (int b = 0; b < 2; ++b) {  // padding columns must read as zero
+    cudaMemset(g->Xhi[b], 0, el * LC);
+    if (g->Xlo[b]) cudaMemset(g->Xlo[b], 0, el * LC);
+  }
+  cudaMemset(g->status, 0, sizeof(int));
+  // the DST-I matrix in FP64, rounded once (symmetric; row and column 0 are the zero pads)
+  std::vector<float> S(LL);
+  for (size_t m = 0; m < L; ++m)
+    for (size_t n = 0; n < L; ++n) {
+      const size_t q = (m * n) % (2 * L);
+      S[m * L + n] = float(std::sin(M_PI * double(q) / double(L)));
     }
-  if (cudaMemcpy(g->S, S.data(), sizeof(float) * NN, cudaMemcpyHostToDevice) != cudaSuccess) return bail("upload");
-  if (mode == PE_GEMM_3XTF32 || mode == PE_GEMM_BF16X3) {
-    k_split_s<<<int((NN + 255) / 256), 256, 0, g->stream>>>(g->S, g->Shi, g->Slo, g->Sbh, g->Sbl, NN, mode);
-    if (cudaGetLastError() != cudaSuccess) return bail("split");
+  if (cudaMemcpy(S32, S.data(), sizeof(float) * LL, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(S32);
+    return bail("upload");
+  }
+  k_split_s<<<int((LL + 255) / 256), 256, 0, g->stream>>>(S32, g->Shi, g->Slo, LL, mode);
+  cudaStreamSynchronize(g->stream);
+  cudaFree(S32);
+  if (cudaGetLastError() != cudaSuccess) return bail("split");
+  if (mode != PE_GEMM_FP32) {
+    bool okt = make_map(&g->mS[0], g->Shi, bf16, L, L, kBM) && make_map(&g->mS[1], split ? g->Slo : g->Shi, bf16, L, L, kBM);
+    for (int b = 0; b < 2 && okt; ++b)
+      okt = make_map(&g->mX[b][0], g->Xhi[b], bf16, L, size_t(g->C), kBN) &&
+            make_map(&g->mX[b][1], split ? g->Xlo[b] : g->Xhi[b], bf16, L, size_t(g->C), kBN);
+    if (!okt) return bail("tensor map (cuTensorMapEncodeTiled)");
   }
   std::vector<GemmSolve> sv(count);
   std::vector<const float2*> yh(count);
@@ -352,17 +646,16 @@ pe_status pe_gemm_batch_create(pe_gemm_batch** out, pe_plan** plans, int count, 
   const float2** dyh = nullptr;
   if (cudaMalloc(&dyh, sizeof(float2*) * count) != cudaSuccess) return bail("cudaMalloc");
   cudaMemcpy(dyh, yh.data(), sizeof(float2*) * count, cudaMemcpyHostToDevice);
-  k_gather<<<int((NB + 255) / 256), 256, 0, g->stream>>>(dyh, g->Y, g->N, count);
+  k_gather<<<int((LB + 255) / 256), 256, 0, g->stream>>>(dyh, g->Y, g->L, count);
   cudaStreamSynchronize(g->stream);
   cudaFree(dyh);
   if (cudaGetLastError() != cudaSuccess) return bail("gather");
   for (int i = 0; i < count; ++i) g->sigma.push_back(plans[i]->k0 * plans[i]->dr);
-  // one range step as a CUDA graph (cuBLAS runs on the user workspace, so it can be captured)
+  // one range step as a CUDA graph
   cudaStream_t cap = nullptr;
   if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return bail("stream");
   cudaStream_t keep = g->stream;
   g->stream = cap;
-  cublasSetStream(g->h, cap);
   cudaGraph_t graph = nullptr;
   if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return bail("capture");
   pe_status st = enqueue_step(g);
@@ -370,7 +663,6 @@ pe_status pe_gemm_batch_create(pe_gemm_batch** out, pe_plan** plans, int count, 
   if (cudaGraphInstantiate(&g->step_graph, graph, 0) != cudaSuccess) return bail("instantiate");
   cudaGraphDestroy(graph);
   g->stream = keep;
-  cublasSetStream(g->h, keep);
   cudaStreamDestroy(cap);
   *out = g;
   return PE_OK;
@@ -386,20 +678,27 @@ pe_status pe_gemm_batch_march(pe_gemm_batch* g, int steps) {
 
 pe_status pe_gemm_batch_read_field(pe_gemm_batch* g, int index, float* out) {
   if (!g || !out || index < 0 || index >= g->B) return PE_ERR_ARG;
-  Args a = args_of(g, 0);
-  const size_t tot = size_t(g->N) * g->B;
-  k_out<<<int((tot + 255) / 256), 256, 0, g->stream>>>(a, float(2.0 / double(g->N + 1)));
-  if (gemm(g) != CUBLAS_STATUS_SUCCESS) return gfail(g, PE_ERR_CUDA, "cuBLAS GEMM failed");
-  std::vector<float> re(g->N), im(g->N);
-  cudaMemcpyAsync(re.data(), g->G + size_t(index) * g->N, sizeof(float) * g->N, cudaMemcpyDeviceToHost, g->stream);
-  cudaMemcpyAsync(im.data(), g->G + size_t(g->B + index) * g->N, sizeof(float) * g->N, cudaMemcpyDeviceToHost,
+  const size_t tot = size_t(g->L) * g->B;
+  ElemArgs a = elem_args(g, 0, 0);
+  a.scale = float(2.0 / double(g->L));
+  stage_out(g, a, int((tot + 255) / 256));
+  const unsigned long long keep = g->gemms_per_step;
+  cudaError_t e = launch_gemm(g, kEpiOut, 0, 0);
+  g->gemms_per_step = keep;
+  if (e != cudaSuccess) return gfail(g, PE_ERR_CUDA, std::string("GEMM launch: ") + cudaGetErrorString(e));
+  std::vector<float> re(g->L), im(g->L);
+  int status = 0;
+  cudaMemcpyAsync(re.data(), g->G + size_t(2 * index) * g->L, sizeof(float) * g->L, cudaMemcpyDeviceToHost, g->stream);
+  cudaMemcpyAsync(im.data(), g->G + size_t(2 * index + 1) * g->L, sizeof(float) * g->L, cudaMemcpyDeviceToHost,
                   g->stream);
+  cudaMemcpyAsync(&status, g->status, sizeof(int), cudaMemcpyDeviceToHost, g->stream);
   if (cudaStreamSynchronize(g->stream) != cudaSuccess) return gfail(g, PE_ERR_CUDA, "sync");
+  if (status != 0) return gfail(g, PE_ERR_TIMEOUT, "GEMM kernel: a barrier wait ran out (device status set)");
   const double ph = std::fmod(g->sigma[index] * double(g->steps_done), 2.0 * M_PI);
   const double c = std::cos(ph), s = std::sin(ph);
-  for (int n = 0; n < g->N; ++n) {
-    out[2 * n] = float(c * re[n] - s * im[n]);
-    out[2 * n + 1] = float(c * im[n] + s * re[n]);
+  for (int n = 0; n < g->N; ++n) {  // depth index n + 1 of the L-indexed output
+    out[2 * n] = float(c * re[n + 1] - s * im[n + 1]);
+    out[2 * n + 1] = float(c * im[n + 1] + s * re[n + 1]);
   }
   return PE_OK;
 }
@@ -410,22 +709,17 @@ void pe_gemm_batch_destroy(pe_gemm_batch* g) {
   if (!g) return;
   if (g->stream) cudaStreamSynchronize(g->stream);
   if (g->step_graph) cudaGraphExecDestroy(g->step_graph);
-  if (g->h) cublasDestroy(g->h);
-  cudaFree(g->ws);
   cudaFree(g->dSolves);
-  cudaFree(g->S);
   cudaFree(g->Shi);
   cudaFree(g->Slo);
-  cudaFree(g->Sbh);
-  cudaFree(g->Sbl);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(g->Xhi[b]);
+    cudaFree(g->Xlo[b]);
+  }
   cudaFree(g->Y);
-  cudaFree(g->T0);
   cudaFree(g->ACC);
   cudaFree(g->G);
-  cudaFree(g->XF);
-  cudaFree(g->XLO);
-  cudaFree(g->XH);
-  cudaFree(g->XL);
+  cudaFree(g->status);
   delete g;
 }
 

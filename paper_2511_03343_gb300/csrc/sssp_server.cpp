@@ -17,11 +17,18 @@
 //                        request's profile nodes (V = n^2 - 1): with n^2 = (c0/c)^2 the
 //                        rescaling n^2 -> s n^2, k0 -> k0/sqrt(s), s = 2/(min n^2 + max n^2),
 //                        keeps k0^2 n^2 = (omega/c)^2 and centres V on zero;
-//   PE_ADMIT_CONVERGENT_ORDER lowers the Pade order until the series converges for every
-//                        term j: the FP64 bound rho_j = max|V| max_m |b_j/(1 + b_j lambda_m)|
-//                        is below 1, or, where it is not, an FP64 power iteration on
-//                        -b_j L_j^{-1} V (DST-I by a host FFT) estimates the spectral radius
-//                        below 0.98.  A request that diverges at every order fails at admission.
+//   PE_ADMIT_CONVERGENT_ORDER lowers the Pade order until the series, cut at the request's
+//                        term limit M, is accurate for every term j: the contraction rate
+//                        rho_j of -b_j L_j^{-1} V must satisfy rho_j^(M-1) <= 1e-5, i.e.
+//                        rho_j <= 0.35 for M = 12.  rho_j is bounded in FP64 by
+//                        max|V| max_m |b_j/(1 + b_j lambda_m)|; where that bound is not small
+//                        enough, an FP64 power iteration (DST-I by a host FFT, on the request's
+//                        grid or, beyond 1023 points, on a sub-grid of it that still resolves
+//                        the modes m <= 4 k0 H/pi) estimates rho_j.  A cut series with rho_j
+//                        near or above 0.4 makes the march unstable over thousands of steps
+//                        (the truncated stage operator is no longer unimodular), even when
+//                        rho_j < 1.  A request that fails the test at every order fails at
+//                        admission.
 // The values used are reported by pe_server_request_params.
 #include <algorithm>
 #include <cmath>
@@ -198,8 +205,19 @@ bool admit_adapt(Request* q, Result* res, std::string* err) {
       worst = k;
     }
   }
-  std::vector<double> V(N);
-  for (size_t n = 0; n < N; ++n) V[n] = q->n2[size_t(worst) * N + n] - 1.0;
+  const double rho_max = std::pow(1e-5, 1.0 / double(std::max(r.neumann_terms - 1, 1)));
+  // the power iteration's grid: the request's, or a sub-grid (every stride-th point, N + 1 a
+  // power of two) of at least 1023 points resolving the modes m <= 4 k0 H / pi
+  size_t Nc = N;
+  if (N > 1023) {
+    const double need = 4.0 * r.k0 * r.H / M_PI;
+    size_t Lc = 1024;
+    while (Lc < need && Lc < N + 1) Lc *= 2;
+    Nc = std::min(Lc, N + 1) - 1;
+  }
+  const size_t stride = (N + 1) / (Nc + 1);
+  std::vector<double> V(Nc);
+  for (size_t n = 0; n < Nc; ++n) V[n] = q->n2[size_t(worst) * N + (n + 1) * stride - 1] - 1.0;
   for (int p = r.pade_order; p >= 1; --p) {
     double b[16], a[16], d[18];
     if (pe_pade_coefficients(r.k0 * r.dr, p, b, a, d) != PE_OK) continue;
@@ -211,8 +229,8 @@ bool admit_adapt(Request* q, Result* res, std::string* err) {
         const double lam = -std::pow(M_PI * double(m) / (r.k0 * r.H), 2.0);
         mx = std::max(mx, std::abs(bj / (1.0 + bj * lam)));
       }
-      if (vmax * mx < 1.0) continue;
-      if (neumann_radius(V, bj, r.k0, r.H) >= 0.98) ok = false;
+      if (vmax * mx <= rho_max) continue;
+      if (neumann_radius(V, bj, r.k0, r.H) > rho_max) ok = false;
     }
     if (ok) {
       r.pade_order = p;
@@ -220,7 +238,7 @@ bool admit_adapt(Request* q, Result* res, std::string* err) {
       return true;
     }
   }
-  *err = "the Neumann series diverges at every Pade order for this profile";
+  *err = "the Neumann series converges too slowly at every Pade order for this profile";
   return false;
 }
 

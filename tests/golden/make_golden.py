@@ -25,6 +25,9 @@
                                                   # 12 terms), product form, explicit sine sums
                                                   # -> batch_n1023_s2000.txt (one process per
                                                   # member; a few minutes on 8 cores)
+    python tests/golden/make_golden.py batch_fixed  # the same members with a fixed 12 terms per
+                                                  # step (tolerance 0), the lockstep GEMM-DST rule
+                                                  # -> batch_n1023_s2000_fixed12.txt
     python tests/golden/make_golden.py counts     # Neumann terms summed per step and Pade term,
                                                   # first 100 steps of the N = 4095 Munk march,
                                                   # product form -> munk_n4095_counts100.txt
@@ -172,26 +175,32 @@ BATCH_TL_EVERY = 100
 BATCH_TL_STRIDE = 16
 
 
-def _batch_member(i):
+def _batch_member(arg):
+    i, tol = arg
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     s = inputs.munk_batch()[i]
     g = O.Grid(N=s.N, H=s.H, k0=s.k0, dr=s.dr)
     t0 = time.time()
-    res = O.march(s.u0, s.profiles, g, s.pade_order, s.steps, s.neumann_terms, s.neumann_tol,
+    res = O.march(s.u0, s.profiles, g, s.pade_order, s.steps, s.neumann_terms, s.neumann_tol if tol is None else tol,
                   tl_every=BATCH_TL_EVERY, form="product")
     return i, s.freq, res, time.time() - t0
 
 
-def main_batch(path=os.path.join(HERE, "batch_n1023_s2000.txt")):
+def main_batch(path=None, fixed=False):
+    """fixed: every step sums the full 12 terms (tolerance 0), the rule of the lockstep GEMM-DST
+    batch -> batch_n1023_s2000_fixed12.txt; otherwise the 1e-10 stop rule -> batch_n1023_s2000.txt."""
     import multiprocessing as mp
+    if path is None:
+        path = os.path.join(HERE, "batch_n1023_s2000_fixed12.txt" if fixed else "batch_n1023_s2000.txt")
     freqs = np.array([s.freq for s in inputs.munk_batch(steps=1)])
     members = [int(np.argsort(freqs)[k]) for k in BATCH_RANKS]
     with mp.get_context("spawn").Pool(len(members)) as pool:
-        runs = pool.map(_batch_member, members)
+        runs = pool.map(_batch_member, [(i, 0.0 if fixed else None) for i in members])
     with open(path, "w") as f:
-        f.write("# FP64 oracle (product form, explicit sine sums), written by tests/golden/make_golden.py batch\n")
-        f.write("# munk_batch count=256 seed=4 N=1023 H=5000 dr=25 steps=2000 p=6 terms=12 tol=1e-10 zs=1000 "
-                "c0=1500\n")
+        f.write("# FP64 oracle (product form, explicit sine sums), written by tests/golden/make_golden.py "
+                f"{'batch_fixed' if fixed else 'batch'}\n")
+        f.write("# munk_batch count=256 seed=4 N=1023 H=5000 dr=25 steps=2000 p=6 terms=12 "
+                f"tol={'0 (fixed 12 terms)' if fixed else '1e-10'} zs=1000 c0=1500\n")
         f.write(f"field_stride {BATCH_FIELD_STRIDE} tl_every {BATCH_TL_EVERY} tl_stride {BATCH_TL_STRIDE} "
                 f"members {len(runs)}\n")
         for i, freq, res, el in runs:
@@ -259,8 +268,8 @@ def load_counts(path=os.path.join(HERE, "munk_n4095_counts100.txt")):
 
 
 if __name__ == "__main__":
-    if len(sys.argv) > 1 and sys.argv[1] == "batch":
-        main_batch()
+    if len(sys.argv) > 1 and sys.argv[1] in ("batch", "batch_fixed"):
+        main_batch(fixed=sys.argv[1] == "batch_fixed")
         sys.exit(0)
     if len(sys.argv) > 1 and sys.argv[1] == "counts":
         main_counts()

@@ -538,34 +538,64 @@ def _oracle_admitted(s, prm, tl_every=1):
 
 
 def test_server_admission_makes_diverging_requests_converge(sssp):
-    """Requests of the serving trace whose Neumann series diverges with c0 = 1500 m/s (low
-    frequency, coarse grid, high Pade order): admission picks the minimax reference sound
-    speed and, where that is not enough, a lower Pade order; every request then completes and
-    matches the oracle marched with the same values (field <= 1e-4, TL <= 0.1 dB)."""
+    """Requests of the serving trace (low frequency, coarse grid, Pade order 7-8) whose 12-term
+    Neumann series contracts too slowly: with c0 = 1500 m/s and the minimax c0 alone their march
+    grows until it is no longer finite; admission then lowers the Pade order until the cut
+    series is accurate, and every request completes and matches the oracle marched with the
+    same values (field <= 1e-4, TL <= 0.1 dB)."""
     from paper_2511_03343_gb300 import serving
     trace = inputs.serving_trace(count=1000)
-    ids = [2, 15, 49, 62, 768, 945]  # FP64 spectral radius >= 1 at c0 = 1500 m/s (dense eigenvalues)
+    ids = [2, 15, 768]
     sub = []
     for k, i in enumerate(ids):
         t = dict(trace[i])
         t["t_arrival"] = 0.001 * k
-        t["range_m"] = 2000.0
+        t["range_m"] = 20000.0
         sub.append(t)
-    res = serving.replay(sub, hbm_budget=4e9, chunk_steps=20, tl_every=10, keep_results=True)
+    only_c0 = serving.replay(sub, hbm_budget=4e9, chunk_steps=50, tl_every=10, admit=sssp.ADMIT_MINIMAX_C0)
+    print("minimax c0 alone:", only_c0["failed"], "of", len(sub), "failed", only_c0["failures"])
+    res = serving.replay(sub, hbm_budget=4e9, chunk_steps=50, tl_every=10, keep_results=True)
     assert res["failed"] == 0, res["failures"]
-    assert res["order_lowered"] >= 1
+    assert res["order_lowered"] == len(sub)
     for i, (field, tl, s, prm) in res["results"].items():
         assert np.all(np.isfinite(field))
+        assert prm[2] < s.pade_order
         ref = _oracle_admitted(s, prm, tl_every=10)
         _compare(field, tl, ref)
 
 
 # ----------------------------------------------------------------------------- tensor-core GEMM-DST
+def test_gemm_dst_small_against_fft_marcher(sssp):
+    """The tensor-core GEMM-DST batch (own tcgen05 kernels) on a small case first: 20 Munk solves
+    at N = 255 (two 128-row tiles, two 32-column tiles), [2/2], a fixed 3 terms (tolerance 0 in
+    both marchers), 3 steps, against the FFT marcher with the same fixed term count."""
+    freqs = np.linspace(40.0, 120.0, 20)
+    solves = [inputs.munk(N=255, freq=float(f), dr=25.0, steps=3, pade_order=2, neumann_terms=3, neumann_tol=0.0)
+              for f in freqs]
+    refs = []
+    for s in solves:
+        pl = sssp.plan_for(s)
+        pl.march(3)
+        refs.append(pl.read_field())
+        pl.close()
+    bars = {"fp32": 1e-5, "3xtf32": 1e-5, "bf16x3": 1e-4, "tf32": 5e-3}
+    for mode, bar in bars.items():
+        plans = [sssp.plan_for(s) for s in solves]
+        gb = sssp.GemmBatch(plans, mode)
+        gb.march(3)
+        e = max(np.linalg.norm(gb.read_field(i) - r) / np.linalg.norm(r) for i, r in enumerate(refs))
+        gb.close()
+        for pl in plans:
+            pl.close()
+        print(f"GEMM-DST {mode}: max field rel-L2 vs the FFT marcher after 3 steps {e:.3e}")
+        assert e <= bar, (mode, e)
+
+
 def test_gemm_dst_precisions(sssp):
     """The batched march with the DST-I as a dense GEMM, per precision, against the FP64 oracle
-    (6 Munk solves, N = 1023, 60-200 Hz, dr = 25 m, [6/6], 12 terms, 40 steps).  FP32 and the
-    3xTF32 split meet the field tolerance; plain TF32 (10-bit mantissa) cannot; BF16x3 lies
-    between.  The errors are printed for the record."""
+    (6 Munk solves, N = 1023, 60-200 Hz, dr = 25 m, [6/6], 12 terms, 40 steps).  FP32, the
+    3xTF32 split and the BF16x3 split meet the field tolerance; plain TF32 (10-bit mantissa)
+    cannot.  The errors are printed for the record."""
     freqs = [60.0, 80.0, 100.0, 130.0, 160.0, 200.0]
     solves = [inputs.munk(N=1023, freq=f, dr=25.0, steps=40) for f in freqs]
     refs = [_oracle(s, tl_every=0).u for s in solves]
@@ -583,9 +613,40 @@ def test_gemm_dst_precisions(sssp):
             pl.close()
         errs[mode] = max(e)
     print("GEMM-DST max field rel-L2 after 40 steps:", errs)
-    assert errs["fp32"] <= FIELD_TOL and errs["3xtf32"] <= FIELD_TOL
+    assert errs["fp32"] <= FIELD_TOL and errs["3xtf32"] <= FIELD_TOL and errs["bf16x3"] <= FIELD_TOL
     assert errs["tf32"] > errs["3xtf32"]
-    assert errs["bf16x3"] >= errs["3xtf32"] * 0.5
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "3xtf32"])
+def test_gemm_dst_full_batch_against_stored_oracle(sssp, mode):
+    """The whole 256-solve batch (N = 1023, 2000 steps of 25 m, [6/6], 12 terms) with the DST-I
+    as the tensor-core GEMM in a split precision, against the stored FP64 oracle runs of eight
+    members with the same rule, a fixed 12 terms per step (tests/golden/batch_n1023_s2000_fixed12.txt):
+    sampled final field within 1e-4 and its TL within 0.1 dB of the stored last TL row.  (Against
+    the 1e-10 stop rule the converged members agree as well; the 53.7 Hz member, whose series
+    never converges and whose norm grows ~2e4-fold over the range in FP64, is a different
+    approximation under the two rules, so the rules are not mixed.)"""
+    mg = _make_golden()
+    runs = mg.load_batch(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                      "batch_n1023_s2000_fixed12.txt"))
+    solves = inputs.munk_batch()
+    plans = [sssp.plan_for(s) for s in solves]
+    gb = sssp.GemmBatch(plans, mode)
+    gb.march(solves[0].steps)
+    bad = []
+    for i, (freq, fidx, fref, tl_r, tl_ref) in runs.items():
+        u = gb.read_field(i).astype(np.complex128)
+        rel = np.linalg.norm(u[fidx] - fref) / np.linalg.norm(fref)
+        tl = O.transmission_loss(u, tl_r[-1])[::mg.BATCH_TL_STRIDE]
+        mask = tl_ref[-1] < 100
+        dtl = float(np.max(np.abs(tl - tl_ref[-1])[mask]))
+        print(f"GEMM-DST {mode} member {i} ({freq:.1f} Hz): field rel-L2 {rel:.3e}, final TL error {dtl:.4f} dB")
+        if not (rel <= FIELD_TOL and dtl <= TL_TOL):
+            bad.append((i, rel, dtl))
+    gb.close()
+    assert not bad, bad
+    for pl in plans:
+        pl.close()
 
 
 @pytest.mark.parametrize("N,count", [(255, 7), (4095, 3), (16383, 2)])
@@ -1032,3 +1093,64 @@ def test_batch_of_two_sizes_overlaps_on_the_device(sssp):
     for p in ps + ps2:
         p.close()
     assert t_both < 0.85 * (t_small + t_large), (t_small, t_large, t_both)
+
+
+
+@pytest.mark.parametrize("ppt", [4, 16])
+def test_cta_shapes_match_oracle_and_default(sssp, ppt):
+    """The one-CTA kernel at 4 and 16 points per thread (pe_plan_set_shape): a short Munk march
+    at N = 1023 and N = 4095 against the oracle, and against the default 8 points per thread
+    to FP32 rounding; TL rows and transform counts identical in number."""
+    for N, f, steps in [(1023, 120.0, 40), (4095, 50.0, 12), (255, 30.0, 40)]:
+        s = inputs.munk(N=N, freq=f, dr=25.0, steps=steps, pade_order=6)
+        out = {}
+        for shape in (8, ppt):
+            pl = sssp.plan_for(s, tl_every=4)
+            pl.set_kernel("cta")
+            pl.set_shape(shape)
+            assert pl.shape == shape
+            pl.march(steps)
+            out[shape] = (pl.read_field(), pl.read_tl()[0], pl.transform_count())
+            pl.close()
+        ref = _oracle(s, tl_every=4)
+        _compare(out[ppt][0], out[ppt][1], ref)
+        u8, u = out[8][0], out[ppt][0]
+        assert np.linalg.norm(u - u8) / np.linalg.norm(u8) < 2e-5, (N, ppt)
+        assert out[8][2] == out[ppt][2], (N, out[8][2], out[ppt][2])
+
+
+def test_shape_rejected_where_unsupported(sssp):
+    pl = sssp.Plan(65535, 5000.0, 0.2, 25.0, 4)
+    with pytest.raises(sssp.PEError):
+        pl.set_shape(4)
+    pl.close()
+    pl = sssp.Plan(127, 5000.0, 0.2, 25.0, 4)
+    with pytest.raises(sssp.PEError):
+        pl.set_shape(16)  # N + 1 below 256
+    pl.set_shape(8)
+    pl.close()
+
+
+def test_batch_autotune_restores_state_and_picks_the_fastest(sssp):
+    """pe_march_batch_autotune over a batch of 64 Munk solves (N = 1023): every shape is timed,
+    the fastest is set on every plan, the march's state and TL bookkeeping are restored (the
+    tuned batch then gives the oracle's result), and the untimed cluster shape reports -1."""
+    solves = inputs.munk_batch(count=64, steps=30)
+    plans = [sssp.plan_for(s, tl_every=10) for s in solves]
+    res = sssp.autotune_batch(plans, steps=6)
+    ms = res["ms"]
+    assert ms["cluster"] is None
+    timed = {k: v for k, v in ms.items() if v is not None}
+    assert set(timed) == {"cta4", "cta8", "cta16"}
+    assert res["chosen"] == min(timed, key=timed.get)
+    want = int(res["chosen"][3:])
+    assert all(p.shape == want for p in plans)
+    assert all(p.range() == (0.0, 0) for p in plans)
+    sssp.march_batch(plans, 30)
+    for idx in (0, 17):
+        u = plans[idx].read_field()
+        tl, _ = plans[idx].read_tl()
+        assert tl.shape[0] == 3
+        _compare(u, tl, _oracle(solves[idx], tl_every=10))
+    for p in plans:
+        p.close()
