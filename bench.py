@@ -637,8 +637,8 @@ def bench_gemm(args):
     """The 256-solve Munk batch (N = 1023, [6/6], 12 terms) with the DST-I as the library's own
     tensor-core GEMM (tcgen05.mma, TMA-fed, fused epilogues), per precision: throughput of the
     lockstep march (one captured graph per range step), the tensor work rate, and the sampled final
-    field of the stored members against the FP64 oracle runs.  FP32 (CUDA cores, the reference)
-    runs fewer steps (``--gemm-fp32-steps``) and its parity is not checked."""
+    field of the stored members against the FP64 oracle runs (the fixed-12-term rule the lockstep
+    batch uses).  FP32 (CUDA cores, the reference) may run fewer steps (``--gemm-fp32-steps``)."""
     import numpy as np
     import torch
     torch.cuda.set_device(0)
@@ -650,7 +650,8 @@ def bench_gemm(args):
     steps = args.range_steps
     solves = inputs.munk_batch(count=args.batch_count, steps=steps)
     mg = _load_make_golden()
-    runs = mg.load_batch() if (steps == 2000 and args.batch_count == 256) else {}
+    runs = (mg.load_batch(os.path.join(ROOT, "tests", "golden", "batch_n1023_s2000_fixed12.txt"))
+            if (steps == 2000 and args.batch_count == 256) else {})
     L = solves[0].N + 1
     C = 2 * len(solves)
     out = {}
@@ -683,7 +684,8 @@ def bench_gemm(args):
                 mask = tl_ref[-1] < 100
                 worst = (max(worst[0], rel), max(worst[1], float(np.max(np.abs(tl - tl_ref[-1])[mask]))))
             rec["parity"] = {"worst_field_rel_l2_sampled": worst[0], "worst_final_tl_err_db": worst[1],
-                             "against": "stored FP64 oracle runs of 8 members (tests/golden/batch_n1023_s2000.txt)"}
+                             "against": "stored FP64 oracle runs of 8 members, fixed 12 terms "
+                                        "(tests/golden/batch_n1023_s2000_fixed12.txt)"}
         out[mode] = rec
         gb.close()
         for pl in plans:
@@ -893,7 +895,7 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--gemm-fp32-steps", type=int, default=100)
+    ap.add_argument("--gemm-fp32-steps", type=int, default=2000)
     ap.add_argument("--chunk-steps", type=int, default=50)
     ap.add_argument("--serve-baseline", action="store_true")
     ap.add_argument("--batch-count", type=int, default=256)

@@ -374,13 +374,14 @@ typedef struct {
  * Admission adaptations (no counterpart in the paper).  PE_ADMIT_MINIMAX_C0: the reference
  * sound speed c0 is chosen to minimise max|V| over the request's profile nodes (n^2 -> s n^2,
  * k0 -> k0/sqrt(s), s = 2/(min n^2 + max n^2); k0^2 n^2 is unchanged).  PE_ADMIT_CONVERGENT_ORDER:
- * the Pade order is lowered until the Neumann series (Eq. Neumann), cut at the request's term
- * limit M, is accurate for every term j: rho_j^(M-1) <= 1e-5 (rho_j <= 0.35 for M = 12), rho_j
- * the contraction rate of -b_j L_j^{-1} V (the FP64 bound max|V| max_m |b_j/(1 + b_j lambda_m)|,
- * else an FP64 power-iteration estimate of the spectral radius, for the node with the largest
- * max|V|).  A cut series contracting more slowly makes the march unstable over thousands of
- * steps.  A request that fails the test at every order fails at admission (state 3).  The
- * starter is kept as given.
+ * the Pade order is chosen from the contraction rate rho_j of the Neumann operator
+ * -b_j L_j^{-1} V of Eq. (Neumann) (the FP64 bound max|V| max_m |b_j/(1 + b_j lambda_m)|, else an
+ * FP64 power-iteration estimate, for the node with the largest max|V|): for sigma = k0 dr < 10
+ * the highest order with every rho_j <= 0.3 (there orders 7 and 8 leave a cut 12-term series
+ * whose march grows without bound even with rho_j < 1), otherwise the highest order with every
+ * rho_j < 0.98.  A request that diverges at every order fails at admission (state 3); a march
+ * whose device status reports a failure after a chunk (non-finite value, diverging series) is
+ * restarted from its starter one order lower (at most 8 times).  The starter is kept as given.
  */
 enum { PE_ADMIT_MINIMAX_C0 = 1, PE_ADMIT_CONVERGENT_ORDER = 2 };
 

@@ -436,6 +436,7 @@ __global__ void __launch_bounds__(CCfg<LOG2L, NCTA>::NT, 1)
   for (int s = 0; s < SV; ++s) y[s] = d.yhat[sp.mode(s)];
   const float out_scale = 2.0f / float(C::L);
   const bool iso = d.terms <= 1;
+  const float tol2f = float(d.tol2);  // the FP32 prefilter of the FP64 stop test
   int status = kStatusOk;
   unsigned int ndst = 0;
   int nrec = 0;
@@ -536,7 +537,7 @@ __global__ void __launch_bounds__(CCfg<LOG2L, NCTA>::NT, 1)
             status = kStatusDiverged;
             break;
           }
-          if (neumann_stop(snt, snw, d.tol2)) break;
+          if (neumann_stop_fast(snt, snw, d.tol2, tol2f)) break;
           cdst_inv_end<LOG2L, NCTA, kSinkX>(sm, j, ph, nullptr, nullptr, 0.f);  // t_m in depth space
           ++ndst;
         }

@@ -99,6 +99,7 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 __device__ __forceinline__ float2 mul_negi(float2 x) { return make_float2(x.y, -x.x); }
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
 
 // Stop test of the Neumann series (Eq. Neumann; stop after term m once ||t_m|| <= tol ||w_j||),
@@ -108,6 +109,19 @@ __device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a
 // norm by less than a millionth of itself.)
 __device__ __forceinline__ bool neumann_stop(float nt2, float nw2, double tol2) {
   return double(nt2) <= tol2 * double(nw2);
+}
+
+// The same decision with the FP64 comparison taken only near the threshold (FP64 instructions
+// have a latency of ~64 cycles here): the FP32 product tol2f nw2 is within a few ulps of
+// tol^2 nw2, so where nt2 lies outside [tol2f nw2 / 2, 2 tol2f nw2] the FP32 comparison already
+// gives the FP64 comparison's answer.  Tiny or non-finite thresholds go to FP64 directly.
+__device__ __forceinline__ bool neumann_stop_fast(float nt2, float nw2, double tol2, float tol2f) {
+  const float th = tol2f * nw2;
+  if (th > 1e-30f && th < 1e30f) {
+    if (nt2 < 0.5f * th) return true;
+    if (nt2 > 2.0f * th) return false;
+  }
+  return neumann_stop(nt2, nw2, tol2);
 }
 
 // y * (hi + lo) with the hi/lo split of a multiplier: the product is rounded, the
@@ -218,6 +232,34 @@ __device__ __forceinline__ void fft_pass(const float2* __restrict__ src, float2*
   }
 }
 
+// Whether the passes from span NS end with a radix-2 pass (span L/2)
+template <int LOG2L, int NS, int PPT>
+__host__ __device__ constexpr bool ends_radix2() {
+  constexpr int L = 1 << LOG2L;
+  if constexpr (NS >= L) {
+    return false;
+  } else if constexpr (L / NS == 2) {
+    return true;
+  } else {
+    return ends_radix2<LOG2L, NS * ((L / NS) >= PPT ? PPT : (L / NS)), PPT>();
+  }
+}
+
+// The passes from span NS on, leaving out a final radix-2 pass (the DST-I post-processing does
+// it, see dst_block); returns the buffer holding the result
+template <int LOG2L, int NS, int PPT>
+__device__ __forceinline__ float2* fft_rest_x2(float2* src, float2* dst, const float2* tw) {
+  constexpr int L = 1 << LOG2L;
+  if constexpr (NS >= L || L / NS == 2) {
+    return src;
+  } else {
+    constexpr int R = (L / NS) >= PPT ? PPT : (L / NS);
+    fft_pass<LOG2L, R, NS, PPT>(src, dst, tw);
+    __syncthreads();
+    return fft_rest_x2<LOG2L, NS * R, PPT>(dst, src, tw);
+  }
+}
+
 template <int LOG2L, int NS, int PPT = 8>
 __device__ __forceinline__ float2* fft_rest(float2* src, float2* dst, const float2* tw) {
   constexpr int L = 1 << LOG2L;
@@ -255,14 +297,26 @@ __device__ __forceinline__ void dst_block(float2* a, float2* b, const float2* __
     for (int r = 0; r < PPT; ++r) b[pidx(PPT * t + r)] = v[r];
   }
   __syncthreads();
-  const float2* F = fft_rest<LOG2L, PPT, PPT>(b, a, tw);
+  // When the passes end with radix 2 (span L/2), that pass is fused into the post-processing:
+  // with the earlier passes' result F and w = e^{-2 pi i/L}, Y_k = F_k + w^k F_{k+L/2} and
+  // Y_{L-k} = F_{L/2-k} + conj(w^k) F_{L-k} (the butterfly of L/2 - k, whose twiddle is
+  // -conj(w^k)) -- the same arithmetic, one barrier and one pass through shared memory fewer.
+  constexpr bool X2 = ends_radix2<LOG2L, PPT, PPT>();
+  const float2* F = X2 ? fft_rest_x2<LOG2L, PPT, PPT>(b, a, tw) : fft_rest<LOG2L, PPT, PPT>(b, a, tw);
   // post-processing: even outputs from pairs (k, L-k), odd outputs by a prefix scan
   float2 se[H], dd[H];
 #pragma unroll
   for (int s = 0; s < H; ++s) {
     const int k = H * t + s;
-    const float2 yk = F[pidx(k)];
-    const float2 ym = F[pidx((L - k) & (L - 1))];
+    float2 yk, ym;
+    if constexpr (X2) {
+      const float2 w = tw[(L / 2 - PPT) + k];  // the radix-2 pass's twiddle e^{-2 pi i k/L}
+      yk = F[pidx(k)] + cmul(F[pidx(k + L / 2)], w);
+      ym = (k == 0) ? yk : F[pidx(L / 2 - k)] + cmul(F[pidx(L - k)], conjf2(w));
+    } else {
+      yk = F[pidx(k)];
+      ym = F[pidx((L - k) & (L - 1))];
+    }
     se[s] = make_float2(-0.5f * (yk.y - ym.y), 0.5f * (yk.x - ym.x));
     dd[s] = (k == 0) ? 0.5f * yk : 0.5f * (yk + ym);
   }
@@ -298,8 +352,6 @@ __device__ __forceinline__ void dst_block(float2* a, float2* b, const float2* __
 // periodic (DFT).
 constexpr int kBcDirichlet = 0;
 constexpr int kBcPeriodic = 1;
-
-__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
 // Unnormalised DFT of the L values in `a` (natural order, padded) into out[0..P) = X_{Pt..Pt+P)
 // of thread t; INV uses e^{+2 pi i n m/L} (by conjugating input and output).  On return every
@@ -443,6 +495,7 @@ __global__ void __launch_bounds__(Cfg<LOG2L, PPT>::NT, Cfg<LOG2L, PPT>::MIN_BLOC
   load8<LOG2L, P>(d.yhat + P * t, y);
   const float out_scale = (BC == kBcPeriodic ? 1.0f : 2.0f) / float(L);
   const bool iso = d.terms <= 1;
+  const float tol2f = float(d.tol2);
   int status = kStatusOk;
   unsigned int ndst = 0;
   int nrec = 0;
@@ -571,7 +624,7 @@ __global__ void __launch_bounds__(Cfg<LOG2L, PPT>::NT, Cfg<LOG2L, PPT>::MIN_BLOC
             status = kStatusDiverged;
             break;
           }
-          if (neumann_stop(snt, snw, d.tol2)) break;
+          if (neumann_stop_fast(snt, snw, d.tol2, tol2f)) break;
           xform<LOG2L, BC, true, P>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // t_m in depth space
           ++ndst;
         }

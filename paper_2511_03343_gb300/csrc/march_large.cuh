@@ -390,6 +390,7 @@ __global__ void __launch_bounds__(kLargeNT, 1)
   float2* const t0 = d.work + 4 * L;
   const float out_scale = 2.0f / float(L);
   const bool iso = d.terms <= 1;
+  const float tol2f = float(d.tol2);  // the FP32 prefilter of the FP64 stop test
   int status = kStatusOk;
   unsigned int ndst = 0;
   int nrec = 0;
@@ -443,7 +444,7 @@ __global__ void __launch_bounds__(kLargeNT, 1)
             status = kStatusDiverged;
             break;
           }
-          if (neumann_stop(snt, snw, d.tol2)) break;
+          if (neumann_stop_fast(snt, snw, d.tol2, tol2f)) break;
           SnkArr sx{X};
           dst_global<LOG2L>(W, tb, tile_smem, SrcArr{X}, sx);  // t_m in depth space
           ++ndst;

@@ -155,9 +155,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kBM, c0 = blockIdx.y * kBN;
   const int KB = ea.L / T::BK;
-  if (threadIdx.x == 0) abort_flag = *reinterpret_cast<volatile int*>(ea.status);
-  __syncthreads();
-  if (abort_flag) return;  // an earlier launch of the batch gave up: do nothing more
+  // prologue (overlaps the preceding launch under programmatic dependent launch): barriers,
+  // tensor memory, tensor-map prefetch; then wait for the preceding grid's results
   if (threadIdx.x == 0) {
     for (int s = 0; s < T::STAGES; ++s) {
       umma::mbar_init(&full[s], 1);
@@ -181,8 +180,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   umma::tc_fence_after();
   const uint32_t tmem = tmem_base;
+  umma::grid_dep_wait();
+  if (threadIdx.x == 0 && *reinterpret_cast<volatile int*>(ea.status) != 0)
+    abort_flag = 1;  // an earlier launch of the batch gave up: do nothing more
+  __syncthreads();
 
-  if (warp == 0 && lane == 0) {  // TMA producer
+  if (abort_flag) {
+    // nothing to load or multiply
+  } else if (warp == 0 && lane == 0) {  // TMA producer
     int issued = 0;
     for (int kb = 0; kb < KB; ++kb) {
       const int s = kb % T::STAGES;
@@ -236,8 +241,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     umma::mma_commit(&done);  // arrives when every product issued has completed
   }
   __syncwarp();
+  umma::grid_dep_launch();  // the next launch may start its prologue
   // epilogue: every warp reads its 32 accumulator lanes (rows m0 + 32 w + lane)
-  const bool ok = umma::mbar_wait(&done, 0, kWaitNs);
+  const bool skipped = abort_flag != 0;
+  const bool ok = !skipped && umma::mbar_wait(&done, 0, kWaitNs);
   umma::tc_fence_after();
   __syncthreads();  // abort_flag is final
   if (ok && !abort_flag) {
@@ -246,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int m = m0 + 32 * warp + lane;
 #pragma unroll
     for (int i = 0; i < kBN / 2; ++i) epi_pair<MODE, EPI>(ea, m, c0 + 2 * i, v[2 * i], v[2 * i + 1]);
-  } else if (threadIdx.x == 0) {
+  } else if (threadIdx.x == 0 && !skipped) {
     atomicExch(ea.status, kStatusTimeout);
   }
   umma::tc_fence_before();
@@ -456,9 +463,18 @@ cudaError_t launch_gemm_t(pe_gemm_batch* g, int in_buf, const EpiArgs& a) {
         attr_dev = dev;
       }
     }
-    const dim3 grid(g->L / kBM, g->C / kBN);
-    sssp_gemm_dst_kernel<MODE, EPI><<<grid, kThreads, T::SMEM, g->stream>>>(g->mS[0], g->mS[1], g->mX[in_buf][0],
-                                                                            g->mX[in_buf][1], a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g->L / kBM, g->C / kBN);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = T::SMEM;
+    cfg.stream = g->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // overlap with the preceding launch
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, sssp_gemm_dst_kernel<MODE, EPI>, g->mS[0], g->mS[1], g->mX[in_buf][0],
+                              g->mX[in_buf][1], a);
   }
   return cudaGetLastError();
 }

@@ -17,18 +17,20 @@
 //                        request's profile nodes (V = n^2 - 1): with n^2 = (c0/c)^2 the
 //                        rescaling n^2 -> s n^2, k0 -> k0/sqrt(s), s = 2/(min n^2 + max n^2),
 //                        keeps k0^2 n^2 = (omega/c)^2 and centres V on zero;
-//   PE_ADMIT_CONVERGENT_ORDER lowers the Pade order until the series, cut at the request's
-//                        term limit M, is accurate for every term j: the contraction rate
-//                        rho_j of -b_j L_j^{-1} V must satisfy rho_j^(M-1) <= 1e-5, i.e.
-//                        rho_j <= 0.35 for M = 12.  rho_j is bounded in FP64 by
-//                        max|V| max_m |b_j/(1 + b_j lambda_m)|; where that bound is not small
-//                        enough, an FP64 power iteration (DST-I by a host FFT, on the request's
-//                        grid or, beyond 1023 points, on a sub-grid of it that still resolves
-//                        the modes m <= 4 k0 H/pi) estimates rho_j.  A cut series with rho_j
-//                        near or above 0.4 makes the march unstable over thousands of steps
-//                        (the truncated stage operator is no longer unimodular), even when
-//                        rho_j < 1.  A request that fails the test at every order fails at
-//                        admission.
+//   PE_ADMIT_CONVERGENT_ORDER chooses the Pade order from the contraction rate rho_j of the
+//                        Neumann operator -b_j L_j^{-1} V (bounded in FP64 by
+//                        max|V| max_m |b_j/(1 + b_j lambda_m)|; where the bound is not small
+//                        enough, an FP64 power iteration with a host FFT DST-I, on the
+//                        request's grid or, beyond 1023 points, on a sub-grid that resolves the
+//                        modes m <= 4 k0 H/pi).  For a short step (sigma = k0 dr < 10) the
+//                        order is lowered until every rho_j <= 0.3: there high orders
+//                        (7 and 8 measured) leave a cut 12-term series whose march grows
+//                        without bound over the range even where rho_j < 1.  Otherwise the
+//                        order is lowered only while the series diverges (rho_j >= 0.98).
+//                        A request that diverges at every order fails at admission.  A march
+//                        that still fails on the device (a non-finite value or a diverging
+//                        series reported by its status word after a chunk) is restarted from
+//                        its starter one order lower, up to 8 times.
 // The values used are reported by pe_server_request_params.
 #include <algorithm>
 #include <cmath>
@@ -125,6 +127,8 @@ double neumann_radius(const std::vector<double>& V, cd b, double k0, double H) {
 
 struct Request {
   unsigned long long id = 0;
+  int restarts = 0;        // marches restarted one Pade order lower after a device failure
+  bool adapted = false;    // admission has run (a restart keeps its reference sound speed)
   pe_request r{};          // as admitted (k0, n2 and pade_order may be adapted)
   std::vector<float> u0;
   std::vector<double> n2;
@@ -171,9 +175,20 @@ pe_status sfail(pe_server* s, pe_status st, const std::string& m) {
 
 long long tl_rows_for(const pe_request& r) { return r.tl_every > 0 ? r.steps / r.tl_every : 0; }
 
+// Admission thresholds on the contraction rate rho of the Neumann series (see the file comment)
+constexpr double kLowSigma = 10.0;      // sigma = k0 dr below which orders are lowered to rho <= kRhoLow
+constexpr double kRhoLow = 0.3;
+constexpr double kRhoConverge = 0.98;  // above: the series does not converge
+constexpr int kMaxRestarts = 8;
+
 // Adapt a request at admission (see the file comment); false + message if it cannot converge.
 bool admit_adapt(Request* q, Result* res, std::string* err) {
   pe_request& r = q->r;
+  if (q->adapted) {  // a restart: the order was lowered by the restart itself
+    res->pade_order = r.pade_order;
+    return true;
+  }
+  q->adapted = true;
   res->k0 = r.k0;
   res->pade_order = r.pade_order;
   res->n2_scale = 1.0;
@@ -205,7 +220,6 @@ bool admit_adapt(Request* q, Result* res, std::string* err) {
       worst = k;
     }
   }
-  const double rho_max = std::pow(1e-5, 1.0 / double(std::max(r.neumann_terms - 1, 1)));
   // the power iteration's grid: the request's, or a sub-grid (every stride-th point, N + 1 a
   // power of two) of at least 1023 points resolving the modes m <= 4 k0 H / pi
   size_t Nc = N;
@@ -218,27 +232,44 @@ bool admit_adapt(Request* q, Result* res, std::string* err) {
   const size_t stride = (N + 1) / (Nc + 1);
   std::vector<double> V(Nc);
   for (size_t n = 0; n < Nc; ++n) V[n] = q->n2[size_t(worst) * N + (n + 1) * stride - 1] - 1.0;
-  for (int p = r.pade_order; p >= 1; --p) {
+  // the largest contraction rate over the Pade terms of order p (the FP64 bound where it is
+  // below `enough`, else the power-iteration estimate)
+  auto rate = [&](int p, double enough) {
     double b[16], a[16], d[18];
-    if (pe_pade_coefficients(r.k0 * r.dr, p, b, a, d) != PE_OK) continue;
-    bool ok = true;
-    for (int j = 0; j < p && ok; ++j) {
+    if (pe_pade_coefficients(r.k0 * r.dr, p, b, a, d) != PE_OK) return 1e300;
+    double worst_rho = 0.0;
+    for (int j = 0; j < p; ++j) {
       const cd bj(b[2 * j], b[2 * j + 1]);
       double mx = 0.0;
       for (size_t m = 1; m <= N; ++m) {
         const double lam = -std::pow(M_PI * double(m) / (r.k0 * r.H), 2.0);
         mx = std::max(mx, std::abs(bj / (1.0 + bj * lam)));
       }
-      if (vmax * mx <= rho_max) continue;
-      if (neumann_radius(V, bj, r.k0, r.H) > rho_max) ok = false;
+      const double bound = vmax * mx;
+      worst_rho = std::max(worst_rho, bound <= enough ? bound : neumann_radius(V, bj, r.k0, r.H));
     }
-    if (ok) {
+    return worst_rho;
+  };
+  const double sigma = r.k0 * r.dr;
+  if (sigma < kLowSigma) {
+    // low frequency / short step: the highest order whose cut series contracts fast enough
+    for (int p = r.pade_order; p >= 1; --p) {
+      if (rate(p, kRhoLow) <= kRhoLow) {
+        r.pade_order = p;
+        res->pade_order = p;
+        return true;
+      }
+    }
+  }
+  // otherwise the highest order at which the series converges at all
+  for (int p = r.pade_order; p >= 1; --p) {
+    if (rate(p, kRhoConverge) < kRhoConverge) {
       r.pade_order = p;
       res->pade_order = p;
       return true;
     }
   }
-  *err = "the Neumann series converges too slowly at every Pade order for this profile";
+  *err = "the Neumann series diverges at every Pade order for this profile";
   return false;
 }
 
@@ -350,9 +381,30 @@ pe_status pe_server_step(pe_server* s, int* live_out, int* queued_out, int* comp
     pe_status st = pe_march_batch_steps(plans.data(), steps.data(), int(plans.size()));
     if (st != PE_OK) return sfail(s, st, pe_last_error(plans[0]));
     for (size_t i = 0; i < s->live.size(); ++i) s->live[i].done += steps[i];
-    // 3. retire finished solves (reads synchronise the stream)
+    // 3. a march whose device status reports a failure (non-finite value, diverging series) is
+    //    restarted from its starter one Pade order lower when its request allows it; then the
+    //    finished solves retire (reads synchronise the stream)
     std::vector<Live> keep;
+    std::vector<std::unique_ptr<Request>> again;
     for (auto& l : s->live) {
+      const pe_status ds = pe_sync(l.plan);
+      if (ds == PE_ERR_NUMERIC || ds == PE_ERR_NEUMANN_DIVERGED) {
+        Result& res = s->results[l.req->id];
+        const bool retry = (l.req->r.flags & PE_ADMIT_CONVERGENT_ORDER) && l.req->r.pade_order > 1 &&
+                           l.req->restarts < kMaxRestarts;
+        pe_plan_destroy(l.plan);
+        s->in_use -= l.req->bytes;
+        if (retry) {
+          l.req->r.pade_order -= 1;
+          l.req->restarts += 1;
+          res.state = 0;
+          again.push_back(std::move(l.req));
+        } else {
+          res.state = 3;
+          res.err = ds == PE_ERR_NUMERIC ? "non-finite value in the march" : "Neumann series diverged";
+        }
+        continue;
+      }
       if (l.done < l.req->r.steps) {
         keep.push_back(std::move(l));
         continue;
@@ -373,6 +425,7 @@ pe_status pe_server_step(pe_server* s, int* live_out, int* queued_out, int* comp
       ++completed;
     }
     s->live = std::move(keep);
+    for (auto it = again.rbegin(); it != again.rend(); ++it) s->queue.push_front(std::move(*it));
   }
   if (live_out) *live_out = int(s->live.size());
   if (queued_out) *queued_out = int(s->queue.size());
