@@ -79,8 +79,12 @@ struct BigCfg {
   static constexpr int TC = 1 << LOG2TC, TR = 1 << LOG2TR;  // columns / rows per tile
   static constexpr int RSP = P + P / 16 + 1, RSQ = Q + Q / 16 + 1;  // padded FFT strides
   static constexpr int BUF = (TC * RSP > TR * RSQ) ? TC * RSP : TR * RSQ;
-  // two tile buffers, then the P- and Q-point twiddle tables (hi + lo)
-  static constexpr size_t SMEM = sizeof(float2) * 2 * size_t(BUF) + sizeof(float4) * (P + Q);
+  // pass A's twiddles w_{2L}^e, e = col k1 < L, as the product of two table entries
+  // w^{(e >> LOG2R) R} w^{e & (R - 1)}; pass B's w_Q^n, n < Q/2
+  static constexpr int LOG2R = (LOG2L + 1) / 2;
+  static constexpr int R = 1 << LOG2R, NT1 = L / R;
+  // two tile buffers, the P- and Q-point twiddle tables, then the three tables above (all hi + lo)
+  static constexpr size_t SMEM = sizeof(float2) * 2 * size_t(BUF) + sizeof(float4) * (P + Q + R + NT1 + Q / 2);
 };
 
 // Tile FFTs use radix-16 Stockham passes (radix min(16, F/NS) at span NS), one butterfly of 16
@@ -143,6 +147,12 @@ __device__ __forceinline__ void load_large_twiddles(float2* sm, const LargeTabs&
   float4* twP = reinterpret_cast<float4*>(sm + 2 * C::BUF);
   for (int i = threadIdx.x; i < C::P; i += kLargeNT) twP[i] = tb.twP[i];
   for (int i = threadIdx.x; i < C::Q; i += kLargeNT) twP[C::P + i] = tb.twQ[i];
+  float4* tlo = twP + C::P + C::Q;  // w^e, e < R
+  float4* thi = tlo + C::R;         // w^{i R}, i < L / R
+  float4* tq = thi + C::NT1;        // w_Q^n = w_{2L}^{P n}, n < Q/2
+  for (int i = threadIdx.x; i < C::R; i += kLargeNT) tlo[i] = tb.tw2L[i];
+  for (int i = threadIdx.x; i < C::NT1; i += kLargeNT) thi[i] = tb.tw2L[i * C::R];
+  for (int i = threadIdx.x; i < C::Q / 2; i += kLargeNT) tq[i] = tb.tw2L[C::P * i];
 }
 
 // Unnormalised DST-I S_k = sum_n x_n sin(pi n k/L), k in [0, L) (S_0 = 0), of the values the
@@ -162,6 +172,9 @@ __device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC
   float2* bufB = sm + C::BUF;
   const float4* twP = reinterpret_cast<const float4*>(sm + 2 * C::BUF);  // copied by load_large_twiddles
   const float4* twQ = twP + P;
+  const float4* tlo = twQ + Q;
+  const float4* thi = tlo + C::R;
+  const float4* tq = thi + C::NT1;
   constexpr int PT = kLargePT, PH = kLargePT / 2;
   float2 pre[PT + 1];
   // pass A: the P-point FFTs of the stored columns n2 in [0, Q/2], twiddled, into W[k1][n2]
@@ -198,8 +211,8 @@ __device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC
       const int idx = t + q * kLargeNT;
       const int k1 = idx >> C::LOG2TC, f = idx & (TC - 1);
       const int col = cb + f;
-      const float4 w = __ldg(tb.tw2L + ((col * k1) & (2 * L - 1)));
-      W[k1 * QS + col] = ffmul(w, F[f * C::RSP + pidx(k1)]);
+      const int e = col * k1;  // < L: col <= Q/2, k1 < P
+      W[k1 * QS + col] = ffmul(thi[e >> C::LOG2R], ffmul(tlo[e & (C::R - 1)], F[f * C::RSP + pidx(k1)]));
     }
     __syncthreads();
   }
@@ -250,7 +263,7 @@ __device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC
       if (n != 0) {  // Y[k][Q - n] from the partner row
         float2 r = make_float2(-pre[PH + q].x, -pre[PH + q].y);
         if (rowof(tile, sl) != 0) {  // times w_Q^{-n} = conj(w_{2L}^{P n})
-          const float4 w = __ldg(tb.tw2L + P * n);
+          const float4 w = tq[n];
           r = ffmul(make_float4(w.x, -w.y, w.z, -w.w), r);
         }
         bufA[sl * C::RSQ + pidx(Q - n)] = r;

@@ -59,12 +59,14 @@ def _depth_summary(depth, points: int = 24) -> Dict:
 
 def replay(trace: List[Dict], hbm_budget: float, chunk_steps: int = 50, tl_every: int = 10,
            range_scale: float = 1.0, max_live: int = 1024, stream=None, keep_results: bool = False,
-           admit: int = sssp.ADMIT_MINIMAX_C0 | sssp.ADMIT_CONVERGENT_ORDER, keep_ids=None):
+           admit: int = sssp.ADMIT_MINIMAX_C0 | sssp.ADMIT_CONVERGENT_ORDER, keep_ids=None,
+           record_params: bool = False):
     """Replay ``trace`` against a fresh server; returns latency / throughput figures.  ``admit``
     are the server's admission adaptations (default: minimax reference sound speed and a Pade
     order at which the Neumann series converges); ``keep_results`` also returns, per request,
     (field, TL rows, solve, (k0, n2 scale, Pade order) it was marched with); ``keep_ids`` keeps
-    those only for the given trace ids."""
+    those only for the given trace ids; ``record_params`` returns every completed request's
+    (k0, n2 scale, Pade order) under "params"."""
     keep = None if keep_ids is None else set(keep_ids)
     keep_results = keep_results or keep is not None
     srv = sssp.Server(int(hbm_budget), max_live=max_live, chunk_steps=chunk_steps, stream=stream)
@@ -76,6 +78,7 @@ def replay(trace: List[Dict], hbm_budget: float, chunk_steps: int = 50, tl_every
     results = {}
     failed = {}
     adapted = {}
+    params = {}
     t0 = time.perf_counter()
     nsteps = 0
     depth = []  # (seconds since start, live solves, queued requests) after every server step
@@ -110,6 +113,8 @@ def replay(trace: List[Dict], hbm_budget: float, chunk_steps: int = 50, tl_every
                 prm = srv.params(rid)
                 if prm[2] != s.pade_order or prm[1] != 1.0:
                     adapted[i] = prm
+                if record_params:
+                    params[i] = prm
                 f, tl = srv.take(rid)
                 if keep_results and (keep is None or trace[i]["id"] in keep):
                     results[i] = (f, tl, s, prm)
@@ -127,4 +132,6 @@ def replay(trace: List[Dict], hbm_budget: float, chunk_steps: int = 50, tl_every
            "queue_depth": _depth_summary(depth)}
     if keep_results:
         out["results"] = results
+    if record_params:
+        out["params"] = params
     return out
