@@ -718,6 +718,51 @@ def bench_gemm(args):
                       "modes": out}), flush=True)
 
 
+def bench_fdssp(args):
+    """The coarse-grid comparison of Section 4.3 (FD-SSP, the 3-point stencil, against SSSP):
+    Munk with H = 4 km, 20 Hz, a smooth beam exp(-((z - 1000 m)/200 m)^2), [4/4], 400 steps of
+    50 m; a reference SSSP march on 2047 points, then SSSP and FD-SSP on 127, 255 and 511 points:
+    the field error at the common depths and the device time of each march."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2511_03343_gb300 import build as B
+    B.build()
+    from paper_2511_03343_gb300 import inputs, sssp
+    stream = torch.cuda.current_stream()
+    H, f, dr, steps, zs = 4000.0, 20.0, 50.0, args.range_steps if args.range_steps != 2000 else 400, 1000.0
+
+    def run(N, op):
+        s = inputs.munk(N=N, H=H, freq=f, dr=dr, steps=steps, pade_order=4, zs=zs)
+        s.u0 = np.exp(-((s.z - zs) / 200.0) ** 2).astype(np.complex128)
+        pl = sssp.plan_for(s, stream=stream, op=op)
+        pl.march(2)
+        pl.set_field(s.u0, 0.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pl.march(steps)
+        e1.record(stream)
+        u = pl.read_field()
+        pl.close()
+        return u, e0.elapsed_time(e1)
+
+    ref, _ = run(2047, "spectral")
+    rows = []
+    for N in (127, 255, 511):
+        stride = 2048 // (N + 1)
+        r = ref[stride - 1::stride]
+        for op in ("spectral", "fd3"):
+            u, ms = run(N, op)
+            rows.append({"N": N, "dz_m": H / (N + 1), "operator": "SSSP" if op == "spectral" else "FD-SSP",
+                         "field_rel_l2_vs_sssp_2047": float(np.linalg.norm(u - r) / np.linalg.norm(r)),
+                         "ms_per_march": ms, "throughput": N * steps / (ms * 1e-3)})
+    print(json.dumps({"metric": "coarse-grid field error (Section 4.3)", "unit": "relative L2",
+                      "config": {"workload": "fdssp_coarse_grid", "H_m": H, "freq_hz": f, "dr_m": dr,
+                                 "range_steps": steps, "pade_order": 4, "reference": "SSSP, N = 2047"},
+                      "rows": rows}), flush=True)
+
+
 def bench_dst(args):
     """Transform-level comparison: the library's batched DST-I kernels against a cuFFT DST-I
     (odd extension to length 2(N+1), complex64 C2C through torch.fft; comparison baseline only).
@@ -899,7 +944,7 @@ def main():
                     help="range steps per march (2000 = the workload; fewer only for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="batch",
-                    choices=["munk", "batch", "eddy", "iso", "serve", "gemm", "dst", "large"])
+                    choices=["munk", "batch", "eddy", "iso", "serve", "gemm", "dst", "large", "fdssp"])
     ap.add_argument("--large-count", type=int, default=64, help="solves in the N = 65535 batch ('large')")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--range-scale", type=float, default=1.0)
@@ -924,6 +969,8 @@ def main():
         bench_gemm(args)
     elif args.workload == "dst":
         bench_dst(args)
+    elif args.workload == "fdssp":
+        bench_fdssp(args)
     elif args.workload == "munk":
         bench_munk(args)
     elif args.workload == "batch":

@@ -250,6 +250,20 @@ pe_status pe_plan_set_kernel(pe_plan* plan, int kernel);
 pe_status pe_plan_get_kernel(const pe_plan* plan, int* kernel);
 
 /*
+ * Depth operator of a plan.  PE_OP_SPECTRAL (default): the paper's DST-I diagonalisation with the
+ * continuous eigenvalues and the Neumann series for V (Section 3).  PE_OP_FD3: FD-SSP, the
+ * comparison of Section 4.3 and the FD-SSP remark of Section 2 — the same product-form Pade
+ * propagator with the standard 3-point finite difference for d_z^2 (our choice of stencil),
+ * X = D2/k0^2 + V, each (1 + b_j X) w_j = y solved directly (tridiagonal; FP64 Thomas factors per
+ * profile node on the host, the sweeps on the GPU); neumann_terms and neumann_tol are not used,
+ * V is always applied and a profile is required.  FD-SSP takes Dirichlet grids with N + 1 in
+ * [8, 4096] and real n^2.  Set the operator before the profile and the field (PE_ERR_STATE
+ * otherwise).  pe_read_field / pe_read_TL / checkpoints work as for spectral plans.
+ */
+enum { PE_OP_SPECTRAL = 0, PE_OP_FD3 = 1 };
+pe_status pe_plan_set_operator(pe_plan* plan, int op);
+
+/*
  * Shape of the one-CTA shared-memory kernel (no counterpart in the paper): points per thread
  * P = 4, 8 (default; 0 means 8) or 16, i.e. L/P threads per solve, each transform a Stockham FFT
  * of radix-P passes.  4 and 16 take Dirichlet grids with N + 1 in [256, 4096]; PE_ERR_ARG

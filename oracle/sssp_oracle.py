@@ -20,6 +20,8 @@ Propagation"), in complex128:
   for the depth-dependent perturbation.
 * Algorithm 1 (SSSP): per range step, w_j for every Pade term, then
   u_n = e^{ihk0}(d0 u_{n-1} + sum_j d_j w_j).
+* Section 4.3's comparison system, FD-SSP: the same Pade product form with the 3-point finite
+  difference for d_z^2 (the stencil is our choice), each (1 + b_j X) w_j = y solved directly.
 
 The Pade coefficients are the definition of the [p/p] approximant (Baker's
 linear system for the denominator, then the numerator) solved with a library
@@ -419,6 +421,63 @@ def march(u0: np.ndarray, profiles, grid: Grid, pade_order: int, steps: int, ter
         r = r0 + n * grid.dr
         want = (n in rec) if rec is not None else (tl_every > 0 and n % tl_every == 0)
         if want:
+            tls.append(transmission_loss(u, r))
+            trs.append(r)
+    tl = np.array(tls) if tls else np.zeros((0, u.shape[0]))
+    return MarchResult(u=u, r=r, tl=tl, tl_ranges=np.array(trs))
+
+
+# ----------------------------------------------------------------------------
+# FD-SSP: the same Pade propagator with the standard 3-point finite difference for d_z^2
+# (the comparison of Section 4.3 and the FD-SSP remark of Section 2; the stencil is our choice)
+# ----------------------------------------------------------------------------
+def fd_second_difference(N: int, H: float) -> np.ndarray:
+    """D2 u_n = (u_{n+1} - 2 u_n + u_{n-1}) / dz^2 on the N interior points of the Dirichlet grid
+    (u_0 = u_{N+1} = 0), dz = H/(N+1), as a dense matrix."""
+    dz = H / (N + 1)
+    D = np.diag(np.full(N, -2.0)) + np.diag(np.ones(N - 1), 1) + np.diag(np.ones(N - 1), -1)
+    return D / dz ** 2
+
+
+def fd_lambdas(N: int, H: float, k0: float) -> np.ndarray:
+    """Eigenvalues of D2/k0^2 on sin(pi m n/(N+1)): -(4/(k0 dz)^2) sin^2(pi m/(2(N+1))), m = 1..N."""
+    dz = H / (N + 1)
+    m = np.arange(1, N + 1, dtype=np.float64)
+    return -(4.0 / (k0 * dz) ** 2) * np.sin(np.pi * m / (2.0 * (N + 1))) ** 2
+
+
+def fd_step(u: np.ndarray, V: np.ndarray, grid: Grid, plan: PadePlan) -> np.ndarray:
+    """One FD-SSP range step in the product form: for each j, (1 + b_j X) w_j = y by a banded
+    (tridiagonal) solve, y -> (a_j/b_j) y + (1 - a_j/b_j) w_j, with X = D2/k0^2 + V; then the
+    factor e^{i k0 dr} P(0)."""
+    from scipy.linalg import solve_banded
+    N = grid.N
+    dz = grid.H / (N + 1)
+    s = 1.0 / (grid.k0 * dz) ** 2
+    y = np.asarray(u, dtype=np.complex128).copy()
+    for aj, bj in zip(plan.a, plan.b):
+        ab = np.zeros((3, N), dtype=np.complex128)
+        ab[0, 1:] = bj * s                       # super-diagonal
+        ab[1, :] = 1.0 + bj * (-2.0 * s + V)     # diagonal
+        ab[2, :-1] = bj * s                      # sub-diagonal
+        w = solve_banded((1, 1), ab, y)
+        y = (aj / bj) * y + (1.0 - aj / bj) * w
+    return np.exp(1j * grid.sigma) * plan.pc[0] * y
+
+
+def fd_march(u0: np.ndarray, profiles, grid: Grid, pade_order: int, steps: int, r0: float = 0.0,
+             tl_every: int = 1, plan: Optional[PadePlan] = None) -> MarchResult:
+    """FD-SSP march of u0 over ``steps`` steps of dr (the node in force at each step's midpoint,
+    TL every ``tl_every`` steps), the finite-difference counterpart of ``march``."""
+    plan = plan or pade_plan(grid.sigma, pade_order)
+    u = np.asarray(u0, dtype=np.complex128).copy()
+    r = r0
+    tls, trs = [], []
+    for n in range(1, steps + 1):
+        V = profile_at(profiles, r + 0.5 * grid.dr) - 1.0
+        u = fd_step(u, V, grid, plan)
+        r = r0 + n * grid.dr
+        if tl_every > 0 and n % tl_every == 0:
             tls.append(transmission_loss(u, r))
             trs.append(r)
     tl = np.array(tls) if tls else np.zeros((0, u.shape[0]))

@@ -64,6 +64,8 @@ struct SolveDesc {
   int terms;             // max Neumann terms incl. m = 0 (<= 1: V ignored)
   int tl_every;          // 0: no TL rows
   int N;
+  const float4* fd;      // FD-SSP plans: nodes x p x L table entries (march_fd.cuh), else null
+  const float4* fdc;     // FD-SSP plans: per stage hi/lo of a_j/b_j and 1 - a_j/b_j
 };
 
 template <int LOG2L, int PPT = 8>

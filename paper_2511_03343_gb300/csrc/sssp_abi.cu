@@ -19,6 +19,7 @@
 #include "cluster_launch.h"
 #include "march_kernel.cuh"
 #include "march_large.cuh"
+#include "fd_launch.h"
 #include "pade_host.h"
 #include "plan_internal.h"
 #include "shape_launch.h"
@@ -423,7 +424,9 @@ cudaError_t tables_for(const pe_plan* p, int ppt, TransformTables* out) {
 // Fill the descriptor for one march of `steps` steps and reserve its TL rows.
 pe_status prepare_desc(pe_plan* p, int steps, SolveDesc* d) {
   if (!p->field_set) return fail(p, PE_ERR_STATE, "pe_march before pe_set_field");
-  if (p->terms > 1 && p->nodes == 0) return fail(p, PE_ERR_STATE, "pe_march with Neumann terms but no profile");
+  if (p->op == PE_OP_FD3 && p->nodes == 0) return fail(p, PE_ERR_STATE, "FD-SSP march needs a profile (n^2)");
+  if (p->op != PE_OP_FD3 && p->terms > 1 && p->nodes == 0)
+    return fail(p, PE_ERR_STATE, "pe_march with Neumann terms but no profile");
   if (steps < 0) return fail(p, PE_ERR_ARG, "steps must be >= 0");
   const long long recs = records_between(p->steps_done, p->steps_done + steps, p->tl_every);
   pe_status st = ensure_tl_cap(p, p->tl_rows + recs);
@@ -455,6 +458,8 @@ pe_status prepare_desc(pe_plan* p, int steps, SolveDesc* d) {
   d->terms = p->terms;
   d->tl_every = p->tl_every;
   d->N = p->N;
+  d->fd = p->dFD;
+  d->fdc = p->dFDc;
   for (long long s = 1; s <= steps; ++s)
     if (p->tl_every > 0 && (p->steps_done + s) % p->tl_every == 0) p->tl_ranges.push_back(p->r_set + double(p->steps_done + s) * p->dr);
   p->tl_rows += recs;
@@ -522,6 +527,8 @@ void pe_plan_destroy(pe_plan* p) {
   cudaFree(p->dNdst);
   cudaFree(p->dTL);
   cudaFree(p->dDesc);
+  cudaFree(p->dFD);
+  cudaFree(p->dFDc);
   delete p;
 }
 
@@ -693,7 +700,12 @@ pe_status pe_set_field(pe_plan* p, const float* u, int on_device, double r) {
     even_extend_kernel<<<(K + 255) / 256, 256, 0, p->stream>>>(p->dStage, K);
     PE_CUDA(p, cudaGetLastError());
   }
-  PE_CUDA(p, launch_dst(p->log2L, p->dStage, p->dYhat, 1.0f, p->tabs, p->stream, p->dWork, p->bc));
+  if (p->op == PE_OP_FD3) {  // FD-SSP marches depth values: index 0 the boundary, 1..N the field
+    PE_CUDA(p, cudaMemsetAsync(p->dYhat, 0, sizeof(float2), p->stream));
+    PE_CUDA(p, cudaMemcpyAsync(p->dYhat + 1, p->dStage, sizeof(float2) * p->N, cudaMemcpyDeviceToDevice, p->stream));
+  } else {
+    PE_CUDA(p, launch_dst(p->log2L, p->dStage, p->dYhat, 1.0f, p->tabs, p->stream, p->dWork, p->bc));
+  }
   // the physical field as given (Dirichlet: index 0 = boundary)
   if (p->off) PE_CUDA(p, cudaMemsetAsync(p->dField, 0, sizeof(float2), p->stream));
   PE_CUDA(p, cudaMemcpyAsync(p->dField + p->off, p->dStage, sizeof(float2) * p->N, cudaMemcpyDeviceToDevice,
@@ -755,6 +767,30 @@ static pe_status append_nodes(pe_plan* p, const double* n2, const double* ranges
     PE_CUDA(p, cudaMemcpyAsync(p->dVi + size_t(p->nodes) * p->L, hosti.data(), sizeof(float) * hosti.size(),
                                cudaMemcpyHostToDevice, p->stream));
   PE_CUDA(p, cudaMemcpyAsync(p->dNodeR + p->nodes, ranges, sizeof(double) * count, cudaMemcpyHostToDevice, p->stream));
+  if (p->op == PE_OP_FD3) {  // FD-SSP: FP64 Thomas factors of every stage for the new nodes
+    if (is_complex) return fail(p, PE_ERR_ARG, "FD-SSP plans take real n^2 only");
+    const size_t per_node = size_t(p->p) * p->L * 3;
+    if (p->nodes + count > p->fd_cap) {
+      const int cap = std::max(p->nodes + count, std::max(4, 2 * p->fd_cap));
+      float4* n = nullptr;
+      PE_CUDA(p, cudaMalloc(&n, sizeof(float4) * per_node * cap));
+      if (p->nodes > 0)
+        PE_CUDA(p, cudaMemcpyAsync(n, p->dFD, sizeof(float4) * per_node * p->nodes, cudaMemcpyDeviceToDevice,
+                                   p->stream));
+      PE_CUDA(p, cudaStreamSynchronize(p->stream));
+      cudaFree(p->dFD);
+      p->dFD = n;
+      p->fd_cap = cap;
+    }
+    std::vector<float4> tab(per_node * count);
+    std::vector<double> Vd(p->N);
+    for (int i = 0; i < count; ++i) {
+      for (int n = 0; n < p->N; ++n) Vd[n] = s[size_t(i) * per + n] - 1.0;
+      sssp_fd::factor_node(Vd.data(), p->N, p->L, p->H, p->k0, p->pade.b, p->p, tab.data() + per_node * i);
+    }
+    PE_CUDA(p, cudaMemcpyAsync(p->dFD + per_node * p->nodes, tab.data(), sizeof(float4) * tab.size(),
+                               cudaMemcpyHostToDevice, p->stream));
+  }
   PE_CUDA(p, cudaStreamSynchronize(p->stream));
   for (int i = 0; i < count; ++i) p->node_r.push_back(ranges[i]);
   p->nodes += count;
@@ -793,7 +829,9 @@ pe_status pe_march(pe_plan* p, int steps) {
   if (steps == 0) return PE_OK;
   PE_CUDA(p, cudaMemcpyAsync(p->dDesc, &d, sizeof(d), cudaMemcpyHostToDevice, p->stream));  // capacity >= 1
   const bool cplx = d.Vi != nullptr;
-  if (use_cluster(p, cplx)) {
+  if (p->op == PE_OP_FD3) {
+    PE_CUDA(p, sssp_fd::launch_march(p->log2L, p->dDesc, 1, p->stream));
+  } else if (use_cluster(p, cplx)) {
     PE_CUDA(p, sssp_cluster::launch_march(p->log2L, p->dDesc, 1, p->stream, cplx, p->device));
   } else {
     const int ppt = (p->log2L <= kMaxSmemLog2) ? shape_of(p) : 8;
@@ -873,13 +911,14 @@ pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
     }
     const bool cplx = d.Vi != nullptr;
     const int group = size_count[std::make_tuple(plans[i]->log2L, plans[i]->complex_profile, plans[i]->bc)];
-    const bool cl = use_cluster(plans[i], cplx, group);
-    const int ppt = (!cl && plans[i]->log2L <= kMaxSmemLog2) ? shape_of(plans[i]) : 8;
+    const bool fd = plans[i]->op == PE_OP_FD3;  // FD-SSP plans: their own kernel (shape -1)
+    const bool cl = !fd && use_cluster(plans[i], cplx, group);
+    const int ppt = fd ? -1 : ((!cl && plans[i]->log2L <= kMaxSmemLog2) ? shape_of(plans[i]) : 8);
     const auto key = std::make_tuple(plans[i]->log2L, cplx, plans[i]->bc, cl, ppt);
     groups[key].push_back(d);
     if (!tabs.count(key)) {
-      TransformTables tb;
-      PE_CUDA(p0, tables_for(plans[i], ppt, &tb));
+      TransformTables tb = plans[i]->tabs;
+      if (!fd) PE_CUDA(p0, tables_for(plans[i], ppt, &tb));
       tabs[key] = tb;
     }
   }
@@ -895,7 +934,9 @@ pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
       p0->desc_cap = bytes;
     }
     PE_CUDA(p0, cudaMemcpyAsync(p0->dDesc, kv.second.data(), bytes, cudaMemcpyHostToDevice, p0->stream));
-    if (std::get<3>(kv.first))
+    if (std::get<4>(kv.first) < 0)
+      PE_CUDA(p0, sssp_fd::launch_march(std::get<0>(kv.first), p0->dDesc, int(kv.second.size()), p0->stream));
+    else if (std::get<3>(kv.first))
       PE_CUDA(p0, sssp_cluster::launch_march(std::get<0>(kv.first), p0->dDesc, int(kv.second.size()), p0->stream,
                                              std::get<1>(kv.first), p0->device));
     else
@@ -924,7 +965,9 @@ pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
     }
     SolveDesc* dd = bl->descs[g];
     PE_CUDA(p0, cudaMemcpyAsync(dd, kv.second.data(), bytes, cudaMemcpyHostToDevice, st));
-    if (std::get<3>(kv.first))
+    if (std::get<4>(kv.first) < 0)
+      PE_CUDA(p0, sssp_fd::launch_march(std::get<0>(kv.first), dd, int(kv.second.size()), st));
+    else if (std::get<3>(kv.first))
       PE_CUDA(p0, sssp_cluster::launch_march(std::get<0>(kv.first), dd, int(kv.second.size()), st,
                                              std::get<1>(kv.first), p0->device));
     else
@@ -1119,6 +1162,28 @@ pe_status pe_plan_autotune(pe_plan* p, int steps, float* ms, int* chosen) {
   if (ncand < 2 && ms) ms[1] = -1.f;
   p->kernel = best_k;
   if (chosen) *chosen = best_k;
+  return PE_OK;
+}
+
+pe_status pe_plan_set_operator(pe_plan* p, int op) {
+  if (!p) return PE_ERR_ARG;
+  if (op != PE_OP_SPECTRAL && op != PE_OP_FD3) return fail(p, PE_ERR_ARG, "op must be PE_OP_SPECTRAL or PE_OP_FD3");
+  if (p->field_set || p->nodes > 0) return fail(p, PE_ERR_STATE, "set the operator before the profile and the field");
+  if (op == PE_OP_FD3) {
+    if (p->user_bc != PE_BC_DIRICHLET || !sssp_fd::supported(p->log2L))
+      return fail(p, PE_ERR_ARG, "FD-SSP plans take Dirichlet grids with N + 1 in [8, 4096]");
+    if (!p->dFDc) {
+      std::vector<float4> c(2 * size_t(p->p));
+      for (int j = 0; j < p->p; ++j) {
+        const cd ab = p->pade.a[j] / p->pade.b[j];
+        split_ff(ab, &c[2 * j]);
+        split_ff(1.0 - ab, &c[2 * j + 1]);
+      }
+      PE_CUDA(p, cudaMalloc(&p->dFDc, sizeof(float4) * c.size()));
+      PE_CUDA(p, cudaMemcpy(p->dFDc, c.data(), sizeof(float4) * c.size(), cudaMemcpyHostToDevice));
+    }
+  }
+  p->op = op;
   return PE_OK;
 }
 

@@ -68,6 +68,7 @@ _SIGNATURES = {
     "pe_plan_get_kernel": (_i, [_vp, ctypes.POINTER(_i)]),
     "pe_plan_autotune": (_i, [_vp, _i, _vp, ctypes.POINTER(_i)]),
     "pe_plan_set_shape": (_i, [_vp, _i]),
+    "pe_plan_set_operator": (_i, [_vp, _i]),
     "pe_plan_get_shape": (_i, [_vp, ctypes.POINTER(_i)]),
     "pe_plan_autotune_shapes": (_i, [_vp, _i, _vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "pe_march_batch_autotune": (_i, [ctypes.POINTER(_vp), _i, _i, _vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
@@ -312,6 +313,11 @@ class Plan:
     def set_kernel(self, kernel: str):
         """'auto', 'cta' (one CTA per solve) or 'cluster' (one solve over a thread-block cluster)."""
         self._c(lib().pe_plan_set_kernel(self._p, KERNELS[kernel]))
+
+    def set_operator(self, op: str):
+        """'spectral' (the paper's DST-I operator, default) or 'fd3' (FD-SSP, 3-point stencil);
+        before the profile and the field."""
+        self._c(lib().pe_plan_set_operator(self._p, {"spectral": 0, "fd3": 1}[op]))
 
     def set_shape(self, points_per_thread: int):
         """Points per thread of the one-CTA kernel: 4, 8 (default) or 16."""
@@ -566,12 +572,15 @@ def march_batch(plans: List[Plan], steps: int):
         raise PEError(st, lib().pe_last_error(plans[0].handle).decode())
 
 
-def plan_for(solve, stream=None, tl_every: int = 0) -> Plan:
-    """Plan, starter field and profile nodes for an ``inputs.Solve`` description."""
+def plan_for(solve, stream=None, tl_every: int = 0, op: str = "spectral") -> Plan:
+    """Plan, starter field and profile nodes for an ``inputs.Solve`` description (``op``: the
+    depth operator, 'spectral' or 'fd3')."""
     pl = Plan(solve.N, solve.H, solve.k0, solve.dr, solve.pade_order, solve.neumann_terms, solve.neumann_tol,
               stream=stream, bc=getattr(solve, "bc", "dirichlet"))
     pl.set_output(tl_every)
-    if solve.neumann_terms > 1:
+    if op != "spectral":
+        pl.set_operator(op)
+    if solve.neumann_terms > 1 or op != "spectral":
         pl.set_profile_nodes(solve.profiles)
     pl.set_field(solve.u0, solve.r0)
     return pl

@@ -644,3 +644,69 @@ def test_fft_dst_backend_at_the_largest_grids_sampled(N):
         O.set_dst_backend("matrix")
     scale = np.sqrt(N) * np.sqrt(np.mean(np.abs(x) ** 2))
     assert np.max(np.abs(got - ref)) <= 1e-11 * scale * math.log2(N + 1)
+
+
+# ----------------------------------------------------------------------------- FD-SSP (Section 4.3)
+def test_fd_second_difference_eigenpairs():
+    """The 3-point D2 is diagonalised by the DST-I: D2 sin(pi m n/(N+1)) equals
+    -(4/dz^2) sin^2(pi m/(2(N+1))) sin(pi m n/(N+1)) (a trigonometric identity), for every m."""
+    N, H = 31, 100.0
+    D = O.fd_second_difference(N, H)
+    k0 = 0.37
+    lam = O.fd_lambdas(N, H, k0)
+    n = np.arange(1, N + 1)
+    for m in (1, 2, 7, 16, 31):
+        v = np.sin(np.pi * m * n / (N + 1))
+        assert np.max(np.abs(D @ v / k0 ** 2 - lam[m - 1] * v)) < 1e-10 * np.max(np.abs(D)) / k0 ** 2
+    # and it tends to the continuous eigenvalue for m << N
+    assert abs(lam[0] / O.lambdas(N, H, k0)[0] - 1) < 1e-3
+
+
+def test_fd_single_mode_isovelocity_closed_form():
+    """In isovelocity a single discrete sine mode marched by FD-SSP is (e^{i sigma} R(lambda_FD))^n
+    times itself, R from mpmath's own Pade at the finite-difference eigenvalue."""
+    N, H, k0, dr, p, steps, m = 63, 100.0, 2 * math.pi * 100 / 1500, 5.0, 4, 30, 5
+    g = O.Grid(N=N, H=H, k0=k0, dr=dr)
+    mpmath, P, Q = _mp_pade(g.sigma, p)
+    lam = float(O.fd_lambdas(N, H, k0)[m - 1])
+    R = complex(mpmath.polyval(P[::-1], lam) / mpmath.polyval(Q[::-1], lam))
+    n = np.arange(1, N + 1)
+    u0 = np.sin(np.pi * m * n / (N + 1)).astype(np.complex128)
+    res = O.fd_march(u0, [(0.0, np.ones(N))], g, p, steps, tl_every=0)
+    expect = (np.exp(1j * g.sigma) * R) ** steps * u0
+    assert np.max(np.abs(res.u - expect)) < 1e-10
+
+
+def test_fd_step_equals_dense_pade_operator():
+    """One FD-SSP step with a Munk profile equals e^{i sigma} prod_j (I + a_j X)(I + b_j X)^{-1}
+    applied by dense LU to X = D2/k0^2 + diag(V) (the banded solve is an independent route)."""
+    N, H = 47, 5000.0
+    z = inputs.depth_grid(N, H)
+    V = inputs.n2_from_c(inputs.munk_c(z)) - 1.0
+    k0 = 2 * math.pi * 30 / 1500
+    g = O.Grid(N=N, H=H, k0=k0, dr=50.0)
+    plan = O.pade_plan(g.sigma, 5)
+    X = O.fd_second_difference(N, H) / k0 ** 2 + np.diag(V)
+    u = _rng_field(N, 5)
+    got = O.fd_step(u, V, g, plan)
+    ref = O.dense_pade_step(X.astype(np.complex128), plan, form="product") @ u
+    assert np.max(np.abs(got - ref)) < 1e-10 * np.max(np.abs(ref))
+
+
+def test_fd_norm_conserved_and_converges_to_spectral():
+    """FD-SSP conserves the norm for real n^2 (X real symmetric, |R| = 1 on the real axis) and,
+    for a smooth field, approaches the spectral marcher as the grid is refined (second order)."""
+    H, f, dr, steps = 5000.0, 30.0, 50.0, 40
+    errs = []
+    for N in (127, 255, 511):
+        z = inputs.depth_grid(N, H)
+        V = inputs.n2_from_c(inputs.munk_c(z)) - 1.0
+        k0 = 2 * math.pi * f / 1500
+        g = O.Grid(N=N, H=H, k0=k0, dr=dr)
+        u0 = inputs.gaussian_starter(z, k0, 1000.0) * 0 + np.exp(-((z - 1200.0) / 300.0) ** 2)
+        fd = O.fd_march(u0, [(0.0, V + 1.0)], g, 4, steps, tl_every=0)
+        assert abs(np.linalg.norm(fd.u) / np.linalg.norm(u0) - 1) < 1e-10
+        sp = O.march(u0, [(0.0, V + 1.0)], g, 4, steps, 40, 1e-13, tl_every=0, form="product")
+        errs.append(np.linalg.norm(fd.u - sp.u) / np.linalg.norm(sp.u))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[1] / errs[2] > 3.0  # about 4 for a second-order stencil
