@@ -2,22 +2,19 @@
 //
 // Same method as march_kernel.cuh (product-form Pade stages with hi/lo multipliers, Neumann
 // series, spectral-resident field), but every length-L array lives in a per-solve workspace
-// in global memory (L2-resident for a single solve, HBM for large batches), one CTA of 256
+// in global memory (L2-resident for a single solve, HBM for large batches), one CTA of 512
 // threads per solve, with a __syncthreads between passes (global writes are visible to the
 // block after it).  The DST-I here is the DFT of the odd extension in two passes of
 // shared-memory tiles (see dst_global), with no prefix scan: the scan form's odd outputs lose
 // accuracy like sqrt(L) (3.6e-5 relative at L = 65536 in FP32), which these grids cannot afford.
-// Element-wise work walks the natural index i = t + 256 q, so every access is coalesced.
+// Element-wise work walks the natural index i = t + 512 q, so every access is coalesced.
 #pragma once
 #include "march_kernel.cuh"
 
 namespace sssp {
 
-// 256 threads and 4096-point tiles (16 points per thread): 94.5 KB of shared memory at
-// L = 65536, so two CTAs (two solves) share an SM and hide each other's tile barriers
-constexpr int kLargeNT = 256;
-constexpr int kLargeLog2Tile = 12;  // points per tile (16 per thread)
-constexpr int kLargeMinBlocks = 2;
+constexpr int kLargeNT = 512;
+constexpr int kLargeLog2Tile = 13;  // points per tile (16 per thread)
 constexpr int kLargeTile = 1 << kLargeLog2Tile;
 constexpr int kLargePT = kLargeTile / kLargeNT;  // points per thread per tile
 constexpr int kLargeMinLog2 = 13;
@@ -385,7 +382,7 @@ struct SnkTL {  // TL row: -10 log10 |u_n|^2 + 10 log10 r, n = 1..N
 };
 
 template <int LOG2L>
-__global__ void __launch_bounds__(kLargeNT, kLargeMinBlocks)
+__global__ void __launch_bounds__(kLargeNT, 1)
     sssp_march_large_kernel(const SolveDesc* __restrict__ descs, const LargeTabs tb) {
   using C = CfgL<LOG2L>;
   constexpr int L = C::L;
@@ -512,7 +509,7 @@ struct SnkScaled {
 };
 
 template <int LOG2L>
-__global__ void __launch_bounds__(kLargeNT, kLargeMinBlocks)
+__global__ void __launch_bounds__(kLargeNT, 1)
     sssp_dst_large_kernel(const float2* __restrict__ in, float2* __restrict__ out, float scale, float2* work,
                           const LargeTabs tb, long long in_stride = 0, long long out_stride = 0) {
   extern __shared__ __align__(16) float2 tile_smem[];
