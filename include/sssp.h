@@ -279,7 +279,10 @@ pe_status pe_plan_get_shape(const pe_plan* plan, int* points_per_thread);
  * steps of the batched march of `plans` (pe_march_batch) with each shape the plans can take —
  * one CTA per solve at 4, 8 and 16 points per thread, and one thread-block cluster per solve —
  * a warm-up run then a timed run each, restores every plan's state and TL bookkeeping after each
- * run, and sets the fastest shape on every plan that can take it.  ms: 4 floats, the timed
+ * run, and sets the fastest shape on every plan that can take it; it then measures every plan's
+ * DST-I count per step on that shape (one more run, restored), and later batched marches launch
+ * each group's solves in descending cost (heavy and light solves share SMs; the results do not
+ * depend on the order).  ms: 4 floats, the timed
  * milliseconds of (CTA P=4, CTA P=8, CTA P=16, cluster), -1 where no plan can take the shape, or
  * NULL; kernel / points_per_thread: the shape chosen, or NULL.  pe_plan_autotune_shapes is the
  * same for one plan.  Plans need a field (and a profile when Neumann terms are asked for);

@@ -26,6 +26,8 @@ struct pe_plan {
   float4* dFD = nullptr;   // FD-SSP: node_cap x p x L x 3 float4 Thomas factors (hi + lo)
   float4* dFDc = nullptr;  // FD-SSP: per stage hi/lo of a_j/b_j and 1 - a_j/b_j
   int fd_cap = 0;          // nodes dFD holds
+  double cost = 0.0;       // DST-I per range step measured by the batch autotuner (0: unknown);
+                           // a batched launch orders its solves by it
   int off = 1;  // index of the first stored depth point in the length-L arrays
   double H = 0, k0 = 0, dr = 0, tol = 0;
   cudaStream_t stream = nullptr;

@@ -1159,7 +1159,15 @@ def test_batch_autotune_restores_state_and_picks_the_fastest(sssp):
         tl, _ = plans[idx].read_tl()
         assert tl.shape[0] == 3
         _compare(u, tl, _oracle(solves[idx], tl_every=10))
-    for p in plans:
+    # the tuned plans carry measured costs and launch in cost order; an untuned batch at the same
+    # shape launches in call order: the same bits
+    plain = [sssp.plan_for(s, tl_every=10) for s in solves]
+    for p in plain:
+        p.set_shape(want)
+    sssp.march_batch(plain, 30)
+    for a, b in zip(plans, plain):
+        assert np.array_equal(a.read_field(), b.read_field())
+    for p in plans + plain:
         p.close()
 
 
@@ -1234,3 +1242,21 @@ def test_coarse_grid_sssp_converges_where_fdssp_does_not(sssp):
         err[(N, op)] = float(np.linalg.norm(u - r) / np.linalg.norm(r))
     print("coarse-grid errors vs SSSP N=2047:", err)
     assert err[(127, "spectral")] < err[(511, "fd3")] < err[(255, "fd3")] < err[(127, "fd3")]
+
+
+def test_fdssp_range_dependent_nodes(sssp):
+    """FD-SSP with a range-dependent profile (Munk + eddy, a node every 2.5 km, each node's
+    Thomas factors computed at set-up) against the oracle's FD-SSP march with the same nodes
+    and the midpoint rule."""
+    N, H, f, dr, steps = 511, 5000.0, 40.0, 50.0, 300
+    s = inputs.munk(N=N, H=H, freq=f, dr=dr, steps=steps, pade_order=5)
+    z = s.z
+    cm = inputs.munk_c(z)
+    s.profiles = [(r, inputs.n2_from_c(cm + inputs.gaussian_eddy_dc(r + 1250.0, z, -20.0, r0=7500.0, Lr=4000.0),
+                                       s.c0)) for r in np.arange(0.0, steps * dr, 2500.0)]
+    pl = sssp.plan_for(s, tl_every=25, op="fd3")
+    pl.march(steps)
+    u = pl.read_field()
+    tl, _ = pl.read_tl()
+    pl.close()
+    _compare(u, tl, _fd_oracle(s, 25))
