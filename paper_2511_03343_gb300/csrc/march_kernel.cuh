@@ -68,6 +68,21 @@ struct SolveDesc {
   const float4* fdc;     // FD-SSP plans: per stage hi/lo of a_j/b_j and 1 - a_j/b_j
 };
 
+// Whether the passes from span NS end with a radix-2 pass (span L/2)
+template <int LOG2L, int NS, int PPT>
+__host__ __device__ constexpr bool ends_radix2() {
+  constexpr int L = 1 << LOG2L;
+  if constexpr (NS >= L) {
+    return false;
+  } else if constexpr (L / NS == 2) {
+    return true;
+  } else {
+    return ends_radix2<LOG2L, NS * ((L / NS) >= PPT ? PPT : (L / NS)), PPT>();
+  }
+}
+
+constexpr bool kTwiddleRegisters = true;
+
 template <int LOG2L, int PPT = 8>
 struct Cfg {
   static constexpr int L = 1 << LOG2L;
@@ -78,9 +93,13 @@ struct Cfg {
   static constexpr int WS = NT >= 32 ? 32 : NT;
   static constexpr int NW = (NT + 31) / 32;
   static constexpr unsigned MASK = NT >= 32 ? 0xffffffffu : ((1u << NT) - 1u);
-  // CTAs per SM the register budget is sized for: 128 registers per thread for P <= 8, 255 for
-  // P = 16 (its 16-point butterflies hold 3 x 16 complex values), at most 16 CTAs
-  static constexpr int REGS = PPT <= 8 ? 128 : 256;
+  // per-thread twiddles of the one-butterfly-per-thread passes kept in registers (P = 8, passes
+  // that end with radix 2)
+  static constexpr bool TWREG = kTwiddleRegisters && PPT == 8 && ends_radix2<LOG2L, PPT, PPT>();
+  // CTAs per SM the register budget is sized for: 128 registers per thread for P <= 8 (168 with
+  // the register twiddles), 255 for P = 16 (its 16-point butterflies hold 3 x 16 complex
+  // values), at most 16 CTAs
+  static constexpr int REGS = PPT <= 8 ? (TWREG ? 168 : 128) : 256;
   static constexpr int MB0 = 65536 / ((NT < 32 ? 32 : NT) * REGS);  // registers go by whole warps
   static constexpr int MIN_BLOCKS = MB0 >= 16 ? 16 : (MB0 < 1 ? 1 : MB0);
   // dynamic shared memory: 2 padded buffers, twiddles, t_0 and B_j areas, sin weights, V row,
@@ -234,19 +253,6 @@ __device__ __forceinline__ void fft_pass(const float2* __restrict__ src, float2*
   }
 }
 
-// Whether the passes from span NS end with a radix-2 pass (span L/2)
-template <int LOG2L, int NS, int PPT>
-__host__ __device__ constexpr bool ends_radix2() {
-  constexpr int L = 1 << LOG2L;
-  if constexpr (NS >= L) {
-    return false;
-  } else if constexpr (L / NS == 2) {
-    return true;
-  } else {
-    return ends_radix2<LOG2L, NS * ((L / NS) >= PPT ? PPT : (L / NS)), PPT>();
-  }
-}
-
 // The passes from span NS on, leaving out a final radix-2 pass (the DST-I post-processing does
 // it, see dst_block); returns the buffer holding the result
 template <int LOG2L, int NS, int PPT>
@@ -259,6 +265,82 @@ __device__ __forceinline__ float2* fft_rest_x2(float2* src, float2* dst, const f
     fft_pass<LOG2L, R, NS, PPT>(src, dst, tw);
     __syncthreads();
     return fft_rest_x2<LOG2L, NS * R, PPT>(dst, src, tw);
+  }
+}
+
+// Per-thread twiddles of the passes after the first, held in registers for a whole march: a pass
+// with one butterfly per thread (L/R = L/P butterflies) applies the same twiddles in every
+// transform, so they are loaded from the shared table once.  TwChain<LOG2L, NS, P> holds those of
+// the passes from span NS on (nothing for passes with more butterflies per thread, and nothing
+// for a final radix-2 pass, which the DST-I post-processing does with its own twiddles `post`).
+template <int LOG2L, int NS, int PPT>
+struct TwChain {
+  static constexpr int L = 1 << LOG2L;
+  static constexpr bool END = (NS >= L) || (L / NS == 2);
+  static constexpr int R = END ? 1 : ((L / NS) >= PPT ? PPT : (L / NS));
+  static constexpr bool REG = !END && (L / R) == (L / PPT);  // one butterfly per thread
+  float2 w[REG ? R - 1 : 1];
+  TwChain<LOG2L, (END ? L : NS * R), PPT> next;
+  __device__ __forceinline__ void load(const float2* tw) {
+    if constexpr (REG && NS > 1) {
+      const int k = threadIdx.x & (NS - 1);
+#pragma unroll
+      for (int r = 1; r < R; ++r) w[r - 1] = tw[(NS - PPT) + (r - 1) * NS + k];
+    }
+    if constexpr (!END) next.load(tw);
+  }
+};
+template <int LOG2L, int PPT>
+struct TwChain<LOG2L, (1 << LOG2L), PPT> {  // past the last pass
+  static constexpr bool END = true, REG = false;
+  static constexpr int R = 1;
+  __device__ __forceinline__ void load(const float2*) {}
+};
+
+// the whole chain of a transform plus the fused radix-2 pass's twiddles e^{-2 pi i k/L},
+// k = (P/2) t + s
+template <int LOG2L, int PPT>
+struct TwRegs {
+  TwChain<LOG2L, PPT, PPT> chain;
+  float2 post[PPT / 2];
+  __device__ __forceinline__ void load(const float2* tw) {
+    constexpr int L = 1 << LOG2L;
+    chain.load(tw);
+#pragma unroll
+    for (int s = 0; s < PPT / 2; ++s) post[s] = tw[(L / 2 - PPT) + (PPT / 2) * int(threadIdx.x) + s];
+  }
+};
+
+// fft_pass with the twiddles of a register chain link
+template <int LOG2L, int R, int NS, int PPT>
+__device__ __forceinline__ void fft_pass_reg(const float2* __restrict__ src, float2* __restrict__ dst,
+                                             const float2 (&w)[R - 1]) {
+  constexpr int L = 1 << LOG2L, NB = L / R;
+  const int j = threadIdx.x;
+  float2 v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = src[pidx(j + r * NB)];
+  const int k = j & (NS - 1);
+#pragma unroll
+  for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r - 1]);
+  dftR<R>(v);
+  const int base = (j - k) * R + k;
+#pragma unroll
+  for (int r = 0; r < R; ++r) dst[pidx(base + r * NS)] = v[r];
+}
+
+// fft_rest_x2 taking register twiddles where the chain holds them
+template <int LOG2L, int NS, int PPT>
+__device__ __forceinline__ float2* fft_rest_x2r(float2* src, float2* dst, const float2* tw,
+                                                const TwChain<LOG2L, NS, PPT>& c) {
+  using Ch = TwChain<LOG2L, NS, PPT>;
+  if constexpr (Ch::END) {
+    return src;
+  } else {
+    if constexpr (Ch::REG && NS > 1) fft_pass_reg<LOG2L, Ch::R, NS, PPT>(src, dst, c.w);
+    else fft_pass<LOG2L, Ch::R, NS, PPT>(src, dst, tw);
+    __syncthreads();
+    return fft_rest_x2r<LOG2L, NS * Ch::R, PPT>(dst, src, tw, c.next);
   }
 }
 
@@ -280,7 +362,8 @@ __device__ __forceinline__ float2* fft_rest(float2* src, float2* dst, const floa
 // On return every thread has finished reading both buffers.
 template <int LOG2L, int PPT = 8>
 __device__ __forceinline__ void dst_block(float2* a, float2* b, const float2* __restrict__ tw,
-                                          const float* __restrict__ sinw, float2* scan_s, float2 (&out)[PPT]) {
+                                          const float* __restrict__ sinw, float2* scan_s, float2 (&out)[PPT],
+                                          const TwRegs<LOG2L, PPT>* twr = nullptr) {
   using C = Cfg<LOG2L, PPT>;
   constexpr int L = C::L, H = C::HALF;
   const int t = threadIdx.x;
@@ -304,7 +387,8 @@ __device__ __forceinline__ void dst_block(float2* a, float2* b, const float2* __
   // Y_{L-k} = F_{L/2-k} + conj(w^k) F_{L-k} (the butterfly of L/2 - k, whose twiddle is
   // -conj(w^k)) -- the same arithmetic, one barrier and one pass through shared memory fewer.
   constexpr bool X2 = ends_radix2<LOG2L, PPT, PPT>();
-  const float2* F = X2 ? fft_rest_x2<LOG2L, PPT, PPT>(b, a, tw) : fft_rest<LOG2L, PPT, PPT>(b, a, tw);
+  const float2* F = X2 ? (twr ? fft_rest_x2r<LOG2L, PPT, PPT>(b, a, tw, twr->chain) : fft_rest_x2<LOG2L, PPT, PPT>(b, a, tw))
+                       : fft_rest<LOG2L, PPT, PPT>(b, a, tw);
   // post-processing: even outputs from pairs (k, L-k), odd outputs by a prefix scan
   float2 se[H], dd[H];
 #pragma unroll
@@ -312,7 +396,7 @@ __device__ __forceinline__ void dst_block(float2* a, float2* b, const float2* __
     const int k = H * t + s;
     float2 yk, ym;
     if constexpr (X2) {
-      const float2 w = tw[(L / 2 - PPT) + k];  // the radix-2 pass's twiddle e^{-2 pi i k/L}
+      const float2 w = twr ? twr->post[s] : tw[(L / 2 - PPT) + k];  // the radix-2 pass's e^{-2 pi i k/L}
       yk = F[pidx(k)] + cmul(F[pidx(k + L / 2)], w);
       ym = (k == 0) ? yk : F[pidx(L / 2 - k)] + cmul(F[pidx(L - k)], conjf2(w));
     } else {
@@ -387,11 +471,12 @@ __device__ __forceinline__ void dft_block(float2* a, float2* b, const float2* __
 // (the inverse transform up to the scale folded into the tables), otherwise depth -> spectral.
 template <int LOG2L, int BC, bool TO_DEPTH, int PPT = 8>
 __device__ __forceinline__ void xform(float2* a, float2* b, const float2* __restrict__ tw,
-                                      const float* __restrict__ sinw, float2* scan_s, float2 (&out)[PPT]) {
+                                      const float* __restrict__ sinw, float2* scan_s, float2 (&out)[PPT],
+                                      const TwRegs<LOG2L, PPT>* twr = nullptr) {
   if constexpr (BC == kBcPeriodic) {
     dft_block<LOG2L, TO_DEPTH, PPT>(a, b, tw, out);
   } else {
-    dst_block<LOG2L, PPT>(a, b, tw, sinw, scan_s, out);  // DST-I is its own inverse
+    dst_block<LOG2L, PPT>(a, b, tw, sinw, scan_s, out, twr);  // DST-I is its own inverse
   }
 }
 
@@ -492,6 +577,12 @@ __global__ void __launch_bounds__(Cfg<LOG2L, PPT>::NT, Cfg<LOG2L, PPT>::MIN_BLOC
   }
   load_tables<LOG2L, PPT>(sm.tw, sm.sinw, tw_g, sin_g);
   __syncthreads();
+  TwRegs<LOG2L, P> twr_v;
+  const TwRegs<LOG2L, P>* twr = nullptr;
+  if constexpr (C::TWREG) {
+    twr_v.load(sm.tw);
+    twr = &twr_v;
+  }
 
   float2 y[P];
   load8<LOG2L, P>(d.yhat + P * t, y);
@@ -566,7 +657,7 @@ __global__ void __launch_bounds__(Cfg<LOG2L, PPT>::NT, Cfg<LOG2L, PPT>::MIN_BLOC
           }
         }
         __syncthreads();
-        xform<LOG2L, BC, true, P>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // t_0 in depth space
+        xform<LOG2L, BC, true, P>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp, twr);  // t_0 in depth space
         ++ndst;
         float first = 0.f;
         for (int m = 1; m < d.terms; ++m) {
@@ -578,7 +669,7 @@ __global__ void __launch_bounds__(Cfg<LOG2L, PPT>::NT, Cfg<LOG2L, PPT>::MIN_BLOC
               sm.bufA[pidx(P * t + i)] = sm.Vs[P * t + i] * tp[i];
           }
           __syncthreads();
-          xform<LOG2L, BC, false, P>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // T(V t_{m-1})
+          xform<LOG2L, BC, false, P>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp, twr);  // T(V t_{m-1})
           ++ndst;
           float nt = 0.f, nw = 0.f;
 #pragma unroll
@@ -627,7 +718,7 @@ __global__ void __launch_bounds__(Cfg<LOG2L, PPT>::NT, Cfg<LOG2L, PPT>::MIN_BLOC
             break;
           }
           if (neumann_stop_fast(snt, snw, d.tol2, tol2f)) break;
-          xform<LOG2L, BC, true, P>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp);  // t_m in depth space
+          xform<LOG2L, BC, true, P>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp, twr);  // t_m in depth space
           ++ndst;
         }
         {
