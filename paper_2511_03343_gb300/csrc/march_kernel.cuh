@@ -82,6 +82,7 @@ __host__ __device__ constexpr bool ends_radix2() {
 }
 
 constexpr bool kTwiddleRegisters = true;
+constexpr bool kOperandRegisters = true;
 
 template <int LOG2L, int PPT = 8>
 struct Cfg {
@@ -96,10 +97,13 @@ struct Cfg {
   // per-thread twiddles of the one-butterfly-per-thread passes kept in registers (P = 8, passes
   // that end with radix 2)
   static constexpr bool TWREG = kTwiddleRegisters && PPT == 8 && ends_radix2<LOG2L, PPT, PPT>();
+  // the Neumann terms' per-thread operands (V row, B_j, t_0) and the sine weights in registers
+  // too, where a CTA is at most 128 threads (the register file then still holds two CTAs)
+  static constexpr bool OPREG = kOperandRegisters && TWREG && NT <= 128;
   // CTAs per SM the register budget is sized for: 128 registers per thread for P <= 8 (168 with
   // the register twiddles), 255 for P = 16 (its 16-point butterflies hold 3 x 16 complex
   // values), at most 16 CTAs
-  static constexpr int REGS = PPT <= 8 ? (TWREG ? 168 : 128) : 256;
+  static constexpr int REGS = PPT <= 8 ? (OPREG ? 255 : (TWREG ? 168 : 128)) : 256;
   static constexpr int MB0 = 65536 / ((NT < 32 ? 32 : NT) * REGS);  // registers go by whole warps
   static constexpr int MIN_BLOCKS = MB0 >= 16 ? 16 : (MB0 < 1 ? 1 : MB0);
   // dynamic shared memory: 2 padded buffers, twiddles, t_0 and B_j areas, sin weights, V row,
@@ -303,9 +307,16 @@ template <int LOG2L, int PPT>
 struct TwRegs {
   TwChain<LOG2L, PPT, PPT> chain;
   float2 post[PPT / 2];
-  __device__ __forceinline__ void load(const float2* tw) {
+  float sw[PPT];  // sine weights of the first pass, n = t + r L/P (filled only with `sinw`)
+  bool has_sw = false;
+  __device__ __forceinline__ void load(const float2* tw, const float* sinw = nullptr) {
     constexpr int L = 1 << LOG2L;
     chain.load(tw);
+    if (sinw) {
+#pragma unroll
+      for (int r = 0; r < PPT; ++r) sw[r] = sinw[int(threadIdx.x) + r * (L / PPT)];
+      has_sw = true;
+    }
 #pragma unroll
     for (int s = 0; s < PPT / 2; ++s) post[s] = tw[(L / 2 - PPT) + (PPT / 2) * int(threadIdx.x) + s];
   }
@@ -374,7 +385,7 @@ __device__ __forceinline__ void dst_block(float2* a, float2* b, const float2* __
       const int n = t + r * (L / PPT);
       const float2 xn = a[pidx(n)];
       const float2 xm = a[pidx((L - n) & (L - 1))];
-      const float s = sinw[n];
+      const float s = (twr && twr->has_sw) ? twr->sw[r] : sinw[n];
       v[r] = make_float2(fmaf(s, xn.x + xm.x, 0.5f * (xn.x - xm.x)), fmaf(s, xn.y + xm.y, 0.5f * (xn.y - xm.y)));
     }
     dftR<PPT>(v);
@@ -580,9 +591,11 @@ __global__ void __launch_bounds__(Cfg<LOG2L, PPT>::NT, Cfg<LOG2L, PPT>::MIN_BLOC
   TwRegs<LOG2L, P> twr_v;
   const TwRegs<LOG2L, P>* twr = nullptr;
   if constexpr (C::TWREG) {
-    twr_v.load(sm.tw);
+    twr_v.load(sm.tw, C::OPREG ? sm.sinw : nullptr);
     twr = &twr_v;
   }
+  // register copies of the thread's V row entries (OPREG), else read from sm.Vs / sm.Vis
+  float vr[P], vi[P];
 
   float2 y[P];
   load8<LOG2L, P>(d.yhat + P * t, y);
@@ -595,14 +608,27 @@ __global__ void __launch_bounds__(Cfg<LOG2L, PPT>::NT, Cfg<LOG2L, PPT>::MIN_BLOC
   int node = d.node0;
   double next_r = (node + 1 < d.nodes) ? d.node_r[node + 1] : 1e300;
   constexpr bool cplx = CPLX;  // complex n^2: launched only for solves with an imaginary profile
-  if (!iso) {
-    const float* Vg = d.V + (size_t)node * L;
-    for (int i = t; i < L; i += C::NT) sm.Vs[i] = Vg[i];
-    if constexpr (cplx) {
-      const float* Vig = d.Vi + (size_t)node * L;
-      for (int i = t; i < L; i += C::NT) sm.Vis[i] = Vig[i];
+  auto load_v = [&](int nd) {
+    const float* Vg = d.V + (size_t)nd * L;
+    const float* Vig = cplx ? d.Vi + (size_t)nd * L : nullptr;
+    if constexpr (C::OPREG) {
+#pragma unroll
+      for (int i = 0; i < P; i += 4) {
+        const float4 q = *reinterpret_cast<const float4*>(Vg + P * t + i);
+        vr[i] = q.x, vr[i + 1] = q.y, vr[i + 2] = q.z, vr[i + 3] = q.w;
+        if constexpr (cplx) {
+          const float4 qi = *reinterpret_cast<const float4*>(Vig + P * t + i);
+          vi[i] = qi.x, vi[i + 1] = qi.y, vi[i + 2] = qi.z, vi[i + 3] = qi.w;
+        }
+      }
+    } else {
+      for (int i = t; i < L; i += C::NT) sm.Vs[i] = Vg[i];
+      if constexpr (cplx) {
+        for (int i = t; i < L; i += C::NT) sm.Vis[i] = Vig[i];
+      }
     }
-  }
+  };
+  if (!iso) load_v(node);
   __syncthreads();
 
   if (iso) {
@@ -629,19 +655,14 @@ __global__ void __launch_bounds__(Cfg<LOG2L, PPT>::NT, Cfg<LOG2L, PPT>::MIN_BLOC
       if (rmid >= next_r) {  // advance to the node in force at this step's midpoint
         while (node + 1 < d.nodes && d.node_r[node + 1] <= rmid) ++node;
         next_r = (node + 1 < d.nodes) ? d.node_r[node + 1] : 1e300;
-        const float* Vg = d.V + (size_t)node * L;
-        for (int i = t; i < L; i += C::NT) sm.Vs[i] = Vg[i];
-        if constexpr (cplx) {
-          const float* Vig = d.Vi + (size_t)node * L;
-          for (int i = t; i < L; i += C::NT) sm.Vis[i] = Vig[i];
-        }
+        load_v(node);
         // first read of Vs is after the syncs of the stage's first transform
       }
       for (int j = 0; j < d.p && status == kStatusOk; ++j) {
         float2 acc[P], tp[P];
-        {
-          float2 Bj[P];
-          load8<LOG2L, P>(d.B + (size_t)j * L + P * t, Bj);
+        float2 Bj[P], t0r[P];  // register copies of B_j and t_0 (OPREG), else in sm.Bs / sm.t0s
+        load8<LOG2L, P>(d.B + (size_t)j * L + P * t, Bj);
+        if constexpr (!C::OPREG) {
 #pragma unroll
           for (int i = 0; i < P; ++i) sm.Bs[i * C::NT + t] = Bj[i];
         }
@@ -651,7 +672,8 @@ __global__ void __launch_bounds__(Cfg<LOG2L, PPT>::NT, Cfg<LOG2L, PPT>::MIN_BLOC
 #pragma unroll
           for (int i = 0; i < P; ++i) {
             const float2 t0 = cmul(Aj[i], y[i]);
-            sm.t0s[i * C::NT + t] = t0;
+            if constexpr (C::OPREG) t0r[i] = t0;
+            else sm.t0s[i * C::NT + t] = t0;
             sm.bufA[pidx(P * t + i)] = t0;
             acc[i] = make_float2(0.f, 0.f);
           }
@@ -663,10 +685,14 @@ __global__ void __launch_bounds__(Cfg<LOG2L, PPT>::NT, Cfg<LOG2L, PPT>::MIN_BLOC
         for (int m = 1; m < d.terms; ++m) {
 #pragma unroll
           for (int i = 0; i < P; ++i) {
-            if constexpr (cplx)
+            if constexpr (C::OPREG) {
+              if constexpr (cplx) sm.bufA[pidx(P * t + i)] = cmul(make_float2(vr[i], vi[i]), tp[i]);
+              else sm.bufA[pidx(P * t + i)] = vr[i] * tp[i];
+            } else if constexpr (cplx) {
               sm.bufA[pidx(P * t + i)] = cmul(make_float2(sm.Vs[P * t + i], sm.Vis[P * t + i]), tp[i]);
-            else
+            } else {
               sm.bufA[pidx(P * t + i)] = sm.Vs[P * t + i] * tp[i];
+            }
           }
           __syncthreads();
           xform<LOG2L, BC, false, P>(sm.bufA, sm.bufB, sm.tw, sm.sinw, sm.scan_s, tp, twr);  // T(V t_{m-1})
@@ -674,10 +700,10 @@ __global__ void __launch_bounds__(Cfg<LOG2L, PPT>::NT, Cfg<LOG2L, PPT>::MIN_BLOC
           float nt = 0.f, nw = 0.f;
 #pragma unroll
           for (int i = 0; i < P; ++i) {
-            tp[i] = cmul(sm.Bs[i * C::NT + t], tp[i]);  // spectral t_m (scaled by 2/L)
+            tp[i] = cmul(C::OPREG ? Bj[i] : sm.Bs[i * C::NT + t], tp[i]);  // spectral t_m (scaled by 2/L)
             acc[i] = acc[i] + tp[i];
             nt += cabs2(tp[i]);
-            nw += cabs2(sm.t0s[i * C::NT + t] + acc[i]);
+            nw += cabs2((C::OPREG ? t0r[i] : sm.t0s[i * C::NT + t]) + acc[i]);
           }
 #pragma unroll
           for (int o = C::WS / 2; o > 0; o >>= 1) {
