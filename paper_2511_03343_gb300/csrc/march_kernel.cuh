@@ -94,16 +94,17 @@ struct Cfg {
   static constexpr int WS = NT >= 32 ? 32 : NT;
   static constexpr int NW = (NT + 31) / 32;
   static constexpr unsigned MASK = NT >= 32 ? 0xffffffffu : ((1u << NT) - 1u);
-  // per-thread twiddles of the one-butterfly-per-thread passes kept in registers (P = 8, passes
-  // that end with radix 2)
-  static constexpr bool TWREG = kTwiddleRegisters && PPT == 8 && ends_radix2<LOG2L, PPT, PPT>();
+  // per-thread twiddles of the one-butterfly-per-thread passes kept in registers (P = 4 and 8,
+  // L <= 1024)
+  static constexpr bool TWREG = kTwiddleRegisters && (PPT == 8 || PPT == 4) && L <= 1024;
   // the Neumann terms' per-thread operands (V row, B_j, t_0) and the sine weights in registers
-  // too, where a CTA is at most 128 threads (the register file then still holds two CTAs)
-  static constexpr bool OPREG = kOperandRegisters && TWREG && NT <= 128;
-  // CTAs per SM the register budget is sized for: 128 registers per thread for P <= 8 (168 with
-  // the register twiddles), 255 for P = 16 (its 16-point butterflies hold 3 x 16 complex
-  // values), at most 16 CTAs
-  static constexpr int REGS = PPT <= 8 ? (OPREG ? 255 : (TWREG ? 168 : 128)) : 256;
+  // too (the register file still holds two CTAs of the largest such grid)
+  static constexpr bool OPREG = kOperandRegisters && TWREG;
+  // CTAs per SM the register budget is sized for: 128 registers per thread for P = 4 and for
+  // P = 8 beyond L = 1024, 255 for P = 8 with the register-resident twiddles and operands (two
+  // CTAs of the 128-thread L = 1024 grid per SM) and for P = 16 (its 16-point butterflies hold
+  // 3 x 16 complex values), at most 16 CTAs
+  static constexpr int REGS = PPT == 8 ? (OPREG ? 255 : (TWREG ? 168 : 128)) : (PPT == 4 ? 128 : 256);
   static constexpr int MB0 = 65536 / ((NT < 32 ? 32 : NT) * REGS);  // registers go by whole warps
   static constexpr int MIN_BLOCKS = MB0 >= 16 ? 16 : (MB0 < 1 ? 1 : MB0);
   // dynamic shared memory: 2 padded buffers, twiddles, t_0 and B_j areas, sin weights, V row,
@@ -312,13 +313,15 @@ struct TwRegs {
   __device__ __forceinline__ void load(const float2* tw, const float* sinw = nullptr) {
     constexpr int L = 1 << LOG2L;
     chain.load(tw);
+    if constexpr (ends_radix2<LOG2L, PPT, PPT>()) {
+#pragma unroll
+      for (int s = 0; s < PPT / 2; ++s) post[s] = tw[(L / 2 - PPT) + (PPT / 2) * int(threadIdx.x) + s];
+    }
     if (sinw) {
 #pragma unroll
       for (int r = 0; r < PPT; ++r) sw[r] = sinw[int(threadIdx.x) + r * (L / PPT)];
       has_sw = true;
     }
-#pragma unroll
-    for (int s = 0; s < PPT / 2; ++s) post[s] = tw[(L / 2 - PPT) + (PPT / 2) * int(threadIdx.x) + s];
   }
 };
 
@@ -340,7 +343,8 @@ __device__ __forceinline__ void fft_pass_reg(const float2* __restrict__ src, flo
   for (int r = 0; r < R; ++r) dst[pidx(base + r * NS)] = v[r];
 }
 
-// fft_rest_x2 taking register twiddles where the chain holds them
+// fft_rest_x2 taking register twiddles where the chain holds them (for passes that do not end
+// with radix 2 it runs them all, like fft_rest)
 template <int LOG2L, int NS, int PPT>
 __device__ __forceinline__ float2* fft_rest_x2r(float2* src, float2* dst, const float2* tw,
                                                 const TwChain<LOG2L, NS, PPT>& c) {
@@ -398,8 +402,8 @@ __device__ __forceinline__ void dst_block(float2* a, float2* b, const float2* __
   // Y_{L-k} = F_{L/2-k} + conj(w^k) F_{L-k} (the butterfly of L/2 - k, whose twiddle is
   // -conj(w^k)) -- the same arithmetic, one barrier and one pass through shared memory fewer.
   constexpr bool X2 = ends_radix2<LOG2L, PPT, PPT>();
-  const float2* F = X2 ? (twr ? fft_rest_x2r<LOG2L, PPT, PPT>(b, a, tw, twr->chain) : fft_rest_x2<LOG2L, PPT, PPT>(b, a, tw))
-                       : fft_rest<LOG2L, PPT, PPT>(b, a, tw);
+  const float2* F = twr ? fft_rest_x2r<LOG2L, PPT, PPT>(b, a, tw, twr->chain)
+                        : (X2 ? fft_rest_x2<LOG2L, PPT, PPT>(b, a, tw) : fft_rest<LOG2L, PPT, PPT>(b, a, tw));
   // post-processing: even outputs from pairs (k, L-k), odd outputs by a prefix scan
   float2 se[H], dd[H];
 #pragma unroll
