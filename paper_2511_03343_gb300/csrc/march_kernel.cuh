@@ -118,9 +118,47 @@ struct Cfg {
 // accesses stay conflict-free and the stride-4 / stride-8 patterns spread over the banks
 __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
 
-__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+// Complex additions, subtractions and real scalings as packed two-lane FP32 instructions
+// (add/sub/mul .f32x2 of sm_100-family GPUs): one instruction for both components, each lane
+// rounded exactly as the scalar instruction would round it.
+constexpr bool kPackedF32 = true;
+
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) {
+  if constexpr (kPackedF32) {
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+  } else {
+    return make_float2(a.x + b.x, a.y + b.y);
+  }
+}
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) {
+  if constexpr (kPackedF32) {
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+  } else {
+    return make_float2(a.x - b.x, a.y - b.y);
+  }
+}
+__device__ __forceinline__ float2 operator*(float s, float2 a) {
+  if constexpr (kPackedF32) {
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rs, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rs, {%4, %4};\n\t"
+        "mul.rn.f32x2 rd, rs, ra;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(s));
+    return r;
+  } else {
+    return make_float2(s * a.x, s * a.y);
+  }
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
