@@ -90,7 +90,8 @@ struct Cfg {
   static constexpr int P = PPT;               // points per thread (radix of the passes)
   static constexpr int HALF = PPT / 2;        // DST-I output pairs per thread
   static constexpr int NT = L / PPT;          // threads per CTA
-  static constexpr int PADL = L + L / 16;     // padded buffer length
+  // padded buffer length (64 more at L = 1024, P = 8 for the span-8 pass's layout, BufMap)
+  static constexpr int PADL = L + L / 16 + 64 * (LOG2L == 10 && PPT == 8);
   static constexpr int WS = NT >= 32 ? 32 : NT;
   static constexpr int NW = (NT + 31) / 32;
   static constexpr unsigned MASK = NT >= 32 ? 0xffffffffu : ((1u << NT) - 1u);
@@ -363,37 +364,79 @@ struct TwRegs {
   }
 };
 
-// fft_pass with the twiddles of a register chain link
-template <int LOG2L, int R, int NS, int PPT>
+// Shared-memory layout of the buffer written by the pass of span NS (NS = 1: the first pass) on
+// the register-twiddle path: pidx unless specialised.  At L = 1024, 8 points per thread, two
+// buffers get layouts of their own (found by counting the bank wavefronts of every warp access
+// of the transform), which make their accesses conflict-free where pidx gives 2-way conflicts:
+// the span-8 pass writes butterfly outputs (j - k) 8 + k + 8 r, so one half-warp stores rows 0
+// and 64 apart -- an extra 2 words per 32 elements moves them to different banks; the span-64
+// pass's output is read by the DST-I post-processing forwards and backwards with stride 4 -- an
+// XOR of the low index bits with (3 b) & 12 within each 16-element block b spreads both.
+template <int LOG2L, int PPT, int NS>
+struct BufMap {
+  static constexpr bool DEFAULT = true;
+  __device__ static __forceinline__ int at(int i) { return pidx(i); }
+};
+template <>
+struct BufMap<10, 8, 8> {
+  static constexpr bool DEFAULT = false;  // indices up to 1023 + 63 + 62 (Cfg::PADL has room)
+  __device__ static __forceinline__ int at(int i) { return i + (i >> 4) + 2 * (i >> 5); }
+};
+template <>
+struct BufMap<10, 8, 64> {
+  static constexpr bool DEFAULT = false;
+  __device__ static __forceinline__ int at(int i) {
+    const int j = i ^ ((3 * (i >> 4)) & 12);
+    return j + (j >> 4);
+  }
+};
+
+// fft_pass with the twiddles of a register chain link, reading the layout SM and writing DM
+template <int LOG2L, int R, int NS, int PPT, class SM, class DM>
 __device__ __forceinline__ void fft_pass_reg(const float2* __restrict__ src, float2* __restrict__ dst,
                                              const float2 (&w)[R - 1]) {
   constexpr int L = 1 << LOG2L, NB = L / R;
   const int j = threadIdx.x;
   float2 v[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) v[r] = src[pidx(j + r * NB)];
+  for (int r = 0; r < R; ++r) v[r] = src[SM::at(j + r * NB)];
   const int k = j & (NS - 1);
 #pragma unroll
   for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r - 1]);
   dftR<R>(v);
   const int base = (j - k) * R + k;
 #pragma unroll
-  for (int r = 0; r < R; ++r) dst[pidx(base + r * NS)] = v[r];
+  for (int r = 0; r < R; ++r) dst[DM::at(base + r * NS)] = v[r];
+}
+
+// span of the last pass fft_rest_x2r runs from span NS on (PREV: the span of the pass before)
+template <int LOG2L, int NS, int PPT, int PREV>
+__host__ __device__ constexpr int chain_last_span() {
+  using Ch = TwChain<LOG2L, NS, PPT>;
+  if constexpr (Ch::END) return PREV;
+  else return chain_last_span<LOG2L, NS * Ch::R, PPT, NS>();
 }
 
 // fft_rest_x2 taking register twiddles where the chain holds them (for passes that do not end
-// with radix 2 it runs them all, like fft_rest)
-template <int LOG2L, int NS, int PPT>
+// with radix 2 it runs them all, like fft_rest); src holds the output of the pass of span PREV,
+// and the returned buffer is in the layout BufMap of the last pass's span
+template <int LOG2L, int NS, int PPT, int PREV = 1>
 __device__ __forceinline__ float2* fft_rest_x2r(float2* src, float2* dst, const float2* tw,
                                                 const TwChain<LOG2L, NS, PPT>& c) {
   using Ch = TwChain<LOG2L, NS, PPT>;
   if constexpr (Ch::END) {
     return src;
   } else {
-    if constexpr (Ch::REG && NS > 1) fft_pass_reg<LOG2L, Ch::R, NS, PPT>(src, dst, c.w);
-    else fft_pass<LOG2L, Ch::R, NS, PPT>(src, dst, tw);
+    using SM = BufMap<LOG2L, PPT, PREV>;
+    using DM = BufMap<LOG2L, PPT, NS>;
+    if constexpr (Ch::REG && NS > 1) {
+      fft_pass_reg<LOG2L, Ch::R, NS, PPT, SM, DM>(src, dst, c.w);
+    } else {
+      static_assert(SM::DEFAULT && DM::DEFAULT, "shared-table passes use the pidx layout");
+      fft_pass<LOG2L, Ch::R, NS, PPT>(src, dst, tw);
+    }
     __syncthreads();
-    return fft_rest_x2r<LOG2L, NS * Ch::R, PPT>(dst, src, tw, c.next);
+    return fft_rest_x2r<LOG2L, NS * Ch::R, PPT, NS>(dst, src, tw, c.next);
   }
 }
 
@@ -442,6 +485,8 @@ __device__ __forceinline__ void dst_block(float2* a, float2* b, const float2* __
   constexpr bool X2 = ends_radix2<LOG2L, PPT, PPT>();
   const float2* F = twr ? fft_rest_x2r<LOG2L, PPT, PPT>(b, a, tw, twr->chain)
                         : (X2 ? fft_rest_x2<LOG2L, PPT, PPT>(b, a, tw) : fft_rest<LOG2L, PPT, PPT>(b, a, tw));
+  using FM = BufMap<LOG2L, PPT, chain_last_span<LOG2L, PPT, PPT, 1>()>;  // F's layout (register path)
+  auto fat = [&](int i) { return twr ? FM::at(i) : pidx(i); };
   // post-processing: even outputs from pairs (k, L-k), odd outputs by a prefix scan
   float2 se[H], dd[H];
 #pragma unroll
@@ -450,11 +495,11 @@ __device__ __forceinline__ void dst_block(float2* a, float2* b, const float2* __
     float2 yk, ym;
     if constexpr (X2) {
       const float2 w = twr ? twr->post[s] : tw[(L / 2 - PPT) + k];  // the radix-2 pass's e^{-2 pi i k/L}
-      yk = F[pidx(k)] + cmul(F[pidx(k + L / 2)], w);
-      ym = (k == 0) ? yk : F[pidx(L / 2 - k)] + cmul(F[pidx(L - k)], conjf2(w));
+      yk = F[fat(k)] + cmul(F[fat(k + L / 2)], w);
+      ym = (k == 0) ? yk : F[fat(L / 2 - k)] + cmul(F[fat(L - k)], conjf2(w));
     } else {
-      yk = F[pidx(k)];
-      ym = F[pidx((L - k) & (L - 1))];
+      yk = F[fat(k)];
+      ym = F[fat((L - k) & (L - 1))];
     }
     se[s] = make_float2(-0.5f * (yk.y - ym.y), 0.5f * (yk.x - ym.x));
     dd[s] = (k == 0) ? 0.5f * yk : 0.5f * (yk + ym);
@@ -763,15 +808,15 @@ __global__ void __launch_bounds__(Cfg<LOG2L, PPT>::NT, Cfg<LOG2L, PPT>::MIN_BLOC
           }
           __syncthreads();
           if (last) break;
-          // block totals: lane w of every warp holds warp w's partials (0 beyond NW), then a
-          // butterfly sum over the whole warp so that EVERY lane holds the same total — the
-          // stop decision below must be uniform across the block (it guards __syncthreads).
-          float snt = (lane < C::NW) ? sm.red[2 * lane] : 0.f;
-          float snw = (lane < C::NW) ? sm.red[2 * lane + 1] : 0.f;
+          // block totals: every thread adds the warps' partials in the same order (broadcast
+          // reads, no dependent shuffles), so EVERY thread holds the same total — the stop
+          // decision below must be uniform across the block (it guards __syncthreads).
+          float snt = 0.f, snw = 0.f;
 #pragma unroll
-          for (int o = C::WS / 2; o > 0; o >>= 1) {
-            snt += __shfl_xor_sync(C::MASK, snt, o, C::WS);
-            snw += __shfl_xor_sync(C::MASK, snw, o, C::WS);
+          for (int w = 0; w < C::NW; ++w) {
+            const float2 pr = reinterpret_cast<const float2*>(sm.red)[w];
+            snt += pr.x;
+            snw += pr.y;
           }
           if (!isfinite(snt) || !isfinite(snw)) {
             status = kStatusNumeric;
