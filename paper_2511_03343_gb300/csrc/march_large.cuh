@@ -20,7 +20,7 @@ constexpr int kLargePT = kLargeTile / kLargeNT;  // points per thread per tile
 constexpr int kLargeMinLog2 = 13;
 constexpr int kLargeMaxLog2 = 16;
 
-// workspace layout (float2 units): X (L) | W (2L) | acc (L) | t0 (L)
+// workspace layout (float2 units): X (L) | W (2L) | w (L) | t0 (L)
 __host__ __device__ constexpr size_t large_work_elems(int L) { return 5 * size_t(L); }
 
 template <int LOG2L>
@@ -321,16 +321,16 @@ struct SrcV {  // x_m = V_m a[m] (V real, or V + i Vi)
     return Vi ? cmul(make_float2(__ldg(V + m), __ldg(Vi + m)), x) : __ldg(V + m) * x;
   }
 };
-struct SrcStage {  // x_m = t0_m = A_m y_m; on the first visit also t0[m] = x_m, acc[m] = 0
+struct SrcStage {  // x_m = t0_m = A_m y_m; on the first visit also t0[m] = w[m] = x_m
   const float2* A;
   const float2* y;
   float2* t0;
-  float2* acc;
+  float2* w;
   __device__ __forceinline__ float2 operator()(int m, bool first) const {
     const float2 v = cmul(__ldg(A + m), y[m]);
     if (first) {
       t0[m] = v;
-      acc[m] = make_float2(0.f, 0.f);
+      w[m] = v;
     }
     return v;
   }
@@ -347,29 +347,29 @@ struct SnkArr {
   __device__ __forceinline__ void prefetch(int, int) {}
   __device__ __forceinline__ void put(int, int k, float2 v) { a[k] = v; }
 };
-struct SnkTerm {  // t_m = B_k S_k: acc += t_m, X = t_m, and the norm partials of the stop test
+// The partial sum w_j = t_0 + t_1 + .. is kept itself (not t_1 + .. beside t_0), so a term
+// streams B and w, and the stage's combine reads t_0 once: y <- R y + beta (w - t_0).
+struct SnkTerm {  // t_m = B_k S_k: w += t_m, X = t_m, and the norm partials of the stop test
   const float2* B;
-  const float2* t0;
-  float2* acc;
+  float2* w;
   float2* X;
   float nt, nw;
-  float2 pb[kLargePT / 2], pa[kLargePT / 2], pt[kLargePT / 2];  // B, acc, t0 of the tile's outputs
+  float2 pb[kLargePT / 2], pw[kLargePT / 2];  // B and w of the tile's outputs
   __device__ __forceinline__ void prefetch(int q, int k) {
     pb[q] = __ldg(B + k);
-    pa[q] = acc[k];
-    pt[q] = t0[k];
+    pw[q] = w[k];
   }
   __device__ __forceinline__ void put(int q, int k, float2 v) {
-    if (k == 0) {  // the zero mode: t_m = 0, acc[0] and t0[0] stay 0
+    if (k == 0) {  // the zero mode: t_m = 0, w[0] and t0[0] stay 0
       X[0] = make_float2(0.f, 0.f);
       return;
     }
     const float2 th = cmul(pb[q], v);
-    const float2 a = pa[q] + th;
-    acc[k] = a;
+    const float2 a = pw[q] + th;
+    w[k] = a;
     X[k] = th;
     nt += cabs2(th);
-    nw += cabs2(pt[q] + a);
+    nw += cabs2(a);
   }
 };
 struct SnkTL {  // TL row: -10 log10 |u_n|^2 + 10 log10 r, n = 1..N
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(kLargeNT, 1)
   float2* const y = d.yhat;
   float2* const X = d.work;
   float2* const W = d.work + L;
-  float2* const acc = d.work + 3 * L;
+  float2* const wsum = d.work + 3 * L;  // w_j = t_0 + t_1 + .. (spectral)
   float2* const t0 = d.work + 4 * L;
   const float out_scale = 2.0f / float(L);
   const bool iso = d.terms <= 1;
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(kLargeNT, 1)
   const float* V = iso ? nullptr : d.V + (size_t)node * L;
   const float* Vi = (iso || d.Vi == nullptr) ? nullptr : d.Vi + (size_t)node * L;
   if (t == 0) {  // the zero mode is never visited by the transform's source
-    acc[0] = make_float2(0.f, 0.f);
+    wsum[0] = make_float2(0.f, 0.f);
     t0[0] = make_float2(0.f, 0.f);
   }
   load_large_twiddles<LOG2L>(tile_smem, tb);
@@ -434,16 +434,16 @@ __global__ void __launch_bounds__(kLargeNT, 1)
         if (d.Vi != nullptr) Vi = d.Vi + (size_t)node * L;
       }
       for (int j = 0; j < d.p && status == kStatusOk; ++j) {
-        // t_0 = L_j^{-1} y in depth space; the source also sets t0 (spectral) and acc = 0
+        // t_0 = L_j^{-1} y in depth space; the source also sets t0 and w = t0 (spectral)
         {
           SnkArr sk{X};
-          dst_global<LOG2L>(W, tb, tile_smem, SrcStage{d.A + (size_t)j * L, y, t0, acc}, sk);
+          dst_global<LOG2L>(W, tb, tile_smem, SrcStage{d.A + (size_t)j * L, y, t0, wsum}, sk);
         }
         ++ndst;
         float first = 0.f;
         for (int m = 1; m < d.terms; ++m) {
-          SnkTerm sk{d.B + (size_t)j * L, t0, acc, X, 0.f, 0.f, {}, {}, {}};
-          dst_global<LOG2L>(W, tb, tile_smem, SrcV{X, V, Vi}, sk);  // B DST(V t_{m-1}), acc += t_m
+          SnkTerm sk{d.B + (size_t)j * L, wsum, X, 0.f, 0.f, {}, {}};
+          dst_global<LOG2L>(W, tb, tile_smem, SrcV{X, V, Vi}, sk);  // B DST(V t_{m-1}), w += t_m
           ++ndst;
           const float snt = block_sum<LOG2L>(sk.nt, red);
           const float snw = block_sum<LOG2L>(sk.nw, red + C::NW);
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(kLargeNT, 1)
 #pragma unroll 4
           for (int q = 0; q < C::PER; ++q) {
             const int i = t + q * kLargeNT;
-            y[i] = ffmul(__ldg(rp + i), y[i]) + cmul(bj, acc[i]);
+            y[i] = ffmul(__ldg(rp + i), y[i]) + cmul(bj, wsum[i] - t0[i]);
           }
         }
         __syncthreads();
