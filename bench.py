@@ -714,7 +714,8 @@ def bench_gemm(args):
             out[mode]["frac_of_bf16_peak"] = out[mode]["tensor_tflops"] / peak
     print(json.dumps({"metric": METRIC, "unit": UNIT, "config": {"workload": "batch_gemm_dst", "solves": len(solves),
                       "N": solves[0].N, "range_steps": steps, "gemm": f"{L} x {C} x {L} per transform, "
-                      "128 x 32 tiles, tcgen05.mma kind::f16 / kind::tf32"}, "bf16_peak_tflops": peak,
+                      "128 x 64 output tiles, K split over 2-CTA clusters (partials summed in distributed shared memory), "
+                      "tcgen05.mma kind::f16 / kind::tf32"}, "bf16_peak_tflops": peak,
                       "modes": out}), flush=True)
 
 

@@ -11,10 +11,12 @@
 //   PE_GEMM_TF32    one tcgen05.mma kind::tf32 product of the TF32-rounded operands;
 //   PE_GEMM_3XTF32  the hi/lo split with TF32 parts, three kind::tf32 products;
 //   PE_GEMM_FP32    a CUDA-core FP32 GEMM (the reference the others are measured against).
-// A CTA owns a 128 x 32 output tile: one thread issues TMA loads of 128-byte swizzled K slices
-// of S and X into a multi-stage shared-memory ring, another issues the MMAs (K-major operands,
-// the accumulator in 32 tensor-memory columns), and after the last product all four warps read
-// their 32 rows back with tcgen05.ld and run the step's element-wise work in the epilogue,
+// A cluster of kKS CTAs owns a 128 x 32 kKS output tile, each CTA one K range of it: one thread
+// issues TMA loads of 128-byte swizzled K slices of S and X (the hi and lo planes of a split
+// operand in one 3D load) into a multi-stage shared-memory ring, another issues the MMAs
+// (K-major operands, the accumulator in tensor memory), then the partial tiles are summed over
+// the cluster's distributed shared memory and each CTA runs the step's element-wise work for
+// its share of the rows in the epilogue (its operand loads issued before the main loop),
 // writing the next GEMM's operand (already split) directly:
 //   after a transform to depth space:    X' = V .* Y                 (the Neumann term's V t)
 //   after a transform to spectral space: t_m = B_j .* Y, acc += t_m, X' = t_m.
@@ -31,6 +33,9 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cooperative_groups.h>
+
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -43,7 +48,8 @@
 namespace {
 
 constexpr int kBM = 128;        // output rows per tile (modes or depths): the MMA's M, one TMEM lane each
-constexpr int kBN = 32;         // output columns per tile (16 complex fields): the MMA's N, 32 TMEM columns
+constexpr int kKS = 2;          // K splits per output tile = CTAs per cluster (1, 2 or 4)
+constexpr int kBN = 32 * kKS;   // output columns per tile: the MMA's N, as many TMEM columns
 constexpr int kRowBytes = 128;  // one swizzled K slice row: 64 BF16 or 32 FP32 values
 constexpr int kThreads = 128;
 constexpr uint64_t kWaitNs = 500000000ull;  // every barrier wait gives up after 0.5 s
@@ -123,6 +129,64 @@ __device__ __forceinline__ void epi_pair(const EpiArgs& a, int m, int col, float
   }
 }
 
+template <typename T>
+__device__ __forceinline__ T* ldg_ptr(T* const* p) {  // a pointer field of a read-only table
+  return reinterpret_cast<T*>(__ldg(reinterpret_cast<const unsigned long long*>(p)));
+}
+
+// The epilogue of 16 output pairs (row m; fields b0 .. b0 + 15, columns 2b and 2b + 1), the
+// same arithmetic as epi_pair in two parts: load() issues every operand load of the 16 pairs
+// (the kernel calls it before its main loop, so the loads complete under the contraction) and
+// apply() takes the accumulator values and does the stores.
+template <int MODE, int EPI>
+struct EpiOps {
+  float vv[16];
+  float2 bb[16], ac[16];
+  __device__ __forceinline__ void load(const EpiArgs& a, int m, int col0) {
+    const int b0 = col0 >> 1;
+    const size_t L = size_t(a.L);
+    if constexpr (EPI == kEpiTimesV) {
+      const float* vp[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) vp[i] = (b0 + i < a.B) ? ldg_ptr(&a.solves[b0 + i].V) : nullptr;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) vv[i] = vp[i] ? __ldg(vp[i] + m) : 0.f;
+    } else if constexpr (EPI == kEpiTerm || EPI == kEpiTermLast) {
+      const float2* bp[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) bp[i] = (b0 + i < a.B) ? ldg_ptr(&a.solves[b0 + i].B) : nullptr;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        bb[i] = bp[i] ? __ldg(bp[i] + size_t(a.j) * L + m) : make_float2(0.f, 0.f);
+        ac[i] = bp[i] ? a.ACC[size_t(b0 + i) * L + m] : make_float2(0.f, 0.f);
+      }
+    }
+  }
+  __device__ __forceinline__ void apply(const EpiArgs& a, int m, int col0, const float (&v)[32]) const {
+    const int b0 = col0 >> 1;
+    const size_t L = size_t(a.L);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      if (b0 + i >= a.B) continue;  // padding columns stay zero
+      const size_t ir = size_t(col0 + 2 * i) * L + m;
+      if constexpr (EPI == kEpiOut) {
+        a.Gout[ir] = v[2 * i];
+        a.Gout[ir + L] = v[2 * i + 1];
+      } else if constexpr (EPI == kEpiTimesV) {
+        put_x<MODE>(a.Xhi, a.Xlo, ir, vv[i] * v[2 * i]);
+        put_x<MODE>(a.Xhi, a.Xlo, ir + L, vv[i] * v[2 * i + 1]);
+      } else {
+        const float2 t = cmulf(bb[i], make_float2(v[2 * i], v[2 * i + 1]));
+        a.ACC[size_t(b0 + i) * L + m] = make_float2(ac[i].x + t.x, ac[i].y + t.y);
+        if constexpr (EPI == kEpiTerm) {
+          put_x<MODE>(a.Xhi, a.Xlo, ir, t.x);
+          put_x<MODE>(a.Xhi, a.Xlo, ir + L, t.y);
+        }
+      }
+    }
+  }
+};
+
 template <int MODE>
 struct Traits {
   static constexpr bool SPLIT = MODE != PE_GEMM_TF32;  // hi/lo operands, three products
@@ -130,20 +194,25 @@ struct Traits {
   static constexpr int EL = BF16 ? 2 : 4;              // operand bytes
   static constexpr int BK = kRowBytes / EL;            // K values per pipeline stage
   static constexpr int A_BYTES = kBM * kRowBytes;      // one S slice (128 rows x 128 B)
-  static constexpr int B_BYTES = kBN * kRowBytes;      // one X slice (32 columns x 128 B)
+  static constexpr int B_BYTES = kBN * kRowBytes;      // one X slice (kBN columns x 128 B)
+  // a stage: [S_hi | S_lo | X_hi | X_lo] (split modes: one 3D load each for S and X), or [S | X]
   static constexpr int STAGE_BYTES = (SPLIT ? 2 : 1) * (A_BYTES + B_BYTES);
-  static constexpr int STAGES = SPLIT ? 4 : 6;
-  static constexpr size_t SMEM = size_t(STAGES) * STAGE_BYTES + 1024;  // + alignment slack
+  static constexpr int STAGES0 = 196608 / STAGE_BYTES;  // ring stages within 192 KB, 2 .. 6
+  static constexpr int STAGES = STAGES0 < 2 ? 2 : (STAGES0 > 6 ? 6 : STAGES0);
+  static constexpr int P_BYTES = kKS > 1 ? kBN * kBM * 4 : 0;  // FP32 partial tile (reuses the ring)
+  static constexpr size_t RING = size_t(STAGES) * STAGE_BYTES;
+  static constexpr size_t SMEM = (RING > size_t(P_BYTES) ? RING : size_t(P_BYTES)) + 1024;  // + alignment slack
   static constexpr uint32_t IDESC = umma::instr_desc(kBM, kBN, BF16 ? umma::kFmtBF16 : umma::kFmtTF32);
 };
 
-// Y = S X for one 128 x 32 output tile with the fused epilogue (see the file comment).
-// Shared memory per stage: [S_hi slice | X_hi slice | S_lo slice | X_lo slice], 1024-byte aligned.
+// Y = S X for one 128 x kBN output tile with the fused epilogue (see the file comment), its K
+// range split over the kKS CTAs of a thread-block cluster: each CTA contracts L / kKS of K into
+// its tensor memory, stores the FP32 partial tile in its shared memory, and after a cluster
+// barrier CTA r sums the 128 / kKS rows [r 128 / kKS, ..) of every CTA's partial (distributed
+// shared memory, in CTA order) and runs their epilogue.
 template <int MODE, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
-    sssp_gemm_dst_kernel(const __grid_constant__ CUtensorMap mSh, const __grid_constant__ CUtensorMap mSl,
-                         const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
-                         EpiArgs ea) {
+    sssp_gemm_dst_kernel(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorMap mX, EpiArgs ea) {
   using T = Traits<MODE>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -153,8 +222,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rank = kKS > 1 ? int(cooperative_groups::this_cluster().block_rank()) : 0;
   const int m0 = blockIdx.x * kBM, c0 = blockIdx.y * kBN;
-  const int KB = ea.L / T::BK;
+  const int KB = ea.L / T::BK / kKS, kb0 = rank * KB;  // this CTA's K blocks
   // prologue (overlaps the preceding launch under programmatic dependent launch): barriers,
   // tensor memory, tensor-map prefetch; then wait for the preceding grid's results
   if (threadIdx.x == 0) {
@@ -165,12 +235,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     umma::mbar_init(&done, 1);
     abort_flag = 0;
     umma::fence_barrier_init();
-    umma::prefetch_tensormap(&mSh);
-    umma::prefetch_tensormap(&mXh);
-    if constexpr (T::SPLIT) {
-      umma::prefetch_tensormap(&mSl);
-      umma::prefetch_tensormap(&mXl);
-    }
+    umma::prefetch_tensormap(&mS);
+    umma::prefetch_tensormap(&mX);
   }
   if (warp == 0) {
     umma::tmem_alloc(&tmem_base, kBN);
@@ -184,6 +250,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0 && *reinterpret_cast<volatile int*>(ea.status) != 0)
     abort_flag = 1;  // an earlier launch of the batch gave up: do nothing more
   __syncthreads();
+  // this thread's epilogue: 32 columns of one output row; its operands load under the main loop
+  constexpr int RP = kBM / kKS;  // rows per CTA after the reduction
+  const int erow = kKS > 1 ? rank * RP + int(threadIdx.x) % RP : int(threadIdx.x);
+  const int ecol = kKS > 1 ? c0 + 32 * (int(threadIdx.x) / RP) : c0;
+  EpiOps<MODE, EPI> ops;
+  if (!abort_flag) ops.load(ea, m0 + erow, ecol);
 
   if (abort_flag) {
     // nothing to load or multiply
@@ -196,12 +268,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       uint8_t* st = smem + size_t(s) * T::STAGE_BYTES;
+      const int kx = (kb0 + kb) * T::BK;
       umma::mbar_expect_tx(&full[s], T::STAGE_BYTES);
-      umma::tma_load_2d(st, &mSh, &full[s], kb * T::BK, m0);
-      umma::tma_load_2d(st + T::A_BYTES, &mXh, &full[s], kb * T::BK, c0);
-      if constexpr (T::SPLIT) {
-        umma::tma_load_2d(st + T::A_BYTES + T::B_BYTES, &mSl, &full[s], kb * T::BK, m0);
-        umma::tma_load_2d(st + 2 * T::A_BYTES + T::B_BYTES, &mXl, &full[s], kb * T::BK, c0);
+      if constexpr (T::SPLIT) {  // both planes (hi, lo) of each operand in one load
+        umma::tma_load_3d(st, &mS, &full[s], kx, m0, 0);
+        umma::tma_load_3d(st + 2 * T::A_BYTES, &mX, &full[s], kx, c0, 0);
+      } else {
+        umma::tma_load_2d(st, &mS, &full[s], kx, m0);
+        umma::tma_load_2d(st + T::A_BYTES, &mX, &full[s], kx, c0);
       }
       issued = kb + 1;
     }
@@ -217,9 +291,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       umma::tc_fence_after();
       const uint8_t* st = smem + size_t(s) * T::STAGE_BYTES;
-      const uint64_t ah = umma::desc_sw128(st), bh = umma::desc_sw128(st + T::A_BYTES);
-      const uint64_t al = umma::desc_sw128(st + T::A_BYTES + T::B_BYTES);
-      const uint64_t bl = umma::desc_sw128(st + 2 * T::A_BYTES + T::B_BYTES);
+      const uint64_t ah = umma::desc_sw128(st);
+      const uint64_t al = umma::desc_sw128(st + (T::SPLIT ? T::A_BYTES : 0));
+      const uint64_t bh = umma::desc_sw128(st + (T::SPLIT ? 2 : 1) * T::A_BYTES);
+      const uint64_t bl = umma::desc_sw128(st + (T::SPLIT ? 2 * T::A_BYTES + T::B_BYTES : T::A_BYTES));
 #pragma unroll
       for (int kk = 0; kk < kRowBytes / 32; ++kk) {  // MMA K steps of 32 bytes (16 BF16 / 8 TF32)
         const uint64_t o = uint64_t(kk * 32) >> 4;
@@ -246,16 +321,41 @@ __global__ void __launch_bounds__(kThreads, 1)
   const bool skipped = abort_flag != 0;
   const bool ok = !skipped && umma::mbar_wait(&done, 0, kWaitNs);
   umma::tc_fence_after();
-  __syncthreads();  // abort_flag is final
-  if (ok && !abort_flag) {
-    float v[32];
-    umma::tmem_ld32(tmem + (uint32_t(32 * warp) << 16), v);
-    const int m = m0 + 32 * warp + lane;
+  __syncthreads();  // abort_flag is final; the ring is no longer read or written
+  const bool good = ok && !abort_flag;
+  float v[32];
+  if constexpr (kKS == 1) {
+    if (good) {
+      umma::tmem_ld32(tmem + (uint32_t(32 * warp) << 16), v);
+      ops.apply(ea, m0 + erow, ecol, v);
+    }
+  } else {
+    float* part = reinterpret_cast<float*>(smem);  // [kBN columns][128 rows] FP32
+    if (good) {
+#pragma unroll 1
+      for (int cc = 0; cc < kBN; cc += 32) {
+        umma::tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(cc), v);
 #pragma unroll
-    for (int i = 0; i < kBN / 2; ++i) epi_pair<MODE, EPI>(ea, m, c0 + 2 * i, v[2 * i], v[2 * i + 1]);
-  } else if (threadIdx.x == 0 && !skipped) {
-    atomicExch(ea.status, kStatusTimeout);
+        for (int i = 0; i < 32; ++i) part[(cc + i) * kBM + 32 * warp + lane] = v[i];
+      }
+    }
+    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+    cl.sync();  // every CTA's partial is written (every CTA reaches this barrier)
+    if (good) {
+      const int colb = ecol - c0;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = 0.f;
+#pragma unroll
+      for (int c = 0; c < kKS; ++c) {
+        const float* pc = cl.map_shared_rank(part, c);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] += pc[(colb + i) * kBM + erow];
+      }
+      ops.apply(ea, m0 + erow, ecol, v);
+    }
+    cl.sync();  // no CTA leaves while its partial may still be read
   }
+  if (!good && threadIdx.x == 0 && !skipped) atomicExch(ea.status, kStatusTimeout);
   umma::tc_fence_before();
   __syncthreads();
   if (warp == 0) umma::tmem_dealloc(tmem, kBN);
@@ -384,19 +484,21 @@ EncodeTiled encode_fn() {
   return fn;
 }
 
-// 2D tensor map of a row-major matrix rows x inner (inner contiguous), tiles of box_rows rows x
-// one 128-byte slice, 128-byte swizzle
-bool make_map(CUtensorMap* m, void* base, bool bf16, size_t inner, size_t rows, int box_rows) {
+// Tensor map of a row-major matrix rows x inner (inner contiguous), tiles of box_rows rows x one
+// 128-byte slice, 128-byte swizzle.  planes = 2: the hi and lo parts, plane_bytes apart, as a 3D
+// map whose box takes both planes in one load.
+bool make_map(CUtensorMap* m, void* base, bool bf16, size_t inner, size_t rows, int box_rows, int planes,
+              size_t plane_bytes) {
   EncodeTiled enc = encode_fn();
   if (!enc) return false;
   const size_t el = bf16 ? 2 : 4;
-  const cuuint64_t dims[2] = {cuuint64_t(inner), cuuint64_t(rows)};
-  const cuuint64_t strides[1] = {cuuint64_t(inner * el)};
-  const cuuint32_t box[2] = {cuuint32_t(kRowBytes / el), cuuint32_t(box_rows)};
-  const cuuint32_t estr[2] = {1, 1};
-  return enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box,
-             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  const cuuint64_t dims[3] = {cuuint64_t(inner), cuuint64_t(rows), cuuint64_t(planes)};
+  const cuuint64_t strides[2] = {cuuint64_t(inner * el), cuuint64_t(plane_bytes)};
+  const cuuint32_t box[3] = {cuuint32_t(kRowBytes / el), cuuint32_t(box_rows), cuuint32_t(planes)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, planes > 1 ? 3 : 2, base,
+             dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -415,7 +517,7 @@ struct pe_gemm_batch {
   float2* ACC = nullptr;
   float* G = nullptr;  // C x L read-out
   int* status = nullptr;
-  CUtensorMap mS[2], mX[2][2];  // [hi, lo]; [buffer][hi, lo]
+  CUtensorMap mS, mX[2];  // S and the ping-pong X operands (split modes: hi and lo planes)
   cudaGraphExec_t step_graph = nullptr;
   unsigned long long gemms_per_step = 0;
   std::string err;
@@ -464,17 +566,20 @@ cudaError_t launch_gemm_t(pe_gemm_batch* g, int in_buf, const EpiArgs& a) {
       }
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(g->L / kBM, g->C / kBN);
+    cfg.gridDim = dim3(g->L / kBM, g->C / kBN, kKS);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = T::SMEM;
     cfg.stream = g->stream;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // overlap with the preceding launch
     attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;  // the K splits of one tile form a cluster
+    attr[1].val.clusterDim.x = 1;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = kKS;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, sssp_gemm_dst_kernel<MODE, EPI>, g->mS[0], g->mS[1], g->mX[in_buf][0],
-                              g->mX[in_buf][1], a);
+    cfg.numAttrs = kKS > 1 ? 2 : 1;
+    return cudaLaunchKernelEx(&cfg, sssp_gemm_dst_kernel<MODE, EPI>, g->mS, g->mX[in_buf], a);
   }
   return cudaGetLastError();
 }
@@ -515,26 +620,27 @@ ElemArgs elem_args(pe_gemm_batch* g, int j, int buf) {
   return a;
 }
 
-template <int MODE>
-void launch_start(pe_gemm_batch* g, const ElemArgs& a, int bl) {
-  k_stage_start<MODE><<<bl, 256, 0, g->stream>>>(a);
-}
+int elem_blocks(const ElemArgs& a) { return int((size_t(a.L) * a.B + 255) / 256); }
 
-void stage_start(pe_gemm_batch* g, const ElemArgs& a, int bl) {
+void stage_start(pe_gemm_batch* g, const ElemArgs& a) {
+  const int bl = elem_blocks(a);
+  cudaStream_t st = g->stream;
   switch (g->mode) {
-    case PE_GEMM_BF16X3: launch_start<PE_GEMM_BF16X3>(g, a, bl); break;
-    case PE_GEMM_TF32: launch_start<PE_GEMM_TF32>(g, a, bl); break;
-    case PE_GEMM_3XTF32: launch_start<PE_GEMM_3XTF32>(g, a, bl); break;
-    default: launch_start<PE_GEMM_FP32>(g, a, bl); break;
+    case PE_GEMM_BF16X3: k_stage_start<PE_GEMM_BF16X3><<<bl, 256, 0, st>>>(a); break;
+    case PE_GEMM_TF32: k_stage_start<PE_GEMM_TF32><<<bl, 256, 0, st>>>(a); break;
+    case PE_GEMM_3XTF32: k_stage_start<PE_GEMM_3XTF32><<<bl, 256, 0, st>>>(a); break;
+    default: k_stage_start<PE_GEMM_FP32><<<bl, 256, 0, st>>>(a); break;
   }
 }
 
-void stage_out(pe_gemm_batch* g, const ElemArgs& a, int bl) {
+void stage_out(pe_gemm_batch* g, const ElemArgs& a) {
+  const int bl = elem_blocks(a);
+  cudaStream_t st = g->stream;
   switch (g->mode) {
-    case PE_GEMM_BF16X3: k_out<PE_GEMM_BF16X3><<<bl, 256, 0, g->stream>>>(a); break;
-    case PE_GEMM_TF32: k_out<PE_GEMM_TF32><<<bl, 256, 0, g->stream>>>(a); break;
-    case PE_GEMM_3XTF32: k_out<PE_GEMM_3XTF32><<<bl, 256, 0, g->stream>>>(a); break;
-    default: k_out<PE_GEMM_FP32><<<bl, 256, 0, g->stream>>>(a); break;
+    case PE_GEMM_BF16X3: k_out<PE_GEMM_BF16X3><<<bl, 256, 0, st>>>(a); break;
+    case PE_GEMM_TF32: k_out<PE_GEMM_TF32><<<bl, 256, 0, st>>>(a); break;
+    case PE_GEMM_3XTF32: k_out<PE_GEMM_3XTF32><<<bl, 256, 0, st>>>(a); break;
+    default: k_out<PE_GEMM_FP32><<<bl, 256, 0, st>>>(a); break;
   }
 }
 
@@ -544,11 +650,9 @@ void stage_out(pe_gemm_batch* g, const ElemArgs& a, int bl) {
 //                       GEMM X0 (depth t_m) epilogue V.*  -> X1        (not after the last term)
 //   y = R_j y + beta_j acc
 pe_status enqueue_step(pe_gemm_batch* g) {
-  const size_t tot = size_t(g->L) * g->B;
-  const int bl = int((tot + 255) / 256);
   g->gemms_per_step = 0;
   for (int j = 0; j < g->p; ++j) {
-    stage_start(g, elem_args(g, j, 0), bl);
+    stage_start(g, elem_args(g, j, 0));
     cudaError_t e = launch_gemm(g, kEpiTimesV, 0, j);
     for (int m = 1; m < g->terms && e == cudaSuccess; ++m) {
       const bool last = (m == g->terms - 1);
@@ -556,7 +660,8 @@ pe_status enqueue_step(pe_gemm_batch* g) {
       if (!last && e == cudaSuccess) e = launch_gemm(g, kEpiTimesV, 0, j);
     }
     if (e != cudaSuccess) return gfail(g, PE_ERR_CUDA, std::string("GEMM launch: ") + cudaGetErrorString(e));
-    k_stage_end<<<bl, 256, 0, g->stream>>>(elem_args(g, j, 0));
+    const ElemArgs ea = elem_args(g, j, 0);
+    k_stage_end<<<elem_blocks(ea), 256, 0, g->stream>>>(ea);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return gfail(g, PE_ERR_CUDA, cudaGetErrorString(e));
@@ -583,7 +688,7 @@ pe_status pe_gemm_batch_create(pe_gemm_batch** out, pe_plan** plans, int count, 
       return PE_ERR_STATE;
     }
   }
-  if (p0->L < kBM || p0->L > 16384) {
+  if (p0->L < kBM || p0->L > 16384 || p0->L / 64 < kKS) {  // every K split gets a whole K block
     p0->err = "GEMM batch: N + 1 must be a power of two in [128, 16384]";
     return PE_ERR_ARG;
   }
@@ -606,24 +711,22 @@ pe_status pe_gemm_batch_create(pe_gemm_batch** out, pe_plan** plans, int count, 
   };
   float* S32 = nullptr;
   if (cudaMalloc(&S32, sizeof(float) * LL) != cudaSuccess) return bail("cudaMalloc");
-  bool okm = cudaMalloc(&g->Shi, el * LL) == cudaSuccess && cudaMalloc(&g->Y, sizeof(float2) * LB) == cudaSuccess &&
+  const size_t planes = split ? 2 : 1;  // hi and lo parts back to back (one allocation each)
+  bool okm = cudaMalloc(&g->Shi, planes * el * LL) == cudaSuccess && cudaMalloc(&g->Y, sizeof(float2) * LB) == cudaSuccess &&
              cudaMalloc(&g->ACC, sizeof(float2) * LB) == cudaSuccess &&
              cudaMalloc(&g->G, sizeof(float) * LC) == cudaSuccess &&
              cudaMalloc(&g->dSolves, sizeof(GemmSolve) * count) == cudaSuccess &&
              cudaMalloc(&g->status, sizeof(int)) == cudaSuccess;
-  for (int b = 0; b < 2 && okm; ++b) okm = cudaMalloc(&g->Xhi[b], el * LC) == cudaSuccess;
+  for (int b = 0; b < 2 && okm; ++b) okm = cudaMalloc(&g->Xhi[b], planes * el * LC) == cudaSuccess;
   if (okm && split) {
-    okm = cudaMalloc(&g->Slo, el * LL) == cudaSuccess;
-    for (int b = 0; b < 2 && okm; ++b) okm = cudaMalloc(&g->Xlo[b], el * LC) == cudaSuccess;
+    g->Slo = static_cast<uint8_t*>(g->Shi) + el * LL;
+    for (int b = 0; b < 2; ++b) g->Xlo[b] = static_cast<uint8_t*>(g->Xhi[b]) + el * LC;
   }
   if (!okm) {
     cudaFree(S32);
     return bail("cudaMalloc");
   }
-  for (int b = 0; b < 2; ++b) {  // padding columns must read as zero
-    cudaMemset(g->Xhi[b], 0, el * LC);
-    if (g->Xlo[b]) cudaMemset(g->Xlo[b], 0, el * LC);
-  }
+  for (int b = 0; b < 2; ++b) cudaMemset(g->Xhi[b], 0, planes * el * LC);  // padding columns must read as zero
   cudaMemset(g->status, 0, sizeof(int));
   // the DST-I matrix in FP64, rounded once (symmetric; row and column 0 are the zero pads)
   std::vector<float> S(LL);
@@ -641,10 +744,9 @@ pe_status pe_gemm_batch_create(pe_gemm_batch** out, pe_plan** plans, int count, 
   cudaFree(S32);
   if (cudaGetLastError() != cudaSuccess) return bail("split");
   if (mode != PE_GEMM_FP32) {
-    bool okt = make_map(&g->mS[0], g->Shi, bf16, L, L, kBM) && make_map(&g->mS[1], split ? g->Slo : g->Shi, bf16, L, L, kBM);
+    bool okt = make_map(&g->mS, g->Shi, bf16, L, L, kBM, int(planes), el * LL);
     for (int b = 0; b < 2 && okt; ++b)
-      okt = make_map(&g->mX[b][0], g->Xhi[b], bf16, L, size_t(g->C), kBN) &&
-            make_map(&g->mX[b][1], split ? g->Xlo[b] : g->Xhi[b], bf16, L, size_t(g->C), kBN);
+      okt = make_map(&g->mX[b], g->Xhi[b], bf16, L, size_t(g->C), kBN, int(planes), el * LC);
     if (!okt) return bail("tensor map (cuTensorMapEncodeTiled)");
   }
   std::vector<GemmSolve> sv(count);
@@ -694,10 +796,9 @@ pe_status pe_gemm_batch_march(pe_gemm_batch* g, int steps) {
 
 pe_status pe_gemm_batch_read_field(pe_gemm_batch* g, int index, float* out) {
   if (!g || !out || index < 0 || index >= g->B) return PE_ERR_ARG;
-  const size_t tot = size_t(g->L) * g->B;
   ElemArgs a = elem_args(g, 0, 0);
   a.scale = float(2.0 / double(g->L));
-  stage_out(g, a, int((tot + 255) / 256));
+  stage_out(g, a);
   const unsigned long long keep = g->gemms_per_step;
   cudaError_t e = launch_gemm(g, kEpiOut, 0, 0);
   g->gemms_per_step = keep;
@@ -726,12 +827,8 @@ void pe_gemm_batch_destroy(pe_gemm_batch* g) {
   if (g->stream) cudaStreamSynchronize(g->stream);
   if (g->step_graph) cudaGraphExecDestroy(g->step_graph);
   cudaFree(g->dSolves);
-  cudaFree(g->Shi);
-  cudaFree(g->Slo);
-  for (int b = 0; b < 2; ++b) {
-    cudaFree(g->Xhi[b]);
-    cudaFree(g->Xlo[b]);
-  }
+  cudaFree(g->Shi);  // the lo planes live in the same allocations
+  for (int b = 0; b < 2; ++b) cudaFree(g->Xhi[b]);
   cudaFree(g->Y);
   cudaFree(g->ACC);
   cudaFree(g->G);
