@@ -617,13 +617,14 @@ def test_gemm_dst_precisions(sssp):
     assert errs["tf32"] > errs["3xtf32"]
 
 
-# Full-length error of the tensor-core splits (measured on the GB300, worst of the 8 stored members):
-# BF16x3 7.4e-3 field / 0.14 dB TL, 3xTF32 1.4e-2 / 0.26 dB.  They do not reach the 1e-4 bar
-# over 2000 steps: each transform carries a systematic error (the BF16 representation of S,
-# 2e-6 relative, and the tensor-core accumulation, ~2.6e-6 per transform where exact
-# accumulation of the same 3xTF32 operands gives 7e-8) that adds up coherently over ~2.6e5
-# transforms.  The bounds below guard these figures against regressions.
-GEMM_FULL_BOUNDS = {"bf16x3": (1.5e-2, 0.25), "3xtf32": (3e-2, 0.5)}
+# Full-length error of the tensor-core splits (measured on the GB300, worst of the 8 stored members,
+# K split in two halves summed in FP32): BF16x3 3.5e-3 field / 0.054 dB TL, 3xTF32 7.1e-3 / 0.11 dB
+# (7.4e-3 / 0.14 and 1.4e-2 / 0.26 with one accumulator over the whole of K).  They do not reach
+# the 1e-4 bar over 2000 steps: each transform carries a systematic error (the BF16
+# representation of S, 2e-6 relative, and the tensor-core accumulation, ~2.6e-6 per transform
+# where exact accumulation of the same 3xTF32 operands gives 7e-8) that adds up coherently over
+# ~2.6e5 transforms.  The bounds below (twice the measured figures) guard them against regressions.
+GEMM_FULL_BOUNDS = {"bf16x3": (7e-3, 0.11), "3xtf32": (1.5e-2, 0.23)}
 
 
 @pytest.mark.parametrize("mode", ["bf16x3", "3xtf32"])
