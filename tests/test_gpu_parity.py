@@ -1127,6 +1127,16 @@ def test_cta_shapes_match_oracle_and_default(sssp, ppt):
         assert out[8][2] == out[ppt][2], (N, out[8][2], out[ppt][2])
 
 
+@pytest.mark.parametrize("N", [7, 15, 31, 63, 127, 255, 511])
+def test_cta_march_small_grids_against_oracle(sssp, N):
+    """The one-CTA march on every small grid (each L = N + 1 takes its own pass chain: register
+    twiddles and operands for L <= 1024, a fused final radix-2 pass where the chain ends with
+    one), a Munk march of 30 steps against the oracle's product form."""
+    s = inputs.munk(N=N, freq=20.0, dr=25.0, steps=30, pade_order=4)
+    u, tl, _, _ = _gpu(sssp, s, tl_every=3, kernel="cta")
+    _compare(u, tl, _oracle(s, tl_every=3))
+
+
 def test_shape_rejected_where_unsupported(sssp):
     pl = sssp.Plan(65535, 5000.0, 0.2, 25.0, 4)
     with pytest.raises(sssp.PEError):
