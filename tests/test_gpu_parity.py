@@ -1131,8 +1131,11 @@ def test_cta_shapes_match_oracle_and_default(sssp, ppt):
 def test_cta_march_small_grids_against_oracle(sssp, N):
     """The one-CTA march on every small grid (each L = N + 1 takes its own pass chain: register
     twiddles and operands for L <= 1024, a fused final radix-2 pass where the chain ends with
-    one), a Munk march of 30 steps against the oracle's product form."""
-    s = inputs.munk(N=N, freq=20.0, dr=25.0, steps=30, pade_order=4)
+    one), a Munk march of 30 steps against the oracle's product form.  The source sits on the
+    grid point nearest 1000 m: on the coarsest grids (625 m spacing at N = 7) a Gaussian of width
+    1/k0 ~ 12 m centred between points underflows FP32 at every grid point."""
+    dz = 5000.0 / (N + 1)
+    s = inputs.munk(N=N, freq=20.0, dr=25.0, steps=30, pade_order=4, zs=round(1000.0 / dz) * dz)
     u, tl, _, _ = _gpu(sssp, s, tl_every=3, kernel="cta")
     _compare(u, tl, _oracle(s, tl_every=3))
 
