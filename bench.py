@@ -526,6 +526,11 @@ def bench_other(args):
         plans.append(pl)
     u0s = [torch.from_numpy(s.u0.astype(np.complex64)).cuda() for s in solves]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    tune = None
+    if args.tune:  # the library's shape autotuner over every shape these solves can take
+        for pl, u0 in zip(plans, u0s):
+            pl.set_field(u0, 0.0)
+        tune = sssp.autotune_batch(plans, steps=4)
 
     def one():
         for pl, u0 in zip(plans, u0s):
@@ -558,8 +563,8 @@ def bench_other(args):
             "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64", "data": "synthetic",
             "config": {"workload": args.workload, "solves": len(solves), "N": [s.N for s in solves][:1],
-                       "kernel": plans[0].kernel,
-                       "range_steps": steps},
+                       "kernel": plans[0].kernel, "cluster_shape": plans[0].cluster_shape,
+                       "range_steps": steps, "autotune": tune},
             "dst_per_step": (nd1 - nd0) / args.steps, "clocks": clk}
     if args.workload == "large":
         # algorithmic bytes of a transform of length L = N + 1: two global passes of 16 B per point
@@ -954,6 +959,8 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tune", action="store_true",
+                    help="eddy / large / iso workloads: run the shape autotuner before timing")
     ap.add_argument("--gemm-fp32-steps", type=int, default=2000)
     ap.add_argument("--chunk-steps", type=int, default=50)
     ap.add_argument("--serve-baseline", action="store_true")

@@ -250,6 +250,22 @@ pe_status pe_plan_set_kernel(pe_plan* plan, int kernel);
 pe_status pe_plan_get_kernel(const pe_plan* plan, int* kernel);
 
 /*
+ * Shape of the cluster kernel (no counterpart in the paper): ncta CTAs per cluster — 0 for the
+ * size's default (8; 16 at N + 1 = 32768), or 16 for N + 1 = 8192 and 16384 — and how each
+ * transform's all-to-all exchange moves the values between the CTAs: push = 1 by remote stores
+ * before the cluster barrier, 0 by remote loads after it, -1 the size's default (pull at
+ * N + 1 = 4096, push from 8192 on).  The exchange mode does not change the arithmetic (the
+ * results are bitwise the same); the cluster size changes how each transform is split, so the
+ * results agree to FP32 rounding.  The shape applies whenever a march of the plan runs the
+ * cluster kernel; batched marches group solves by it.  PE_ERR_ARG for a shape the plan (Dirichlet
+ * grids with N + 1 in [4096, 32768]) or the device cannot take.  pe_plan_get_cluster_shape
+ * reports the shape a cluster march of the plan takes (ncta 0 and push -1 for plans the cluster
+ * kernel does not take).
+ */
+pe_status pe_plan_set_cluster_shape(pe_plan* plan, int ncta, int push);
+pe_status pe_plan_get_cluster_shape(const pe_plan* plan, int* ncta, int* push);
+
+/*
  * Depth operator of a plan.  PE_OP_SPECTRAL (default): the paper's DST-I diagonalisation with the
  * continuous eigenvalues and the Neumann series for V (Section 3).  PE_OP_FD3: FD-SSP, the
  * comparison of Section 4.3 and the FD-SSP remark of Section 2 — the same product-form Pade
@@ -277,17 +293,22 @@ pe_status pe_plan_get_shape(const pe_plan* plan, int* points_per_thread);
 /*
  * Shape autotuners (no counterpart in the paper).  pe_march_batch_autotune times `steps` range
  * steps of the batched march of `plans` (pe_march_batch) with each shape the plans can take —
- * one CTA per solve at 4, 8 and 16 points per thread, and one thread-block cluster per solve —
+ * one CTA per solve at 4, 8 and 16 points per thread, and one thread-block cluster per solve in
+ * each cluster shape (pe_plan_set_cluster_shape) —
  * a warm-up run then a timed run each, restores every plan's state and TL bookkeeping after each
  * run, and sets the fastest shape on every plan that can take it; it then measures every plan's
  * DST-I count per step on that shape (one more run, restored), and later batched marches launch
  * each group's solves in descending cost (heavy and light solves share SMs; the results do not
- * depend on the order).  ms: 4 floats, the timed
- * milliseconds of (CTA P=4, CTA P=8, CTA P=16, cluster), -1 where no plan can take the shape, or
- * NULL; kernel / points_per_thread: the shape chosen, or NULL.  pe_plan_autotune_shapes is the
+ * depend on the order).  ms: PE_AUTOTUNE_SHAPES floats, the timed milliseconds of (CTA P=4,
+ * CTA P=8, CTA P=16, cluster of the default size pulling, the same pushing, 16-CTA cluster
+ * pulling, the same pushing), -1 where no plan can take the shape (a 16-CTA entry is -1 where
+ * 16 is the default size: the default-size entries time it), or NULL; kernel /
+ * points_per_thread: the shape chosen (pe_plan_get_cluster_shape gives the cluster shape set),
+ * or NULL.  pe_plan_autotune_shapes is the
  * same for one plan.  Plans need a field (and a profile when Neumann terms are asked for);
  * synchronises.
  */
+enum { PE_AUTOTUNE_SHAPES = 7 };
 pe_status pe_march_batch_autotune(pe_plan** plans, int count, int steps, float* ms, int* kernel,
                                   int* points_per_thread);
 pe_status pe_plan_autotune_shapes(pe_plan* plan, int steps, float* ms, int* kernel, int* points_per_thread);

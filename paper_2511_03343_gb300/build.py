@@ -20,7 +20,7 @@ LIB = os.path.join(BUILD, "libsssp.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["sssp_abi.cu", "sssp_cluster.cu", "sssp_shapes.cu", "sssp_fd.cu", "sssp_noalloc.cu", "sssp_gemm.cu"]
+CUDA_SOURCES = ["sssp_abi.cu", "sssp_cluster.cu", "sssp_cluster_shapes.cu", "sssp_shapes.cu", "sssp_fd.cu", "sssp_noalloc.cu", "sssp_gemm.cu"]
 CXX_SOURCES = ["pade_host.cpp", "sssp_server.cpp"]
 
 

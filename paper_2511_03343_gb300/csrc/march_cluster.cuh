@@ -18,7 +18,7 @@
 //   X[k1 + M k2] = sum_r w_R^{r k2} (w_L^{r k1} FFT_M(row r)[k1]).
 // CTA j owns k1 in [jQ, (j+1)Q), Q = M/NCTA: the twiddled FFT outputs reach the CTA owning
 // their k1 (the one all-to-all exchange of a transform) either pushed by remote stores before
-// the barrier or pulled by remote loads after it (CCfg::PUSH); the owner keeps the
+// the barrier or pulled by remote loads after it (template flag PUSH); the owner keeps the
 // outputs k = k1 + M k2 < L/2 (k2 < R/2): spectral layout, thread (k1', e, h) owning
 // S_{2(k1 + M k2) + e} for k2 in [h R/4, (h+1) R/4).  The R-point DFT of a thread pair is
 // split by residue parity: thread h transforms the R/2 residues of parity h and the pair swaps
@@ -37,7 +37,7 @@
 
 namespace sssp {
 
-template <int LOG2L, int NCTA>
+template <int LOG2L, int NCTA, bool PUSH>
 struct CCfg {
   static constexpr int L = 1 << LOG2L;
   static constexpr int R = 2 * NCTA;
@@ -53,9 +53,6 @@ struct CCfg {
   static constexpr int PAD4 = P4 + P4 / 16;
   static constexpr int NW = NT / 32;
   static constexpr int DV = 2 * M / NT;   // depth points per thread in element-wise loops
-  // exchange by remote stores (push) or remote loads (pull): push measured faster from
-  // L = 8192 on (eddy N = 16383: 2.84 s against 3.12 s), pull at L = 4096 (312 ms against 320 ms)
-  static constexpr bool PUSH = LOG2L >= 13;
   // bufA, bufB, E0, E1 (padded) | X, wL rows, c rows (2M each) | twM (M) | wR (H)
   // | part (2 parities x NCTA CTA partials of the stop test) | V rows (2M floats) | red (2 NW)
   static constexpr size_t SMEM =
@@ -65,12 +62,12 @@ struct CCfg {
   static_assert(NT >= 32 && NT % 32 == 0 && M >= 64, "grid too small for this cluster");
 };
 
-template <int LOG2L, int NCTA>
+template <int LOG2L, int NCTA, bool PUSH>
 struct CSmem {
   float2 *bufA, *bufB, *E[2], *X, *wLs, *cs, *twM, *wR, *part;
   float *Vs, *red, *Vis;
   __device__ __forceinline__ explicit CSmem(unsigned char* base) {
-    using C = CCfg<LOG2L, NCTA>;
+    using C = CCfg<LOG2L, NCTA, PUSH>;
     bufA = reinterpret_cast<float2*>(base);
     bufB = bufA + C::PAD4;
     E[0] = bufB + C::PAD4;
@@ -154,15 +151,15 @@ struct StBuf {
 // last forward pass: twiddle w_L^{r k1} of the row, pushed into the exchange area of the CTA
 // that owns k1, at ((2 r + e) Q + k1 - its first k1)
 // (pull: into this CTA's own area at (f M + k1), read by the owner of k1 after the barrier)
-template <int LOG2L, int NCTA>
+template <int LOG2L, int NCTA, bool PUSH>
 struct StExch {
   float2* E;  // this CTA's exchange area (mapped to the owner per store when pushing)
   const float2* wLs;
   int j;
   __device__ __forceinline__ void operator()(int f, int o, float2 v) const {
-    using C = CCfg<LOG2L, NCTA>;
+    using C = CCfg<LOG2L, NCTA, PUSH>;
     const float2 w = cmul(v, wLs[(f >> 1) * C::M + o]);
-    if constexpr (C::PUSH) {
+    if constexpr (PUSH) {
       const int r = res_of<NCTA>(j, f >> 1);
       float2* Eo = cooperative_groups::this_cluster().map_shared_rank(E, o >> C::LOG2Q);
       Eo[pidx((2 * r + (f & 1)) * C::Q + (o & (C::Q - 1)))] = w;
@@ -197,7 +194,7 @@ __device__ __forceinline__ float2 mul_ihalf(float2 x) { return make_float2(-0.5f
 
 // Forward pre-processing loader (first pass): u or v of the depth values X (times V when
 // WITHV) for FFT f = 2 row + e.
-template <int LOG2L, int NCTA, bool WITHV, bool CPLX>
+template <int LOG2L, int NCTA, bool PUSH, bool WITHV, bool CPLX>
 struct LdPre {
   const float2* X;
   const float* Vs;
@@ -211,7 +208,7 @@ struct LdPre {
     else return Vs[p] * x;
   }
   __device__ __forceinline__ float2 operator()(int f, int m) const {
-    constexpr int M = CCfg<LOG2L, NCTA>::M;
+    constexpr int M = CCfg<LOG2L, NCTA, PUSH>::M;
     const int row = f >> 1;
     const int p = row * M + m;
     const float2 x = val(p), xm = val(mirror_pos<M>(j, row, m));
@@ -222,15 +219,15 @@ struct LdPre {
 // Inverse first pass: the values the other CTAs pushed for residue row f >> 1, term f & 1, at
 // (f M + k1) of this CTA's exchange area, times w_L^{r k1}.
 // (pull: read from the area of the CTA owning k1, at ((2 r + e) Q + k1 - its first k1))
-template <int LOG2L, int NCTA>
+template <int LOG2L, int NCTA, bool PUSH>
 struct LdExch {
   const float2* E;
   const float2* wLs;
   int j;
   __device__ __forceinline__ float2 operator()(int f, int k1) const {
-    using C = CCfg<LOG2L, NCTA>;
+    using C = CCfg<LOG2L, NCTA, PUSH>;
     float2 z;
-    if constexpr (C::PUSH) {
+    if constexpr (PUSH) {
       z = E[pidx(f * C::M + k1)];
     } else {
       const int r = res_of<NCTA>(j, f >> 1);
@@ -242,34 +239,34 @@ struct LdExch {
 };
 
 // thread's spectral coordinates
-template <int LOG2L, int NCTA>
+template <int LOG2L, int NCTA, bool PUSH>
 struct Spec {
   int h, e, k1;  // k1: global
   __device__ __forceinline__ Spec(int j) {
-    using C = CCfg<LOG2L, NCTA>;
+    using C = CCfg<LOG2L, NCTA, PUSH>;
     const int t = threadIdx.x;
     h = t & 1;
     e = (t >> 1) & 1;
     k1 = j * C::Q + (t >> 2);
   }
   __device__ __forceinline__ int mode(int s) const {
-    using C = CCfg<LOG2L, NCTA>;
+    using C = CCfg<LOG2L, NCTA, PUSH>;
     return 2 * (k1 + C::M * (h * C::SV + s)) + e;
   }
 };
 
 // Forward DST-I of the depth values in X (times V when WITHV): out[s] = S at sp.mode(s).
 // Uses bufA, bufB and the exchange area of parity ph (one cluster barrier; ph advances).
-template <int LOG2L, int NCTA, bool WITHV, bool CPLX>
-__device__ __forceinline__ void cdst_fwd(CSmem<LOG2L, NCTA>& sm, int j, const Spec<LOG2L, NCTA>& sp, int& ph,
-                                         float2 (&out)[CCfg<LOG2L, NCTA>::SV]) {
-  using C = CCfg<LOG2L, NCTA>;
+template <int LOG2L, int NCTA, bool PUSH, bool WITHV, bool CPLX>
+__device__ __forceinline__ void cdst_fwd(CSmem<LOG2L, NCTA, PUSH>& sm, int j, const Spec<LOG2L, NCTA, PUSH>& sp, int& ph,
+                                         float2 (&out)[CCfg<LOG2L, NCTA, PUSH>::SV]) {
+  using C = CCfg<LOG2L, NCTA, PUSH>;
   constexpr int M = C::M;
   float2* E = sm.E[ph & 1];
-  cpass<C::LOG2M, C::NT, 8, 1>(LdPre<LOG2L, NCTA, WITHV, CPLX>{sm.X, sm.Vs, sm.Vis, sm.cs, j}, StBuf<M>{sm.bufA},
+  cpass<C::LOG2M, C::NT, 8, 1>(LdPre<LOG2L, NCTA, PUSH, WITHV, CPLX>{sm.X, sm.Vs, sm.Vis, sm.cs, j}, StBuf<M>{sm.bufA},
                               sm.twM);
   __syncthreads();
-  cfft_rest<C::LOG2M, C::NT, 8>(sm.bufA, sm.bufB, sm.twM, StExch<LOG2L, NCTA>{E, sm.wLs, j});
+  cfft_rest<C::LOG2M, C::NT, 8>(sm.bufA, sm.bufB, sm.twM, StExch<LOG2L, NCTA, PUSH>{E, sm.wLs, j});
   cooperative_groups::this_cluster().sync();  // the pushed values are visible after it
   ++ph;
   // R-point DFT across residues, split by residue parity over the thread pair (h = 0, 1)
@@ -277,7 +274,7 @@ __device__ __forceinline__ void cdst_fwd(CSmem<LOG2L, NCTA>& sm, int j, const Sp
   const int k1l = sp.k1 & (C::Q - 1);
 #pragma unroll
   for (int s = 0; s < C::H; ++s) {
-    if constexpr (C::PUSH) {
+    if constexpr (PUSH) {
       D[s] = E[pidx((2 * (2 * s + sp.h) + sp.e) * C::Q + k1l)];
     } else {
       int own, row;
@@ -306,10 +303,10 @@ constexpr int kSinkField = 2;  // the physical envelope in global memory
 
 // First half of the inverse DST-I: from the spectral values in[s] (at sp.mode(s)), the
 // transposed R-point DFTs into the exchange area of parity ph; then the cluster barrier.
-template <int LOG2L, int NCTA>
-__device__ __forceinline__ void cdst_inv_begin(CSmem<LOG2L, NCTA>& sm, const Spec<LOG2L, NCTA>& sp, int& ph,
-                                               const float2 (&in)[CCfg<LOG2L, NCTA>::SV]) {
-  using C = CCfg<LOG2L, NCTA>;
+template <int LOG2L, int NCTA, bool PUSH>
+__device__ __forceinline__ void cdst_inv_begin(CSmem<LOG2L, NCTA, PUSH>& sm, const Spec<LOG2L, NCTA, PUSH>& sp, int& ph,
+                                               const float2 (&in)[CCfg<LOG2L, NCTA, PUSH>::SV]) {
+  using C = CCfg<LOG2L, NCTA, PUSH>;
   float2* E = sm.E[ph & 1];
   float2 W[C::H];
 #pragma unroll
@@ -330,7 +327,7 @@ __device__ __forceinline__ void cdst_inv_begin(CSmem<LOG2L, NCTA>& sm, const Spe
   const int k1l = sp.k1 & (C::Q - 1);
 #pragma unroll
   for (int s = 0; s < C::H; ++s) {
-    if constexpr (C::PUSH) {
+    if constexpr (PUSH) {
       int own, row;
       owner_of<NCTA>(2 * s + sp.h, own, row);
       cl.map_shared_rank(E, own)[pidx((2 * row + sp.e) * C::M + sp.k1)] = W[s];
@@ -344,12 +341,12 @@ __device__ __forceinline__ void cdst_inv_begin(CSmem<LOG2L, NCTA>& sm, const Spe
 
 // Second half: gather this CTA's residue rows from the exchange area written before the last
 // barrier (parity ph - 1), local FFTs, transposed pre-processing into the sink.
-template <int LOG2L, int NCTA, int SINK>
-__device__ __forceinline__ void cdst_inv_end(CSmem<LOG2L, NCTA>& sm, int j, int ph, float2* fout, float* tlrow,
+template <int LOG2L, int NCTA, bool PUSH, int SINK>
+__device__ __forceinline__ void cdst_inv_end(CSmem<LOG2L, NCTA, PUSH>& sm, int j, int ph, float2* fout, float* tlrow,
                                              float lr) {
-  using C = CCfg<LOG2L, NCTA>;
+  using C = CCfg<LOG2L, NCTA, PUSH>;
   constexpr int M = C::M;
-  cpass<C::LOG2M, C::NT, 8, 1>(LdExch<LOG2L, NCTA>{sm.E[(ph - 1) & 1], sm.wLs, j}, StBuf<M>{sm.bufA}, sm.twM);
+  cpass<C::LOG2M, C::NT, 8, 1>(LdExch<LOG2L, NCTA, PUSH>{sm.E[(ph - 1) & 1], sm.wLs, j}, StBuf<M>{sm.bufA}, sm.twM);
   __syncthreads();
   constexpr bool inA = CPasses<C::LOG2M>::LAST_IN_A;
   float2* F = inA ? sm.bufA : sm.bufB;
@@ -378,11 +375,11 @@ __device__ __forceinline__ void cdst_inv_end(CSmem<LOG2L, NCTA>& sm, int j, int 
   if constexpr (SINK == kSinkX) __syncthreads();
 }
 
-template <int LOG2L, int NCTA>
-__device__ __forceinline__ void cload_tables(CSmem<LOG2L, NCTA>& sm, int j, const float2* __restrict__ twM_g,
+template <int LOG2L, int NCTA, bool PUSH>
+__device__ __forceinline__ void cload_tables(CSmem<LOG2L, NCTA, PUSH>& sm, int j, const float2* __restrict__ twM_g,
                                              const float2* __restrict__ wL_g, const float2* __restrict__ c_g,
                                              const float2* __restrict__ wR_g) {
-  using C = CCfg<LOG2L, NCTA>;
+  using C = CCfg<LOG2L, NCTA, PUSH>;
   for (int i = threadIdx.x; i < 2 * C::M; i += C::NT) {
     const int row = i >> C::LOG2M, m = i & (C::M - 1);
     const int r = res_of<NCTA>(j, row);
@@ -393,9 +390,9 @@ __device__ __forceinline__ void cload_tables(CSmem<LOG2L, NCTA>& sm, int j, cons
   for (int i = threadIdx.x; i < C::H; i += C::NT) sm.wR[i] = wR_g[i];
 }
 
-template <int LOG2L, int NCTA, bool CPLX>
-__device__ __forceinline__ void cload_V(CSmem<LOG2L, NCTA>& sm, int j, const SolveDesc& d, int node) {
-  using C = CCfg<LOG2L, NCTA>;
+template <int LOG2L, int NCTA, bool PUSH, bool CPLX>
+__device__ __forceinline__ void cload_V(CSmem<LOG2L, NCTA, PUSH>& sm, int j, const SolveDesc& d, int node) {
+  using C = CCfg<LOG2L, NCTA, PUSH>;
   const float* Vg = d.V + (size_t)node * C::L;
   const float* Vig = CPLX ? d.Vi + (size_t)node * C::L : nullptr;
   for (int i = threadIdx.x; i < 2 * C::M; i += C::NT) {
@@ -409,15 +406,15 @@ __device__ __forceinline__ void cload_V(CSmem<LOG2L, NCTA>& sm, int j, const Sol
 // ---------------------------------------------------------------------------------------
 // The persistent cluster march: cluster blockIdx.x / NCTA marches solve descs[that].
 // ---------------------------------------------------------------------------------------
-template <int LOG2L, int NCTA, bool CPLX>
-__global__ void __launch_bounds__(CCfg<LOG2L, NCTA>::NT, 1)
+template <int LOG2L, int NCTA, bool PUSH, bool CPLX>
+__global__ void __launch_bounds__(CCfg<LOG2L, NCTA, PUSH>::NT, 1)
     sssp_march_cluster_kernel(const SolveDesc* __restrict__ descs, const float2* __restrict__ twM_g,
                               const float2* __restrict__ wL_g, const float2* __restrict__ c_g,
                               const float2* __restrict__ wR_g) {
-  using C = CCfg<LOG2L, NCTA>;
+  using C = CCfg<LOG2L, NCTA, PUSH>;
   constexpr int SV = C::SV;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CSmem<LOG2L, NCTA> sm(smem_raw);
+  CSmem<LOG2L, NCTA, PUSH> sm(smem_raw);
   __shared__ SolveDesc d;
   cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
   const int j = int(cl.block_rank());
@@ -428,9 +425,9 @@ __global__ void __launch_bounds__(CCfg<LOG2L, NCTA>::NT, 1)
     int* dst = reinterpret_cast<int*>(&d);
     for (int i = t; i < int(sizeof(SolveDesc) / sizeof(int)); i += C::NT) dst[i] = src[i];
   }
-  cload_tables<LOG2L, NCTA>(sm, j, twM_g, wL_g, c_g, wR_g);
+  cload_tables<LOG2L, NCTA, PUSH>(sm, j, twM_g, wL_g, c_g, wR_g);
   __syncthreads();
-  const Spec<LOG2L, NCTA> sp(j);
+  const Spec<LOG2L, NCTA, PUSH> sp(j);
   float2 y[SV];
 #pragma unroll
   for (int s = 0; s < SV; ++s) y[s] = d.yhat[sp.mode(s)];
@@ -443,16 +440,16 @@ __global__ void __launch_bounds__(CCfg<LOG2L, NCTA>::NT, 1)
   int ph = 0;
   int node = d.node0;
   double next_r = (node + 1 < d.nodes) ? d.node_r[node + 1] : 1e300;
-  if (!iso) cload_V<LOG2L, NCTA, CPLX>(sm, j, d, node);
+  if (!iso) cload_V<LOG2L, NCTA, PUSH, CPLX>(sm, j, d, node);
   __syncthreads();
 
   auto record = [&](int s) {
     float2 o[SV];
 #pragma unroll
     for (int i = 0; i < SV; ++i) o[i] = out_scale * y[i];
-    cdst_inv_begin<LOG2L, NCTA>(sm, sp, ph, o);
+    cdst_inv_begin<LOG2L, NCTA, PUSH>(sm, sp, ph, o);
     const float lr = float(10.0 * log10(d.r0 + double(s + 1) * d.dr));
-    cdst_inv_end<LOG2L, NCTA, kSinkTL>(sm, j, ph, nullptr, d.tl + (size_t)(d.rec0 + nrec) * d.N, lr);
+    cdst_inv_end<LOG2L, NCTA, PUSH, kSinkTL>(sm, j, ph, nullptr, d.tl + (size_t)(d.rec0 + nrec) * d.N, lr);
     ++ndst;
     ++nrec;
   };
@@ -473,7 +470,7 @@ __global__ void __launch_bounds__(CCfg<LOG2L, NCTA>::NT, 1)
       if (rmid >= next_r) {
         while (node + 1 < d.nodes && d.node_r[node + 1] <= rmid) ++node;
         next_r = (node + 1 < d.nodes) ? d.node_r[node + 1] : 1e300;
-        cload_V<LOG2L, NCTA, CPLX>(sm, j, d, node);  // read after the barriers of the stage's first transform
+        cload_V<LOG2L, NCTA, PUSH, CPLX>(sm, j, d, node);  // read after the barriers of the stage's first transform
       }
       for (int jj = 0; jj < d.p && status == kStatusOk; ++jj) {
         float2 acc[SV], tp[SV], t0[SV], Bj[SV];
@@ -484,12 +481,12 @@ __global__ void __launch_bounds__(CCfg<LOG2L, NCTA>::NT, 1)
           t0[i] = cmul(d.A[(size_t)jj * C::L + md], y[i]);
           acc[i] = make_float2(0.f, 0.f);
         }
-        cdst_inv_begin<LOG2L, NCTA>(sm, sp, ph, t0);
-        cdst_inv_end<LOG2L, NCTA, kSinkX>(sm, j, ph, nullptr, nullptr, 0.f);  // t_0 in depth space
+        cdst_inv_begin<LOG2L, NCTA, PUSH>(sm, sp, ph, t0);
+        cdst_inv_end<LOG2L, NCTA, PUSH, kSinkX>(sm, j, ph, nullptr, nullptr, 0.f);  // t_0 in depth space
         ++ndst;
         float first = 0.f;
         for (int m = 1; m < d.terms; ++m) {
-          cdst_fwd<LOG2L, NCTA, true, CPLX>(sm, j, sp, ph, tp);  // T(V t_{m-1})
+          cdst_fwd<LOG2L, NCTA, PUSH, true, CPLX>(sm, j, sp, ph, tp);  // T(V t_{m-1})
           ++ndst;
           float nt = 0.f, nw = 0.f;
 #pragma unroll
@@ -521,7 +518,7 @@ __global__ void __launch_bounds__(CCfg<LOG2L, NCTA>::NT, 1)
             }
             if (lane < NCTA) cl.map_shared_rank(sm.part, lane)[pbase + j] = make_float2(a, b);
           }
-          cdst_inv_begin<LOG2L, NCTA>(sm, sp, ph, tp);  // (its cluster barrier publishes part)
+          cdst_inv_begin<LOG2L, NCTA, PUSH>(sm, sp, ph, tp);  // (its cluster barrier publishes part)
           float snt = 0.f, snw = 0.f;
           for (int c = 0; c < NCTA; ++c) {
             const float2 pc = sm.part[pbase + c];
@@ -538,7 +535,7 @@ __global__ void __launch_bounds__(CCfg<LOG2L, NCTA>::NT, 1)
             break;
           }
           if (neumann_stop_fast(snt, snw, d.tol2, tol2f)) break;
-          cdst_inv_end<LOG2L, NCTA, kSinkX>(sm, j, ph, nullptr, nullptr, 0.f);  // t_m in depth space
+          cdst_inv_end<LOG2L, NCTA, PUSH, kSinkX>(sm, j, ph, nullptr, nullptr, 0.f);  // t_m in depth space
           ++ndst;
         }
         const float2 bj = d.beta[jj];
@@ -559,8 +556,8 @@ __global__ void __launch_bounds__(CCfg<LOG2L, NCTA>::NT, 1)
     float2 o[SV];
 #pragma unroll
     for (int i = 0; i < SV; ++i) o[i] = out_scale * y[i];
-    cdst_inv_begin<LOG2L, NCTA>(sm, sp, ph, o);
-    cdst_inv_end<LOG2L, NCTA, kSinkField>(sm, j, ph, d.field, nullptr, 0.f);
+    cdst_inv_begin<LOG2L, NCTA, PUSH>(sm, sp, ph, o);
+    cdst_inv_end<LOG2L, NCTA, PUSH, kSinkField>(sm, j, ph, d.field, nullptr, 0.f);
     ++ndst;
   }
   if (t == 0 && j == 0) {
@@ -572,31 +569,31 @@ __global__ void __launch_bounds__(CCfg<LOG2L, NCTA>::NT, 1)
 
 // DST-I of one field per cluster: out = scale * DST(in); field b = blockIdx.x / NCTA reads N
 // values at in + b * in_stride (n = 1..N) and writes L values at out + b * out_stride.
-template <int LOG2L, int NCTA>
-__global__ void __launch_bounds__(CCfg<LOG2L, NCTA>::NT, 1)
+template <int LOG2L, int NCTA, bool PUSH>
+__global__ void __launch_bounds__(CCfg<LOG2L, NCTA, PUSH>::NT, 1)
     sssp_dst_cluster_kernel(const float2* __restrict__ in, float2* __restrict__ out, float scale,
                             const float2* __restrict__ twM_g, const float2* __restrict__ wL_g,
                             const float2* __restrict__ c_g, const float2* __restrict__ wR_g, long long in_stride,
                             long long out_stride) {
-  using C = CCfg<LOG2L, NCTA>;
+  using C = CCfg<LOG2L, NCTA, PUSH>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CSmem<LOG2L, NCTA> sm(smem_raw);
+  CSmem<LOG2L, NCTA, PUSH> sm(smem_raw);
   cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
   const int j = int(cl.block_rank());
   const long long b = blockIdx.x / NCTA;
   in += b * in_stride;
   out += b * out_stride;
-  cload_tables<LOG2L, NCTA>(sm, j, twM_g, wL_g, c_g, wR_g);
+  cload_tables<LOG2L, NCTA, PUSH>(sm, j, twM_g, wL_g, c_g, wR_g);
   for (int i = threadIdx.x; i < 2 * C::M; i += C::NT) {
     const int row = i >> C::LOG2M, m = i & (C::M - 1);
     const int n = res_of<NCTA>(j, row) + C::R * m;
     sm.X[i] = (n == 0) ? make_float2(0.f, 0.f) : in[n - 1];
   }
   __syncthreads();
-  const Spec<LOG2L, NCTA> sp(j);
+  const Spec<LOG2L, NCTA, PUSH> sp(j);
   int ph = 0;
   float2 o[C::SV];
-  cdst_fwd<LOG2L, NCTA, false, false>(sm, j, sp, ph, o);
+  cdst_fwd<LOG2L, NCTA, PUSH, false, false>(sm, j, sp, ph, o);
 #pragma unroll
   for (int s = 0; s < C::SV; ++s) {
     const int md = sp.mode(s);

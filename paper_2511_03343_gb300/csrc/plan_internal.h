@@ -22,6 +22,8 @@ struct pe_plan {
   int N_user = 0;   // grid points the caller sees
   int kernel = 0;   // PE_KERNEL_AUTO / PE_KERNEL_CTA / PE_KERNEL_CLUSTER
   int ppt = 8;      // points per thread of the one-CTA kernel (4, 8 or 16; pe_plan_set_shape)
+  int cl_ncta = 0;  // cluster kernel shape: CTAs per cluster (0: the size's default) and
+  int cl_push = -1; // exchange by remote stores 1 / loads 0 (-1: default; pe_plan_set_cluster_shape)
   int op = 0;       // PE_OP_SPECTRAL (the paper's DST-I operator) or PE_OP_FD3 (FD-SSP)
   float4* dFD = nullptr;   // FD-SSP: node_cap x p x L x 3 float4 Thomas factors (hi + lo)
   float4* dFDc = nullptr;  // FD-SSP: per stage hi/lo of a_j/b_j and 1 - a_j/b_j

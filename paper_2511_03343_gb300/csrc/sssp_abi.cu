@@ -399,9 +399,23 @@ bool use_cluster(const pe_plan* p, bool cplx, int group = 1) {
   if (p->bc != PE_BC_DIRICHLET || !sssp_cluster::supported(p->log2L)) return false;
   if (p->kernel == PE_KERNEL_CTA) return false;
   int clusters = 0;
-  if (sssp_cluster::max_active_clusters(p->log2L, cplx, &clusters) != cudaSuccess || clusters < 1) return false;
+  if (sssp_cluster::max_active_clusters(p->log2L, cplx, &clusters, p->cl_ncta, p->cl_push) != cudaSuccess ||
+      clusters < 1)
+    return false;
   if (p->kernel == PE_KERNEL_AUTO && p->log2L == 12 && group > clusters) return false;
   return true;
+}
+
+// The cluster shape a march of the plan takes (its own, else the size's default), as
+// (CTAs per cluster, push exchange), and as one code 2 NCTA + push for the batch's group key
+void cluster_shape_of(const pe_plan* p, int* ncta, int* push) {
+  *ncta = p->cl_ncta ? p->cl_ncta : sssp_cluster::ncta(p->log2L);
+  *push = p->cl_push >= 0 ? p->cl_push : (sssp_cluster::push_default(p->log2L) ? 1 : 0);
+}
+int cluster_code(const pe_plan* p) {
+  int n = 0, u = 0;
+  cluster_shape_of(p, &n, &u);
+  return 2 * n + u;
 }
 
 // Points per thread of the one-CTA shared-memory kernel a march of this plan runs (8 unless a
@@ -832,7 +846,8 @@ pe_status pe_march(pe_plan* p, int steps) {
   if (p->op == PE_OP_FD3) {
     PE_CUDA(p, sssp_fd::launch_march(p->log2L, p->dDesc, 1, p->stream));
   } else if (use_cluster(p, cplx)) {
-    PE_CUDA(p, sssp_cluster::launch_march(p->log2L, p->dDesc, 1, p->stream, cplx, p->device));
+    PE_CUDA(p, sssp_cluster::launch_march(p->log2L, p->dDesc, 1, p->stream, cplx, p->device, p->cl_ncta,
+                                          p->cl_push));
   } else {
     const int ppt = (p->log2L <= kMaxSmemLog2) ? shape_of(p) : 8;
     TransformTables tb;
@@ -914,13 +929,15 @@ pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
     const int group = size_count[std::make_tuple(plans[i]->log2L, plans[i]->complex_profile, plans[i]->bc)];
     const bool fd = plans[i]->op == PE_OP_FD3;  // FD-SSP plans: their own kernel (shape -1)
     const bool cl = !fd && use_cluster(plans[i], cplx, group);
-    const int ppt = fd ? -1 : ((!cl && plans[i]->log2L <= kMaxSmemLog2) ? shape_of(plans[i]) : 8);
+    // the shape slot of the group key: points per thread of the one-CTA kernel, -1 for FD-SSP, the
+    // cluster shape's code (2 NCTA + push, >= 16) for the cluster kernel
+    const int ppt = fd ? -1 : (cl ? cluster_code(plans[i]) : (plans[i]->log2L <= kMaxSmemLog2 ? shape_of(plans[i]) : 8));
     const auto key = std::make_tuple(plans[i]->log2L, cplx, plans[i]->bc, cl, ppt);
     groups[key].push_back(d);
     costs[key].push_back(plans[i]->cost);
     if (!tabs.count(key)) {
       TransformTables tb = plans[i]->tabs;
-      if (!fd) PE_CUDA(p0, tables_for(plans[i], ppt, &tb));
+      if (!fd && !cl) PE_CUDA(p0, tables_for(plans[i], ppt, &tb));
       tabs[key] = tb;
     }
   }
@@ -955,7 +972,8 @@ pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
       PE_CUDA(p0, sssp_fd::launch_march(std::get<0>(kv.first), p0->dDesc, int(kv.second.size()), p0->stream));
     else if (std::get<3>(kv.first))
       PE_CUDA(p0, sssp_cluster::launch_march(std::get<0>(kv.first), p0->dDesc, int(kv.second.size()), p0->stream,
-                                             std::get<1>(kv.first), p0->device));
+                                             std::get<1>(kv.first), p0->device, std::get<4>(kv.first) / 2,
+                                             std::get<4>(kv.first) & 1));
     else
       PE_CUDA(p0, launch_march(std::get<0>(kv.first), p0->dDesc, int(kv.second.size()), tabs[kv.first], p0->stream,
                                std::get<1>(kv.first), std::get<2>(kv.first), std::get<4>(kv.first)));
@@ -986,7 +1004,8 @@ pe_status pe_march_batch_steps(pe_plan** plans, const int* steps, int count) {
       PE_CUDA(p0, sssp_fd::launch_march(std::get<0>(kv.first), dd, int(kv.second.size()), st));
     else if (std::get<3>(kv.first))
       PE_CUDA(p0, sssp_cluster::launch_march(std::get<0>(kv.first), dd, int(kv.second.size()), st,
-                                             std::get<1>(kv.first), p0->device));
+                                             std::get<1>(kv.first), p0->device, std::get<4>(kv.first) / 2,
+                                             std::get<4>(kv.first) & 1));
     else
       PE_CUDA(p0, launch_march(std::get<0>(kv.first), dd, int(kv.second.size()), tabs[kv.first], st,
                                std::get<1>(kv.first), std::get<2>(kv.first), std::get<4>(kv.first)));
@@ -1220,6 +1239,33 @@ pe_status pe_plan_get_shape(const pe_plan* p, int* points_per_thread) {
   return PE_OK;
 }
 
+pe_status pe_plan_set_cluster_shape(pe_plan* p, int ncta, int push) {
+  if (!p) return PE_ERR_ARG;
+  if (push < -1 || push > 1) return fail(p, PE_ERR_ARG, "push must be -1 (default), 0 (pull) or 1 (push)");
+  if (p->user_bc != PE_BC_DIRICHLET || !sssp_cluster::shape_supported(p->log2L, ncta, push))
+    return fail(p, PE_ERR_ARG,
+                "cluster shapes: Dirichlet grids with N + 1 in [4096, 32768]; ncta 0, the size's default or "
+                "16 for N + 1 in {8192, 16384}");
+  int a = 0, b = 0;
+  PE_CUDA(p, sssp_cluster::max_active_clusters(p->log2L, false, &a, ncta, push));
+  PE_CUDA(p, sssp_cluster::max_active_clusters(p->log2L, true, &b, ncta, push));
+  if (a < 1 || b < 1) return fail(p, PE_ERR_ARG, "this device cannot hold a cluster of that shape");
+  p->cl_ncta = ncta;
+  p->cl_push = push;
+  return PE_OK;
+}
+
+pe_status pe_plan_get_cluster_shape(const pe_plan* p, int* ncta, int* push) {
+  if (!p || !ncta || !push) return PE_ERR_ARG;
+  if (p->user_bc != PE_BC_DIRICHLET || !sssp_cluster::supported(p->log2L)) {
+    *ncta = 0;
+    *push = -1;
+    return PE_OK;
+  }
+  cluster_shape_of(p, ncta, push);
+  return PE_OK;
+}
+
 pe_status pe_plan_get_kernel(const pe_plan* p, int* kernel) {
   if (!p || !kernel) return PE_ERR_ARG;
   *kernel = use_cluster(p, p->complex_profile) ? PE_KERNEL_CLUSTER : PE_KERNEL_CTA;
@@ -1230,17 +1276,25 @@ pe_status pe_plan_get_kernel(const pe_plan* p, int* kernel) {
 
 namespace {
 
-// The (kernel, points per thread) shapes the autotuners search, in the order of their timing
-// outputs: one CTA at 4, 8 and 16 points per thread, then the thread-block cluster.
-constexpr int kShapes = 4;
-const int kShapeKernel[kShapes] = {PE_KERNEL_CTA, PE_KERNEL_CTA, PE_KERNEL_CTA, PE_KERNEL_CLUSTER};
-const int kShapePpt[kShapes] = {4, 8, 16, 8};
+// The shapes the autotuners search, in the order of their timing outputs: one CTA at 4, 8 and
+// 16 points per thread, then the thread-block cluster with 8 CTAs (16 at N + 1 = 32768) pulling
+// and pushing its exchange, then 16-CTA clusters (N + 1 = 8192 and 16384) pulling and pushing.
+constexpr int kShapes = PE_AUTOTUNE_SHAPES;
+const int kShapeKernel[kShapes] = {PE_KERNEL_CTA,     PE_KERNEL_CTA,     PE_KERNEL_CTA,    PE_KERNEL_CLUSTER,
+                                   PE_KERNEL_CLUSTER, PE_KERNEL_CLUSTER, PE_KERNEL_CLUSTER};
+const int kShapePpt[kShapes] = {4, 8, 16, 8, 8, 8, 8};
+const int kShapeNcta[kShapes] = {0, 0, 0, 0, 0, 16, 16};  // 0: the size's default
+const int kShapePush[kShapes] = {-1, -1, -1, 0, 1, 0, 1};
 
 bool shape_ok(const pe_plan* p, int c) {
   if (kShapeKernel[c] == PE_KERNEL_CLUSTER) {
     int clusters = 0;
-    return p->user_bc == PE_BC_DIRICHLET && sssp_cluster::supported(p->log2L) &&
-           sssp_cluster::max_active_clusters(p->log2L, p->complex_profile, &clusters) == cudaSuccess && clusters > 0;
+    const int n = kShapeNcta[c];
+    if (n != 0 && n == sssp_cluster::ncta(p->log2L)) return false;  // the same shape as ncta 0
+    return p->user_bc == PE_BC_DIRICHLET && sssp_cluster::shape_supported(p->log2L, n, kShapePush[c]) &&
+           sssp_cluster::max_active_clusters(p->log2L, p->complex_profile, &clusters, n, kShapePush[c]) ==
+               cudaSuccess &&
+           clusters > 0;
   }
   if (kShapePpt[c] == 8) return true;
   return p->bc == PE_BC_DIRICHLET && sssp_shapes::supported(p->log2L, kShapePpt[c]);
@@ -1251,7 +1305,7 @@ struct SavedMarch {
   double r_set = 0.0;
   long long steps = 0, tl_rows = 0;
   std::vector<double> tl_ranges;
-  int kernel = 0, ppt = 8;
+  int kernel = 0, ppt = 8, cl_ncta = 0, cl_push = -1;
 };
 
 pe_status save_march(pe_plan* p, SavedMarch* sv) {
@@ -1261,6 +1315,8 @@ pe_status save_march(pe_plan* p, SavedMarch* sv) {
   sv->tl_ranges = p->tl_ranges;
   sv->kernel = p->kernel;
   sv->ppt = p->ppt;
+  sv->cl_ncta = p->cl_ncta;
+  sv->cl_push = p->cl_push;
   return st;
 }
 
@@ -1299,6 +1355,10 @@ pe_status autotune_batch(pe_plan** plans, int count, int steps, float* ms, int* 
       if (shape_ok(plans[i], c)) {
         plans[i]->kernel = kShapeKernel[c];
         plans[i]->ppt = kShapePpt[c];
+        if (kShapeKernel[c] == PE_KERNEL_CLUSTER) {
+          plans[i]->cl_ncta = kShapeNcta[c];
+          plans[i]->cl_push = kShapePush[c];
+        }
       }
     float t = 0.f;
     for (int rep = 0; rep < 2 && st == PE_OK; ++rep) {  // the first run warms tables and caches
@@ -1324,9 +1384,15 @@ pe_status autotune_batch(pe_plan** plans, int count, int steps, float* ms, int* 
   for (int i = 0; i < count; ++i) {  // the previous setting, then the winner where it applies
     plans[i]->kernel = sv[size_t(i)].kernel;
     plans[i]->ppt = sv[size_t(i)].ppt;
+    plans[i]->cl_ncta = sv[size_t(i)].cl_ncta;
+    plans[i]->cl_push = sv[size_t(i)].cl_push;
     if (st == PE_OK && best_c >= 0 && shape_ok(plans[i], best_c)) {
       plans[i]->kernel = kShapeKernel[best_c];
       plans[i]->ppt = kShapePpt[best_c];
+      if (kShapeKernel[best_c] == PE_KERNEL_CLUSTER) {
+        plans[i]->cl_ncta = kShapeNcta[best_c];
+        plans[i]->cl_push = kShapePush[best_c];
+      }
     }
   }
   if (st != PE_OK) return st;

@@ -1,5 +1,6 @@
-// Host side of the cluster march (march_cluster.cuh): per-size tables, launch with the
-// cluster dimension, and the check that a cluster of this shape fits on the device.
+// Host side of the cluster march (march_cluster.cuh): per-shape tables, the default shape of
+// every size, the launch with the cluster dimension, and the check that a cluster of a shape
+// fits on the device (the other shapes are instantiated in sssp_cluster_shapes.cu).
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -8,24 +9,25 @@
 #include <utility>
 #include <vector>
 
+#include "cluster_host.cuh"
 #include "cluster_launch.h"
-#include "march_cluster.cuh"
 
 namespace {
 
-using sssp::CCfg;
-
-struct ClusterTables {
-  float2* twM = nullptr;  // per-pass Stockham twiddles of the M-point FFT
-  float2* wL = nullptr;   // R x M: w_L^{r k1}
-  float2* c = nullptr;    // R x M: e^{-i pi (r + R m)/L}
-  float2* wR = nullptr;   // R/2: w_R^{k2}
-};
+using sssp_cluster_host::ClusterTables;
+using sssp_cluster_host::dst_t;
+using sssp_cluster_host::fits_t;
+using sssp_cluster_host::march_t;
 
 std::mutex g_mu;
-std::map<std::pair<int, int>, ClusterTables> g_tabs;  // (device, log2 L)
+std::map<std::tuple<int, int, int>, ClusterTables> g_tabs;  // (device, log2 L, NCTA)
 
+// The default shape of each size: 8 CTAs (16 at L = 32768, whose 8-CTA rows would not fit in
+// shared memory); the exchange pushed by remote stores from L = 8192 on and pulled by remote
+// loads at L = 4096, the faster of the two at each size as measured (eddy N = 16383: 2.84 s
+// pushed against 3.12 s pulled; N = 4095: 312 ms pulled against 320 ms pushed).
 int ncta_for(int log2L) { return log2L >= 15 ? 16 : 8; }
+bool push_for(int log2L) { return log2L >= 13; }
 
 cudaError_t upload(float2** dst, const std::vector<float2>& v) {
   cudaError_t e = cudaMalloc(dst, sizeof(float2) * v.size());
@@ -35,15 +37,19 @@ cudaError_t upload(float2** dst, const std::vector<float2>& v) {
 
 float2 expi(double ang) { return make_float2(float(std::cos(ang)), float(std::sin(ang))); }
 
-cudaError_t get_cluster_tables(int device, int log2L, ClusterTables* out) {
+}  // namespace
+
+namespace sssp_cluster_host {
+
+cudaError_t get_cluster_tables(int device, int log2L, int ncta, ClusterTables* out) {
   std::lock_guard<std::mutex> lk(g_mu);
-  auto key = std::make_pair(device, log2L);
+  auto key = std::make_tuple(device, log2L, ncta);
   auto it = g_tabs.find(key);
   if (it != g_tabs.end()) {
     *out = it->second;
     return cudaSuccess;
   }
-  const int L = 1 << log2L, R = 2 * ncta_for(log2L), M = L / R;
+  const int L = 1 << log2L, R = 2 * ncta, M = L / R;
   std::vector<float2> tw(M, make_float2(0.f, 0.f));
   std::vector<float2> wL(L), c(L), wR(R / 2);
   for (int ns = 8; ns < M; ns *= 8) {  // same per-pass layout as the one-CTA transform
@@ -76,125 +82,75 @@ cudaError_t get_cluster_tables(int device, int log2L, ClusterTables* out) {
   return cudaSuccess;
 }
 
-template <class K>
-cudaError_t prepare(K kern, size_t smem, int ncta) {
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e == cudaSuccess && ncta > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  return e;
-}
-
-void cluster_config(cudaLaunchConfig_t* cfg, cudaLaunchAttribute* at, int ncta, int clusters, int threads,
-                    size_t smem, cudaStream_t st) {
-  *cfg = cudaLaunchConfig_t{};
-  cfg->gridDim = dim3(unsigned(ncta * clusters));
-  cfg->blockDim = dim3(unsigned(threads));
-  cfg->dynamicSmemBytes = smem;
-  cfg->stream = st;
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = unsigned(ncta);
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg->attrs = at;
-  cfg->numAttrs = 1;
-}
-
-template <class K, class... A>
-cudaError_t launch_cluster(K kern, int ncta, int clusters, int threads, size_t smem, cudaStream_t st, A... args) {
-  cudaLaunchConfig_t cfg;
-  cudaLaunchAttribute at[1];
-  cluster_config(&cfg, at, ncta, clusters, threads, smem, st);
-  return cudaLaunchKernelEx(&cfg, kern, args...);
-}
-
-template <int LOG2L, int NCTA>
-cudaError_t march_t(const sssp::SolveDesc* d, int count, cudaStream_t st, bool cplx, const ClusterTables& t) {
-  using C = CCfg<LOG2L, NCTA>;
-  if (cplx) {
-    auto k = sssp::sssp_march_cluster_kernel<LOG2L, NCTA, true>;
-    cudaError_t e = prepare(k, C::SMEM_CPLX, NCTA);
-    if (e != cudaSuccess) return e;
-    return launch_cluster(k, NCTA, count, C::NT, C::SMEM_CPLX, st, d, (const float2*)t.twM, (const float2*)t.wL,
-                          (const float2*)t.c, (const float2*)t.wR);
-  }
-  auto k = sssp::sssp_march_cluster_kernel<LOG2L, NCTA, false>;
-  cudaError_t e = prepare(k, C::SMEM, NCTA);
-  if (e != cudaSuccess) return e;
-  return launch_cluster(k, NCTA, count, C::NT, C::SMEM, st, d, (const float2*)t.twM, (const float2*)t.wL,
-                        (const float2*)t.c, (const float2*)t.wR);
-}
-
-template <int LOG2L, int NCTA>
-cudaError_t dst_t(const float2* in, float2* out, float scale, int count, long long is, long long os, cudaStream_t st,
-                  const ClusterTables& t) {
-  using C = CCfg<LOG2L, NCTA>;
-  auto k = sssp::sssp_dst_cluster_kernel<LOG2L, NCTA>;
-  cudaError_t e = prepare(k, C::SMEM, NCTA);
-  if (e != cudaSuccess) return e;
-  return launch_cluster(k, NCTA, count, C::NT, C::SMEM, st, in, out, scale, (const float2*)t.twM,
-                        (const float2*)t.wL, (const float2*)t.c, (const float2*)t.wR, is, os);
-}
-
-template <int LOG2L, int NCTA>
-cudaError_t fits_t(bool cplx, int* clusters) {
-  using C = CCfg<LOG2L, NCTA>;
-  cudaLaunchConfig_t cfg;
-  cudaLaunchAttribute at[1];
-  if (cplx) {
-    auto k = sssp::sssp_march_cluster_kernel<LOG2L, NCTA, true>;
-    cudaError_t e = prepare(k, C::SMEM_CPLX, NCTA);
-    if (e != cudaSuccess) return e;
-    cluster_config(&cfg, at, NCTA, 1, C::NT, C::SMEM_CPLX, 0);
-    return cudaOccupancyMaxActiveClusters(clusters, k, &cfg);
-  }
-  auto k = sssp::sssp_march_cluster_kernel<LOG2L, NCTA, false>;
-  cudaError_t e = prepare(k, C::SMEM, NCTA);
-  if (e != cudaSuccess) return e;
-  cluster_config(&cfg, at, NCTA, 1, C::NT, C::SMEM, 0);
-  return cudaOccupancyMaxActiveClusters(clusters, k, &cfg);
-}
-
-}  // namespace
+}  // namespace sssp_cluster_host
 
 namespace sssp_cluster {
 
 bool supported(int log2L) { return log2L >= kMinLog2 && log2L <= kMaxLog2; }
 
 int ncta(int log2L) { return ncta_for(log2L); }
+bool push_default(int log2L) { return push_for(log2L); }
 
-cudaError_t max_active_clusters(int log2L, bool cplx, int* clusters) {
+bool shape_supported(int log2L, int ncta, int push) {
+  if (!supported(log2L)) return false;
+  if (ncta == 0 || ncta == ncta_for(log2L)) return true;  // the default NCTA, either exchange
+  return ncta == 16 && (log2L == 13 || log2L == 14);      // 16-CTA clusters of L = 8192, 16384
+}
+
+namespace {
+// the explicit shape of a request (0 / -1: the size's default)
+void resolve(int log2L, int& ncta, int& push) {
+  if (ncta == 0) ncta = ncta_for(log2L);
+  if (push < 0) push = push_for(log2L) ? 1 : 0;
+}
+bool is_default(int log2L, int ncta, int push) { return ncta == ncta_for(log2L) && (push != 0) == push_for(log2L); }
+}  // namespace
+
+cudaError_t max_active_clusters(int log2L, bool cplx, int* clusters, int ncta, int push) {
   *clusters = 0;
+  if (!shape_supported(log2L, ncta, push)) return cudaErrorInvalidValue;
+  resolve(log2L, ncta, push);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   static std::mutex mu;
-  static std::map<std::tuple<int, int, bool>, int> cache;  // (device, log2 L, complex) -> clusters
+  // (device, log2 L, complex, NCTA, push) -> clusters
+  static std::map<std::tuple<int, int, bool, int, int>, int> cache;
   std::lock_guard<std::mutex> lk(mu);
-  const auto key = std::make_tuple(dev, log2L, cplx);
+  const auto key = std::make_tuple(dev, log2L, cplx, ncta, push);
   auto it = cache.find(key);
   if (it != cache.end()) {
     *clusters = it->second;
     return cudaSuccess;
   }
-  switch (log2L) {
-    case 12: e = fits_t<12, 8>(cplx, clusters); break;
-    case 13: e = fits_t<13, 8>(cplx, clusters); break;
-    case 14: e = fits_t<14, 8>(cplx, clusters); break;
-    case 15: e = fits_t<15, 16>(cplx, clusters); break;
-    default: return cudaErrorInvalidValue;
+  if (!is_default(log2L, ncta, push)) {
+    e = sssp_cluster_host::fits_alt(log2L, ncta, push != 0, cplx, clusters);
+  } else {
+    switch (log2L) {
+      case 12: e = fits_t<12, 8, false>(cplx, clusters); break;
+      case 13: e = fits_t<13, 8, true>(cplx, clusters); break;
+      case 14: e = fits_t<14, 8, true>(cplx, clusters); break;
+      case 15: e = fits_t<15, 16, true>(cplx, clusters); break;
+      default: return cudaErrorInvalidValue;
+    }
   }
   if (e == cudaSuccess) cache[key] = *clusters;
   return e;
 }
 
-cudaError_t launch_march(int log2L, const sssp::SolveDesc* d, int count, cudaStream_t st, bool cplx, int device) {
+cudaError_t launch_march(int log2L, const sssp::SolveDesc* d, int count, cudaStream_t st, bool cplx, int device,
+                         int ncta, int push) {
+  if (!shape_supported(log2L, ncta, push)) return cudaErrorInvalidValue;
+  resolve(log2L, ncta, push);
   ClusterTables t;
-  cudaError_t e = get_cluster_tables(device, log2L, &t);
+  cudaError_t e = sssp_cluster_host::get_cluster_tables(device, log2L, ncta, &t);
   if (e != cudaSuccess) return e;
+  if (!is_default(log2L, ncta, push)) return sssp_cluster_host::march_alt(log2L, ncta, push != 0, d, count, st, cplx, t);
   switch (log2L) {
-    case 12: return march_t<12, 8>(d, count, st, cplx, t);
-    case 13: return march_t<13, 8>(d, count, st, cplx, t);
-    case 14: return march_t<14, 8>(d, count, st, cplx, t);
-    case 15: return march_t<15, 16>(d, count, st, cplx, t);
+    case 12: return march_t<12, 8, false>(d, count, st, cplx, t);
+    case 13: return march_t<13, 8, true>(d, count, st, cplx, t);
+    case 14: return march_t<14, 8, true>(d, count, st, cplx, t);
+    case 15: return march_t<15, 16, true>(d, count, st, cplx, t);
   }
   return cudaErrorInvalidValue;
 }
@@ -202,13 +158,13 @@ cudaError_t launch_march(int log2L, const sssp::SolveDesc* d, int count, cudaStr
 cudaError_t launch_dst(int log2L, const float2* in, float2* out, float scale, int count, long long in_stride,
                        long long out_stride, cudaStream_t st, int device) {
   ClusterTables t;
-  cudaError_t e = get_cluster_tables(device, log2L, &t);
+  cudaError_t e = sssp_cluster_host::get_cluster_tables(device, log2L, ncta_for(log2L), &t);
   if (e != cudaSuccess) return e;
   switch (log2L) {
-    case 12: return dst_t<12, 8>(in, out, scale, count, in_stride, out_stride, st, t);
-    case 13: return dst_t<13, 8>(in, out, scale, count, in_stride, out_stride, st, t);
-    case 14: return dst_t<14, 8>(in, out, scale, count, in_stride, out_stride, st, t);
-    case 15: return dst_t<15, 16>(in, out, scale, count, in_stride, out_stride, st, t);
+    case 12: return dst_t<12, 8, false>(in, out, scale, count, in_stride, out_stride, st, t);
+    case 13: return dst_t<13, 8, true>(in, out, scale, count, in_stride, out_stride, st, t);
+    case 14: return dst_t<14, 8, true>(in, out, scale, count, in_stride, out_stride, st, t);
+    case 15: return dst_t<15, 16, true>(in, out, scale, count, in_stride, out_stride, st, t);
   }
   return cudaErrorInvalidValue;
 }

@@ -70,6 +70,8 @@ _SIGNATURES = {
     "pe_plan_set_shape": (_i, [_vp, _i]),
     "pe_plan_set_operator": (_i, [_vp, _i]),
     "pe_plan_get_shape": (_i, [_vp, ctypes.POINTER(_i)]),
+    "pe_plan_set_cluster_shape": (_i, [_vp, _i, _i]),
+    "pe_plan_get_cluster_shape": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "pe_plan_autotune_shapes": (_i, [_vp, _i, _vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "pe_march_batch_autotune": (_i, [ctypes.POINTER(_vp), _i, _i, _vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "pe_state_size": (_sz, [_vp]),
@@ -323,6 +325,18 @@ class Plan:
         """Points per thread of the one-CTA kernel: 4, 8 (default) or 16."""
         self._c(lib().pe_plan_set_shape(self._p, int(points_per_thread)))
 
+    def set_cluster_shape(self, ncta: int = 0, push: int = -1):
+        """Cluster-kernel shape: CTAs per cluster (0: the size's default, or 16 for N + 1 = 8192 /
+        16384) and the exchange mode (1 push, 0 pull, -1 the size's default)."""
+        self._c(lib().pe_plan_set_cluster_shape(self._p, int(ncta), int(push)))
+
+    @property
+    def cluster_shape(self) -> Tuple[int, int]:
+        """(CTAs per cluster, push) a cluster march of this plan takes ((0, -1): no cluster kernel)."""
+        n, u = _i(0), _i(0)
+        self._c(lib().pe_plan_get_cluster_shape(self._p, ctypes.byref(n), ctypes.byref(u)))
+        return n.value, u.value
+
     @property
     def shape(self) -> int:
         """Points per thread of the one-CTA kernel a march runs (0: cluster or large-grid kernel)."""
@@ -534,12 +548,20 @@ class GemmBatch:
             pass
 
 
-SHAPE_NAMES = ("cta4", "cta8", "cta16", "cluster")
+# the shapes the autotuners time, in the order of their timing outputs (include/sssp.h): one CTA
+# at 4/8/16 points per thread; the cluster of the size's default CTA count pulling / pushing its
+# exchange; 16-CTA clusters pulling / pushing (N + 1 = 8192, 16384)
+SHAPE_NAMES = ("cta4", "cta8", "cta16", "cluster_pull", "cluster_push", "cluster16_pull", "cluster16_push")
 
 
 def _shape_result(ms, k, p):
-    return {"chosen": ("cluster" if k.value == KERNELS["cluster"] else f"cta{p.value}"),
-            "ms": {n: (float(ms[i]) if ms[i] >= 0 else None) for i, n in enumerate(SHAPE_NAMES)}}
+    t = {n: (float(ms[i]) if ms[i] >= 0 else None) for i, n in enumerate(SHAPE_NAMES)}
+    timed = {n: v for n, v in t.items() if v is not None}
+    chosen = min(timed, key=timed.get) if timed else None  # the library keeps the first fastest
+    if chosen is not None:
+        want_cluster = k.value == KERNELS["cluster"]
+        assert chosen.startswith("cluster") == want_cluster and (want_cluster or chosen == f"cta{p.value}")
+    return {"chosen": chosen, "ms": t}
 
 
 def autotune_batch(plans: List[Plan], steps: int = 8) -> dict:
@@ -547,7 +569,7 @@ def autotune_batch(plans: List[Plan], steps: int = 8) -> dict:
     (one CTA per solve at 4/8/16 points per thread, one cluster per solve), restore their state,
     and set the fastest (pe_march_batch_autotune)."""
     arr = (_vp * len(plans))(*[p.handle for p in plans])
-    ms = (ctypes.c_float * 4)()
+    ms = (ctypes.c_float * len(SHAPE_NAMES))()
     k, p = _i(0), _i(0)
     st = lib().pe_march_batch_autotune(arr, len(plans), int(steps), ctypes.cast(ms, _vp), ctypes.byref(k),
                                        ctypes.byref(p))

@@ -1160,7 +1160,7 @@ def test_batch_autotune_restores_state_and_picks_the_fastest(sssp):
     plans = [sssp.plan_for(s, tl_every=10) for s in solves]
     res = sssp.autotune_batch(plans, steps=6)
     ms = res["ms"]
-    assert ms["cluster"] is None
+    assert all(ms[k] is None for k in ms if k.startswith("cluster"))
     timed = {k: v for k, v in ms.items() if v is not None}
     assert set(timed) == {"cta4", "cta8", "cta16"}
     assert res["chosen"] == min(timed, key=timed.get)
@@ -1183,6 +1183,61 @@ def test_batch_autotune_restores_state_and_picks_the_fastest(sssp):
         assert np.array_equal(a.read_field(), b.read_field())
     for p in plans + plain:
         p.close()
+
+
+def test_cluster_shapes_match_oracle_and_autotune(sssp):
+    """The cluster kernel's shapes on N = 8191 (8 and 16 CTAs per cluster, the transform's exchange
+    pulled by remote loads or pushed by remote stores) each march the Munk case to the oracle's
+    result; the exchange mode moves the same values, so pull and push give the same bits.  The
+    batch autotuner then times every shape four such solves can take (the one-CTA large-grid
+    kernel and the four cluster shapes), sets the fastest, restores the march, and the tuned
+    batch still gives the oracle's result."""
+    s = inputs.munk(N=8191, freq=100.0, dr=25.0, steps=8)
+    ref = _oracle(s)
+    out = {}
+    for n, u in [(0, 0), (0, 1), (16, 0), (16, 1)]:
+        pl = sssp.plan_for(s, tl_every=1)
+        pl.set_kernel("cluster")
+        pl.set_cluster_shape(n, u)
+        assert pl.cluster_shape == (n or 8, u)
+        pl.march(s.steps)
+        f = pl.read_field()
+        tl, _ = pl.read_tl()
+        pl.close()
+        _compare(f, tl, ref)
+        out[(n, u)] = f
+    assert np.array_equal(out[(0, 0)], out[(0, 1)])
+    assert np.array_equal(out[(16, 0)], out[(16, 1)])
+    solves = [s] + [inputs.munk(N=8191, freq=f, dr=25.0, steps=8) for f in (120.0, 150.0, 200.0)]
+    plans = [sssp.plan_for(x, tl_every=1) for x in solves]
+    res = sssp.autotune_batch(plans, steps=2)
+    timed = {k: v for k, v in res["ms"].items() if v is not None}
+    assert set(timed) == {"cta8", "cluster_pull", "cluster_push", "cluster16_pull", "cluster16_push"}, timed
+    assert res["chosen"] == min(timed, key=timed.get)
+    want = {"cluster_pull": (8, 0), "cluster_push": (8, 1), "cluster16_pull": (16, 0),
+            "cluster16_push": (16, 1)}.get(res["chosen"])
+    for p in plans:
+        assert p.range() == (0.0, 0)
+        assert p.kernel == ("cluster" if want else "cta")
+        if want:
+            assert p.cluster_shape == want
+    sssp.march_batch(plans, s.steps)
+    f = plans[0].read_field()
+    tl, _ = plans[0].read_tl()
+    _compare(f, tl, ref)
+    for p in plans:
+        p.close()
+    small = sssp.Plan(4095, 5000.0, 0.2, 25.0, 4)
+    with pytest.raises(sssp.PEError):
+        small.set_cluster_shape(16, 1)  # 16-CTA clusters: N + 1 = 8192 and 16384 only
+    small.set_cluster_shape(8, 1)
+    assert small.cluster_shape == (8, 1)
+    small.close()
+    tiny = sssp.Plan(1023, 5000.0, 0.2, 25.0, 4)
+    with pytest.raises(sssp.PEError):
+        tiny.set_cluster_shape(0, 0)
+    assert tiny.cluster_shape == (0, -1)
+    tiny.close()
 
 
 # ----------------------------------------------------------------------------- FD-SSP (Section 4.3)
