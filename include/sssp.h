@@ -231,7 +231,7 @@ pe_status pe_dst1_noalloc(const float* in, float* out, int N, void* cuda_stream)
  * Which kernel marches a plan (no counterpart in the paper, which gives no implementation).
  *   PE_KERNEL_CTA      one CTA per solve, the field in that SM's shared memory (N + 1 <= 4096) or
  *                      in a per-plan global workspace (larger grids);
- *   PE_KERNEL_CLUSTER  one solve over a thread-block cluster of 8 CTAs (16 for N + 1 = 32768),
+ *   PE_KERNEL_CLUSTER  one solve over a thread-block cluster of 8 or 16 CTAs (the cluster shape below),
  *                      every length-(N + 1) array in the cluster's distributed shared memory and
  *                      each DST-I of Section 3.1 as local FFTs plus one all-to-all exchange;
  *                      Dirichlet grids with N + 1 in [4096, 32768];
@@ -250,17 +250,18 @@ pe_status pe_plan_set_kernel(pe_plan* plan, int kernel);
 pe_status pe_plan_get_kernel(const pe_plan* plan, int* kernel);
 
 /*
- * Shape of the cluster kernel (no counterpart in the paper): ncta CTAs per cluster — 0 for the
- * size's default (8; 16 at N + 1 = 32768), or 16 for N + 1 = 8192 and 16384 — and how each
+ * Shape of the cluster kernel (no counterpart in the paper): ncta CTAs per cluster — 8
+ * (N + 1 = 4096 .. 16384) or 16 (N + 1 = 8192 .. 32768), 0 for the size's default — and how each
  * transform's all-to-all exchange moves the values between the CTAs: push = 1 by remote stores
- * before the cluster barrier, 0 by remote loads after it, -1 the size's default (pull at
- * N + 1 = 4096, push from 8192 on).  The exchange mode does not change the arithmetic (the
- * results are bitwise the same); the cluster size changes how each transform is split, so the
- * results agree to FP32 rounding.  The shape applies whenever a march of the plan runs the
- * cluster kernel; batched marches group solves by it.  PE_ERR_ARG for a shape the plan (Dirichlet
- * grids with N + 1 in [4096, 32768]) or the device cannot take.  pe_plan_get_cluster_shape
- * reports the shape a cluster march of the plan takes (ncta 0 and push -1 for plans the cluster
- * kernel does not take).
+ * before the cluster barrier, 0 by remote loads after it, -1 the size's default.  The defaults
+ * are the shapes measured fastest for batches of 1 to 38 solves: 8 CTAs at N + 1 = 4096 and
+ * 8192, 16 CTAs at 16384 and 32768, the exchange pulled.  The exchange mode does not
+ * change the arithmetic (the results are bitwise the same); the cluster size changes how each
+ * transform is split, so the results agree to FP32 rounding.  The shape applies whenever a march
+ * of the plan runs the cluster kernel; batched marches group solves by it.  PE_ERR_ARG for a shape
+ * the plan (Dirichlet grids with N + 1 in [4096, 32768]) or the device cannot take.
+ * pe_plan_get_cluster_shape reports the shape a cluster march of the plan takes (ncta 0 and
+ * push -1 for plans the cluster kernel does not take).
  */
 pe_status pe_plan_set_cluster_shape(pe_plan* plan, int ncta, int push);
 pe_status pe_plan_get_cluster_shape(const pe_plan* plan, int* ncta, int* push);
@@ -300,10 +301,9 @@ pe_status pe_plan_get_shape(const pe_plan* plan, int* points_per_thread);
  * DST-I count per step on that shape (one more run, restored), and later batched marches launch
  * each group's solves in descending cost (heavy and light solves share SMs; the results do not
  * depend on the order).  ms: PE_AUTOTUNE_SHAPES floats, the timed milliseconds of (CTA P=4,
- * CTA P=8, CTA P=16, cluster of the default size pulling, the same pushing, 16-CTA cluster
- * pulling, the same pushing), -1 where no plan can take the shape (a 16-CTA entry is -1 where
- * 16 is the default size: the default-size entries time it), or NULL; kernel /
- * points_per_thread: the shape chosen (pe_plan_get_cluster_shape gives the cluster shape set),
+ * CTA P=8, CTA P=16, 8-CTA cluster pulling, 8-CTA cluster pushing, 16-CTA cluster pulling, 16-CTA
+ * cluster pushing), -1 where no plan can take the shape, or NULL; kernel / points_per_thread: the
+ * shape chosen (pe_plan_get_cluster_shape gives the cluster shape set),
  * or NULL.  pe_plan_autotune_shapes is the
  * same for one plan.  Plans need a field (and a profile when Neumann terms are asked for);
  * synchronises.

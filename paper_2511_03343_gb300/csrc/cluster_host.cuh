@@ -1,7 +1,6 @@
 // Host-side launch helpers of the cluster march (march_cluster.cuh), shared by the translation
-// units that instantiate its shapes: sssp_cluster.cu (the default shape of every size, the
-// transform tables, the dispatch) and sssp_cluster_shapes.cu (the other shapes the autotuner
-// times).  Internal to the library.
+// units that instantiate its shapes: sssp_cluster.cu (the transform tables, the dispatch, the
+// 8-CTA shapes) and sssp_cluster_shapes.cu (the 16-CTA shapes).  Internal to the library.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -98,9 +97,14 @@ cudaError_t fits_t(bool cplx, int* clusters) {
 }
 
 
-// the non-default shapes (sssp_cluster_shapes.cu): cudaErrorInvalidValue for a shape not built
-cudaError_t march_alt(int log2L, int ncta, bool push, const sssp::SolveDesc* d, int count, cudaStream_t st,
-                      bool cplx, const ClusterTables& t);
-cudaError_t fits_alt(int log2L, int ncta, bool push, bool cplx, int* clusters);
+// the 8-CTA shapes (sssp_cluster.cu: L = 4096 .. 16384) and the 16-CTA shapes
+// (sssp_cluster_shapes.cu: L = 8192 .. 32768), either exchange; cudaErrorInvalidValue for a shape
+// not built
+cudaError_t march_8(int log2L, bool push, const sssp::SolveDesc* d, int count, cudaStream_t st, bool cplx,
+                    const ClusterTables& t);
+cudaError_t fits_8(int log2L, bool push, bool cplx, int* clusters);
+cudaError_t march_16(int log2L, bool push, const sssp::SolveDesc* d, int count, cudaStream_t st, bool cplx,
+                     const ClusterTables& t);
+cudaError_t fits_16(int log2L, bool push, bool cplx, int* clusters);
 
 }  // namespace sssp_cluster_host

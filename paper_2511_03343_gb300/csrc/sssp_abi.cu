@@ -1277,20 +1277,20 @@ pe_status pe_plan_get_kernel(const pe_plan* p, int* kernel) {
 namespace {
 
 // The shapes the autotuners search, in the order of their timing outputs: one CTA at 4, 8 and
-// 16 points per thread, then the thread-block cluster with 8 CTAs (16 at N + 1 = 32768) pulling
-// and pushing its exchange, then 16-CTA clusters (N + 1 = 8192 and 16384) pulling and pushing.
+// 16 points per thread, then thread-block clusters of 8 CTAs (N + 1 = 4096 .. 16384) pulling
+// and pushing the transform's exchange, then of 16 CTAs (N + 1 = 8192 .. 32768) pulling and
+// pushing.
 constexpr int kShapes = PE_AUTOTUNE_SHAPES;
 const int kShapeKernel[kShapes] = {PE_KERNEL_CTA,     PE_KERNEL_CTA,     PE_KERNEL_CTA,    PE_KERNEL_CLUSTER,
                                    PE_KERNEL_CLUSTER, PE_KERNEL_CLUSTER, PE_KERNEL_CLUSTER};
 const int kShapePpt[kShapes] = {4, 8, 16, 8, 8, 8, 8};
-const int kShapeNcta[kShapes] = {0, 0, 0, 0, 0, 16, 16};  // 0: the size's default
+const int kShapeNcta[kShapes] = {0, 0, 0, 8, 8, 16, 16};
 const int kShapePush[kShapes] = {-1, -1, -1, 0, 1, 0, 1};
 
 bool shape_ok(const pe_plan* p, int c) {
   if (kShapeKernel[c] == PE_KERNEL_CLUSTER) {
     int clusters = 0;
     const int n = kShapeNcta[c];
-    if (n != 0 && n == sssp_cluster::ncta(p->log2L)) return false;  // the same shape as ncta 0
     return p->user_bc == PE_BC_DIRICHLET && sssp_cluster::shape_supported(p->log2L, n, kShapePush[c]) &&
            sssp_cluster::max_active_clusters(p->log2L, p->complex_profile, &clusters, n, kShapePush[c]) ==
                cudaSuccess &&

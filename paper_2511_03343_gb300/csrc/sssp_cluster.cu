@@ -1,6 +1,6 @@
 // Host side of the cluster march (march_cluster.cuh): per-shape tables, the default shape of
-// every size, the launch with the cluster dimension, and the check that a cluster of a shape
-// fits on the device (the other shapes are instantiated in sssp_cluster_shapes.cu).
+// every size, the launch with the cluster dimension, the check that a cluster of a shape fits on
+// the device, and the 8-CTA shapes (the 16-CTA ones are instantiated in sssp_cluster_shapes.cu).
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -22,12 +22,17 @@ using sssp_cluster_host::march_t;
 std::mutex g_mu;
 std::map<std::tuple<int, int, int>, ClusterTables> g_tabs;  // (device, log2 L, NCTA)
 
-// The default shape of each size: 8 CTAs (16 at L = 32768, whose 8-CTA rows would not fit in
-// shared memory); the exchange pushed by remote stores from L = 8192 on and pulled by remote
-// loads at L = 4096, the faster of the two at each size as measured (eddy N = 16383: 2.84 s
-// pushed against 3.12 s pulled; N = 4095: 312 ms pulled against 320 ms pushed).
-int ncta_for(int log2L) { return log2L >= 15 ? 16 : 8; }
-bool push_for(int log2L) { return log2L >= 13; }
+// The default shape of each size, the fastest of the shapes the autotuner times at every batch
+// size measured (1 .. 38 Munk solves, 4 steps), always pulling the exchange: 8 CTAs at L = 4096
+// (0.50 ms against 0.51 pushed) and 8192 (0.54 against 0.58 pushed, 0.75 on 16 CTAs); 16 CTAs at
+// L = 16384 (alone: 1.02 ms against 1.44 on 8 CTAs pushing; 38 solves: 4.1 against 4.7 ms) and
+// 32768 (1.68 against 1.71 pushed; 8-CTA rows would not fit in shared memory there).
+int ncta_for(int log2L) { return log2L >= 14 ? 16 : 8; }
+bool push_for(int) { return false; }
+
+// CTAs per cluster of the transform-only kernel (pe_dst1 on a cluster plan), a fixed shape:
+// 8 CTAs up to L = 16384, 16 at 32768
+int dst_ncta(int log2L) { return log2L >= 15 ? 16 : 8; }
 
 cudaError_t upload(float2** dst, const std::vector<float2>& v) {
   cudaError_t e = cudaMalloc(dst, sizeof(float2) * v.size());
@@ -82,6 +87,26 @@ cudaError_t get_cluster_tables(int device, int log2L, int ncta, ClusterTables* o
   return cudaSuccess;
 }
 
+cudaError_t march_8(int log2L, bool push, const sssp::SolveDesc* d, int count, cudaStream_t st, bool cplx,
+                    const ClusterTables& t) {
+  switch (log2L) {
+    case 12: return push ? march_t<12, 8, true>(d, count, st, cplx, t) : march_t<12, 8, false>(d, count, st, cplx, t);
+    case 13: return push ? march_t<13, 8, true>(d, count, st, cplx, t) : march_t<13, 8, false>(d, count, st, cplx, t);
+    case 14: return push ? march_t<14, 8, true>(d, count, st, cplx, t) : march_t<14, 8, false>(d, count, st, cplx, t);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t fits_8(int log2L, bool push, bool cplx, int* clusters) {
+  *clusters = 0;
+  switch (log2L) {
+    case 12: return push ? fits_t<12, 8, true>(cplx, clusters) : fits_t<12, 8, false>(cplx, clusters);
+    case 13: return push ? fits_t<13, 8, true>(cplx, clusters) : fits_t<13, 8, false>(cplx, clusters);
+    case 14: return push ? fits_t<14, 8, true>(cplx, clusters) : fits_t<14, 8, false>(cplx, clusters);
+  }
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace sssp_cluster_host
 
 namespace sssp_cluster {
@@ -92,9 +117,10 @@ int ncta(int log2L) { return ncta_for(log2L); }
 bool push_default(int log2L) { return push_for(log2L); }
 
 bool shape_supported(int log2L, int ncta, int push) {
-  if (!supported(log2L)) return false;
-  if (ncta == 0 || ncta == ncta_for(log2L)) return true;  // the default NCTA, either exchange
-  return ncta == 16 && (log2L == 13 || log2L == 14);      // 16-CTA clusters of L = 8192, 16384
+  if (!supported(log2L) || push < -1 || push > 1) return false;
+  if (ncta == 0) return true;                                  // the size's default
+  if (ncta == 8) return log2L <= 14;                           // 8-CTA rows fit up to L = 16384
+  return ncta == 16 && log2L >= 13;                            // 16-CTA clusters from L = 8192
 }
 
 namespace {
@@ -103,7 +129,6 @@ void resolve(int log2L, int& ncta, int& push) {
   if (ncta == 0) ncta = ncta_for(log2L);
   if (push < 0) push = push_for(log2L) ? 1 : 0;
 }
-bool is_default(int log2L, int ncta, int push) { return ncta == ncta_for(log2L) && (push != 0) == push_for(log2L); }
 }  // namespace
 
 cudaError_t max_active_clusters(int log2L, bool cplx, int* clusters, int ncta, int push) {
@@ -123,17 +148,8 @@ cudaError_t max_active_clusters(int log2L, bool cplx, int* clusters, int ncta, i
     *clusters = it->second;
     return cudaSuccess;
   }
-  if (!is_default(log2L, ncta, push)) {
-    e = sssp_cluster_host::fits_alt(log2L, ncta, push != 0, cplx, clusters);
-  } else {
-    switch (log2L) {
-      case 12: e = fits_t<12, 8, false>(cplx, clusters); break;
-      case 13: e = fits_t<13, 8, true>(cplx, clusters); break;
-      case 14: e = fits_t<14, 8, true>(cplx, clusters); break;
-      case 15: e = fits_t<15, 16, true>(cplx, clusters); break;
-      default: return cudaErrorInvalidValue;
-    }
-  }
+  e = ncta == 16 ? sssp_cluster_host::fits_16(log2L, push != 0, cplx, clusters)
+                 : sssp_cluster_host::fits_8(log2L, push != 0, cplx, clusters);
   if (e == cudaSuccess) cache[key] = *clusters;
   return e;
 }
@@ -145,20 +161,14 @@ cudaError_t launch_march(int log2L, const sssp::SolveDesc* d, int count, cudaStr
   ClusterTables t;
   cudaError_t e = sssp_cluster_host::get_cluster_tables(device, log2L, ncta, &t);
   if (e != cudaSuccess) return e;
-  if (!is_default(log2L, ncta, push)) return sssp_cluster_host::march_alt(log2L, ncta, push != 0, d, count, st, cplx, t);
-  switch (log2L) {
-    case 12: return march_t<12, 8, false>(d, count, st, cplx, t);
-    case 13: return march_t<13, 8, true>(d, count, st, cplx, t);
-    case 14: return march_t<14, 8, true>(d, count, st, cplx, t);
-    case 15: return march_t<15, 16, true>(d, count, st, cplx, t);
-  }
-  return cudaErrorInvalidValue;
+  return ncta == 16 ? sssp_cluster_host::march_16(log2L, push != 0, d, count, st, cplx, t)
+                    : sssp_cluster_host::march_8(log2L, push != 0, d, count, st, cplx, t);
 }
 
 cudaError_t launch_dst(int log2L, const float2* in, float2* out, float scale, int count, long long in_stride,
                        long long out_stride, cudaStream_t st, int device) {
   ClusterTables t;
-  cudaError_t e = sssp_cluster_host::get_cluster_tables(device, log2L, ncta_for(log2L), &t);
+  cudaError_t e = sssp_cluster_host::get_cluster_tables(device, log2L, dst_ncta(log2L), &t);
   if (e != cudaSuccess) return e;
   switch (log2L) {
     case 12: return dst_t<12, 8, false>(in, out, scale, count, in_stride, out_stride, st, t);

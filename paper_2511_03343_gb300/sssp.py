@@ -326,8 +326,8 @@ class Plan:
         self._c(lib().pe_plan_set_shape(self._p, int(points_per_thread)))
 
     def set_cluster_shape(self, ncta: int = 0, push: int = -1):
-        """Cluster-kernel shape: CTAs per cluster (0: the size's default, or 16 for N + 1 = 8192 /
-        16384) and the exchange mode (1 push, 0 pull, -1 the size's default)."""
+        """Cluster-kernel shape: CTAs per cluster (0: the size's default; 8 for N + 1 <= 16384, 16 for
+        N + 1 >= 8192) and the exchange mode (1 push, 0 pull, -1 the size's default)."""
         self._c(lib().pe_plan_set_cluster_shape(self._p, int(ncta), int(push)))
 
     @property
@@ -549,9 +549,9 @@ class GemmBatch:
 
 
 # the shapes the autotuners time, in the order of their timing outputs (include/sssp.h): one CTA
-# at 4/8/16 points per thread; the cluster of the size's default CTA count pulling / pushing its
-# exchange; 16-CTA clusters pulling / pushing (N + 1 = 8192, 16384)
-SHAPE_NAMES = ("cta4", "cta8", "cta16", "cluster_pull", "cluster_push", "cluster16_pull", "cluster16_push")
+# at 4/8/16 points per thread; 8-CTA clusters (N + 1 = 4096 .. 16384) pulling / pushing the
+# transform's exchange; 16-CTA clusters (N + 1 = 8192 .. 32768) pulling / pushing
+SHAPE_NAMES = ("cta4", "cta8", "cta16", "cluster8_pull", "cluster8_push", "cluster16_pull", "cluster16_push")
 
 
 def _shape_result(ms, k, p):

@@ -160,7 +160,7 @@ def test_munk_full_size_against_stored_oracle(sssp, kernel):
     assert err["sum"][0] <= FIELD_TOL and err["sum"][1] <= TL_TOL
 
 
-@pytest.mark.parametrize("kernel", ["auto", "cta"])
+@pytest.mark.parametrize("kernel", ["auto", "cta", "cluster8"])
 def test_eddy_full_length_against_stored_oracle(sssp, kernel):
     """The range-dependent workload at full length (N = 16383, 4000 steps of 25 m, [8/8], a
     profile node per step) against the stored FP64 oracle runs (library DST-I backend):
@@ -178,7 +178,11 @@ def test_eddy_full_length_against_stored_oracle(sssp, kernel):
             for form, name in (("product", "eddy_n16383_s4000.txt"), ("sum", "eddy_n16383_s4000_sum.txt"))}
     meta = runs["product"][0]
     pl = sssp.plan_for(s, tl_every=int(meta["tl_every"]))
-    pl.set_kernel(kernel)
+    if kernel == "cluster8":  # 8-CTA clusters pushing the exchange (auto: 16 CTAs pulling)
+        pl.set_kernel("cluster")
+        pl.set_cluster_shape(8, 1)
+    else:
+        pl.set_kernel(kernel)
     pl.march(s.steps)
     u = pl.read_field()
     tl, rng = pl.read_tl()
@@ -1194,27 +1198,30 @@ def test_cluster_shapes_match_oracle_and_autotune(sssp):
     batch still gives the oracle's result."""
     s = inputs.munk(N=8191, freq=100.0, dr=25.0, steps=8)
     ref = _oracle(s)
+    pl = sssp.plan_for(s, tl_every=1)
+    assert pl.cluster_shape == (8, 0)  # the default of N + 1 = 8192
+    pl.close()
     out = {}
-    for n, u in [(0, 0), (0, 1), (16, 0), (16, 1)]:
+    for n, u in [(8, 0), (8, 1), (16, 0), (16, 1)]:
         pl = sssp.plan_for(s, tl_every=1)
         pl.set_kernel("cluster")
         pl.set_cluster_shape(n, u)
-        assert pl.cluster_shape == (n or 8, u)
+        assert pl.cluster_shape == (n, u)
         pl.march(s.steps)
         f = pl.read_field()
         tl, _ = pl.read_tl()
         pl.close()
         _compare(f, tl, ref)
         out[(n, u)] = f
-    assert np.array_equal(out[(0, 0)], out[(0, 1)])
+    assert np.array_equal(out[(8, 0)], out[(8, 1)])
     assert np.array_equal(out[(16, 0)], out[(16, 1)])
     solves = [s] + [inputs.munk(N=8191, freq=f, dr=25.0, steps=8) for f in (120.0, 150.0, 200.0)]
     plans = [sssp.plan_for(x, tl_every=1) for x in solves]
     res = sssp.autotune_batch(plans, steps=2)
     timed = {k: v for k, v in res["ms"].items() if v is not None}
-    assert set(timed) == {"cta8", "cluster_pull", "cluster_push", "cluster16_pull", "cluster16_push"}, timed
+    assert set(timed) == {"cta8", "cluster8_pull", "cluster8_push", "cluster16_pull", "cluster16_push"}, timed
     assert res["chosen"] == min(timed, key=timed.get)
-    want = {"cluster_pull": (8, 0), "cluster_push": (8, 1), "cluster16_pull": (16, 0),
+    want = {"cluster8_pull": (8, 0), "cluster8_push": (8, 1), "cluster16_pull": (16, 0),
             "cluster16_push": (16, 1)}.get(res["chosen"])
     for p in plans:
         assert p.range() == (0.0, 0)
@@ -1229,10 +1236,15 @@ def test_cluster_shapes_match_oracle_and_autotune(sssp):
         p.close()
     small = sssp.Plan(4095, 5000.0, 0.2, 25.0, 4)
     with pytest.raises(sssp.PEError):
-        small.set_cluster_shape(16, 1)  # 16-CTA clusters: N + 1 = 8192 and 16384 only
+        small.set_cluster_shape(16, 1)  # 16-CTA clusters from N + 1 = 8192 on
     small.set_cluster_shape(8, 1)
     assert small.cluster_shape == (8, 1)
     small.close()
+    big = sssp.Plan(32767, 5000.0, 0.2, 25.0, 4)
+    assert big.cluster_shape == (16, 0)
+    with pytest.raises(sssp.PEError):
+        big.set_cluster_shape(8, 0)  # 8-CTA rows of N + 1 = 32768 do not fit in shared memory
+    big.close()
     tiny = sssp.Plan(1023, 5000.0, 0.2, 25.0, 4)
     with pytest.raises(sssp.PEError):
         tiny.set_cluster_shape(0, 0)
