@@ -444,7 +444,7 @@ def _served_block(args, sssp, stream):
     trace = inputs.serving_trace(count=args.serve_requests)
     check = [t["id"] for t in trace if t["N"] <= 1023][:6]
     res = serving.replay(trace, hbm_budget=120e9, chunk_steps=args.chunk_steps, tl_every=10,
-                         range_scale=args.served_range_scale, stream=stream, keep_ids=check)
+                         range_scale=args.served_range_scale, stream=stream, keep_ids=check, pacing=args.pacing)
     worst, same = 0.0, True
     for i, (field, tl, s, prm) in res.pop("results").items():
         k0, sc, p = prm
@@ -463,7 +463,7 @@ def _served_block(args, sssp, stream):
     res["parity_vs_plain"] = {"requests": len(check), "bitwise_equal": bool(same), "max_tl_diff_db": worst}
     res["config"] = {"requests": len(trace), "rate_per_s": 200, "range_scale": args.served_range_scale,
                      "budget_bytes": 120e9, "chunk_steps": args.chunk_steps, "tl_every": 10,
-                     "admission": "minimax c0 + convergent Pade order"}
+                     "pacing": args.pacing, "admission": "minimax c0 + convergent Pade order"}
     res.pop("queue_depth", None)
     return res
 
@@ -603,14 +603,15 @@ def bench_serve(args):
     clocks = ClockSampler(0)
     clocks.start()
     res = serving.replay(trace, hbm_budget=120e9, chunk_steps=args.chunk_steps, tl_every=10,
-                         range_scale=args.range_scale, stream=stream, record_params=True)
+                         range_scale=args.range_scale, stream=stream, record_params=True, pacing=args.pacing)
     clk = clocks.stop()
     prm = res.pop("params")
     line = {"metric": METRIC, "value": res["throughput"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": 1e3 * res["wall_s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64", "data": "synthetic",
             "config": {"workload": "serving_mix", "requests": len(trace), "rate_per_s": 200,
-                       "range_scale": args.range_scale, "budget_bytes": 120e9, "chunk_steps": args.chunk_steps},
+                       "range_scale": args.range_scale, "budget_bytes": 120e9, "chunk_steps": args.chunk_steps,
+                       "pacing": args.pacing},
             "served": {k: v for k, v in res.items() if k != "results"}, "clocks": clk}
     if args.serve_baseline:
         # one-at-a-time: every request marched alone on the plain marcher with the values admission
@@ -963,6 +964,8 @@ def main():
                     help="eddy / large / iso workloads: run the shape autotuner before timing")
     ap.add_argument("--gemm-fp32-steps", type=int, default=2000)
     ap.add_argument("--chunk-steps", type=int, default=50)
+    ap.add_argument("--pacing", type=int, default=64,
+                    help="serving: a cheaper request marches up to this many chunks per server step (1: lockstep)")
     ap.add_argument("--serve-baseline", action="store_true")
     ap.add_argument("--baseline-steps", type=int, default=4)
     ap.add_argument("--batch-count", type=int, default=256)

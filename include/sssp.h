@@ -386,10 +386,14 @@ void pe_gemm_batch_destroy(pe_gemm_batch* batch);
  * Serving loop (continuous batching).  The paper marches one solve at a time; this is the
  * deployment form: many independent marches share the GPU.  Requests queue in arrival order;
  * each pe_server_step admits queued requests while a slot is free and their device bytes
- * (pe_plan_bytes_estimate) fit in the remaining budget, advances every live solve by up to
- * `chunk_steps` range steps in one batched march, and retires finished ones (field and TL
- * rows copied to host memory, plan freed).  A solve's result is bit-identical to marching it
- * alone.  The server is not thread-safe.
+ * (pe_plan_bytes_estimate) fit in the remaining budget, advances every live solve in one
+ * batched march, and retires finished ones (field and TL rows copied to host memory, plan
+ * freed).  Pacing: the costliest kind of live request (transforms per step x the work of a
+ * transform, (1 + p (terms - 1)) (N + 1) log2(N + 1)) marches up to `chunk_steps` range steps per
+ * pe_server_step and a cheaper one up to w times as many, w = the largest live cost over its own
+ * cost rounded down, at most max_weight (64 by default; pe_server_set_pacing, 1 = every request
+ * `chunk_steps`), so that small grids do not march at the pace of the largest.  A solve's result
+ * is bit-identical to marching it alone.  The server is not thread-safe.
  * ------------------------------------------------------------------------------------ */
 typedef struct pe_server pe_server;
 
@@ -435,6 +439,8 @@ pe_status pe_neumann_radius_estimate(const double* V, int N, double H, double k0
 
 /* hbm_budget_bytes > 0, max_live >= 1 concurrent solves, chunk_steps >= 1 steps per launch. */
 pe_status pe_server_create(pe_server** out, size_t hbm_budget_bytes, int max_live, int chunk_steps, void* cuda_stream);
+/* Pacing limit (see above): max_weight in [1, 4096]; PE_ERR_ARG otherwise. */
+pe_status pe_server_set_pacing(pe_server* server, int max_weight);
 void pe_server_destroy(pe_server* server);
 const char* pe_server_error(const pe_server* server);
 /* Queue a request (inputs copied); *id identifies it.  PE_ERR_OOM if it can never fit. */

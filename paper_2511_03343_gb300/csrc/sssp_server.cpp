@@ -5,8 +5,9 @@
 // arrival order.  At every pe_server_step the loop
 //   1. admits queued requests in order while a slot is free and the plan's device bytes
 //      (pe_plan_bytes_estimate) fit in what is left of the memory budget,
-//   2. advances every live solve by up to `chunk_steps` range steps with one batched march
-//      (one kernel launch per grid size, one CTA per solve, each with its own step count),
+//   2. advances every live solve with one batched march (one kernel launch per grid size,
+//      each with its own step count): the costliest kind of request live by `chunk_steps`
+//      range steps, cheaper ones by proportionally more (pacing, pe_server_set_pacing),
 //   3. retires the solves that reached their range: reads field and TL rows to host memory
 //      and frees the plan, so the next queued requests can be admitted.
 // A request that arrives while others are on the GPU joins them at the next step; all live
@@ -158,6 +159,7 @@ struct Result {
 struct pe_server {
   size_t budget = 0, in_use = 0, peak = 0;
   int max_live = 0, chunk = 0, peak_live = 0;
+  int max_weight = 64;  // pacing: a small grid marches up to this many chunks per step
   void* stream = nullptr;
   unsigned long long next_id = 1;
   std::deque<std::unique_ptr<Request>> queue;
@@ -180,6 +182,13 @@ constexpr double kLowSigma = 10.0;      // sigma = k0 dr below which orders are 
 constexpr double kRhoLow = 0.3;
 constexpr double kRhoConverge = 0.98;  // above: the series does not converge
 constexpr int kMaxRestarts = 8;
+
+// GPU work of one range step of a request, up to a constant: its transform count per step
+// (1 + p (terms - 1) at most) times the work of one transform of L = N + 1 points (L log2 L)
+double step_cost(const pe_request& r) {
+  const double L = double(r.N) + 1.0;
+  return L * std::log2(L) * (1.0 + double(r.pade_order) * double(std::max(r.neumann_terms - 1, 0)));
+}
 
 // Adapt a request at admission (see the file comment); false + message if it cannot converge.
 bool admit_adapt(Request* q, Result* res, std::string* err) {
@@ -306,6 +315,13 @@ pe_status pe_server_create(pe_server** out, size_t hbm_budget_bytes, int max_liv
   return PE_OK;
 }
 
+pe_status pe_server_set_pacing(pe_server* s, int max_weight) {
+  if (!s) return PE_ERR_ARG;
+  if (max_weight < 1 || max_weight > 4096) return sfail(s, PE_ERR_ARG, "max_weight must be in [1, 4096]");
+  s->max_weight = max_weight;
+  return PE_OK;
+}
+
 void pe_server_destroy(pe_server* s) {
   if (!s) return;
   for (auto& l : s->live) pe_plan_destroy(l.plan);
@@ -369,14 +385,20 @@ pe_status pe_server_step(pe_server* s, int* live_out, int* queued_out, int* comp
     s->live.push_back(std::move(l));
   }
   s->peak_live = std::max(s->peak_live, int(s->live.size()));
-  // 2. one batched march of every live solve
+  // 2. one batched march of every live solve.  Pacing: the grid sizes march as concurrent
+  //    launches, and the step lasts as long as the slowest, so a request of the costliest kind
+  //    live marches `chunk` steps and a cheaper one w chunks, w = that cost over its own (at
+  //    most max_weight): small grids are not held to the pace of the largest.
   int completed = 0;
   if (!s->live.empty()) {
     std::vector<pe_plan*> plans;
     std::vector<int> steps;
+    double cmax = 0.0;
+    for (auto& l : s->live) cmax = std::max(cmax, step_cost(l.req->r));
     for (auto& l : s->live) {
+      const double w = std::min(double(s->max_weight), std::max(1.0, std::floor(cmax / step_cost(l.req->r))));
       plans.push_back(l.plan);
-      steps.push_back(int(std::min<long long>(s->chunk, l.req->r.steps - l.done)));
+      steps.push_back(int(std::min<long long>((long long)(double(s->chunk) * w), l.req->r.steps - l.done)));
     }
     pe_status st = pe_march_batch_steps(plans.data(), steps.data(), int(plans.size()));
     if (st != PE_OK) return sfail(s, st, pe_last_error(plans[0]));

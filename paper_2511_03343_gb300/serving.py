@@ -60,16 +60,18 @@ def _depth_summary(depth, points: int = 24) -> Dict:
 def replay(trace: List[Dict], hbm_budget: float, chunk_steps: int = 50, tl_every: int = 10,
            range_scale: float = 1.0, max_live: int = 1024, stream=None, keep_results: bool = False,
            admit: int = sssp.ADMIT_MINIMAX_C0 | sssp.ADMIT_CONVERGENT_ORDER, keep_ids=None,
-           record_params: bool = False):
+           record_params: bool = False, pacing: int = 64):
     """Replay ``trace`` against a fresh server; returns latency / throughput figures.  ``admit``
     are the server's admission adaptations (default: minimax reference sound speed and a Pade
     order at which the Neumann series converges); ``keep_results`` also returns, per request,
     (field, TL rows, solve, (k0, n2 scale, Pade order) it was marched with); ``keep_ids`` keeps
     those only for the given trace ids; ``record_params`` returns every completed request's
-    (k0, n2 scale, Pade order) under "params"."""
+    (k0, n2 scale, Pade order) under "params"; ``pacing``: the server's pacing limit (a cheaper
+    request marches up to that many chunks per step; 1 = lockstep)."""
     keep = None if keep_ids is None else set(keep_ids)
     keep_results = keep_results or keep is not None
     srv = sssp.Server(int(hbm_budget), max_live=max_live, chunk_steps=chunk_steps, stream=stream)
+    srv.set_pacing(pacing)
     order = sorted(range(len(trace)), key=lambda i: trace[i]["t_arrival"])
     pending = list(order)
     running = {}     # id -> (trace index, arrival wall time)

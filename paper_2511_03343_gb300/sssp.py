@@ -87,6 +87,7 @@ _SIGNATURES = {
     "pe_gemm_batch_destroy": (None, [_vp]),
     "pe_plan_bytes_estimate": (_sz, [_i, _i, _i, ctypes.c_longlong]),
     "pe_server_create": (_i, [ctypes.POINTER(_vp), _sz, _i, _i, _vp]),
+    "pe_server_set_pacing": (_i, [_vp, _i]),
     "pe_server_destroy": (None, [_vp]),
     "pe_server_error": (ctypes.c_char_p, [_vp]),
     "pe_server_submit": (_i, [_vp, _vp, ctypes.POINTER(ctypes.c_ulonglong)]),
@@ -453,6 +454,11 @@ class Server:
             self.close()
         except Exception:
             pass
+
+    def set_pacing(self, max_weight: int):
+        """Pacing limit: a cheaper request marches up to ``max_weight`` chunks per step (1: every
+        request one chunk, in lockstep with the costliest)."""
+        self._c(lib().pe_server_set_pacing(self._s, int(max_weight)))
 
     def submit(self, solve, tl_every: int = 0, steps: Optional[int] = None, admit: int = 0) -> int:
         """Queue an ``inputs.Solve``; returns the request id.  ``admit``: ADMIT_* bits."""

@@ -677,11 +677,12 @@ def test_dst1_batch_equals_single(sssp, N, count):
     pl.close()
 
 
-@pytest.mark.parametrize("N", [511, 8191])
+@pytest.mark.parametrize("N", [511, 8191, 16383])
 def test_absorbing_layer(sssp, N):
     """Complex n^2 (Section 3.1's complex absorbing potential) in the bottom 20 % of a Munk guide:
-    the march matches the oracle and the field's norm decreases (energy leaves through the layer)."""
-    s = inputs.munk(N=N, freq=60.0 if N < 4096 else 100.0, dr=25.0, steps=40 if N < 4096 else 6)
+    the march matches the oracle and the field's norm decreases (energy leaves through the layer).
+    N = 8191 runs the 8-CTA cluster kernel with a complex profile, N = 16383 the 16-CTA one."""
+    s = inputs.munk(N=N, freq=60.0 if N < 4096 else 100.0, dr=25.0, steps=40 if N < 4096 else (6 if N < 16383 else 3))
     z = s.z
     za = 0.8 * s.H
     n2 = s.profiles[0][1].astype(np.complex128) + 1j * 0.02 * np.clip((z - za) / (s.H - za), 0.0, None) ** 2
@@ -892,6 +893,46 @@ def test_server_cancel_running(sssp):
         pl.close()
     with pytest.raises(sssp.PEError, match="cancelled"):
         srv.take(ids[1])
+    srv.close()
+
+
+def test_server_pacing_lets_small_grids_finish_first(sssp):
+    """Pacing: a cheap request (N = 255) beside a costly one (N = 4095, 24x the work per step)
+    marches 24 chunks per server step, so it finishes in the second step instead of the 40th
+    (lockstep, pacing 1); both results equal marching alone, bit for bit, either way."""
+    small = inputs.munk(N=255, freq=40.0, dr=25.0, steps=400)
+    big = inputs.munk(N=4095, freq=50.0, dr=50.0, steps=100)
+    ref = []
+    for s in (small, big):
+        pl = sssp.plan_for(s)
+        pl.march(s.steps)
+        ref.append(pl.read_field())
+        pl.close()
+
+    def run(pacing):
+        srv = sssp.Server(hbm_budget_bytes=2_000_000_000, max_live=4, chunk_steps=10)
+        srv.set_pacing(pacing)
+        a, b = srv.submit(small, tl_every=0), srv.submit(big, tl_every=0)
+        n, small_done = 0, None
+        while srv.state(a) < 2 or srv.state(b) < 2:
+            srv.step()
+            n += 1
+            if small_done is None and srv.state(a) == 2:
+                small_done = n
+        fa, _ = srv.take(a)
+        fb, _ = srv.take(b)
+        srv.close()
+        return small_done, n, fa, fb
+
+    paced = run(64)
+    lock = run(1)
+    assert paced[:2] == (2, 10), paced[:2]
+    assert lock[:2] == (40, 40), lock[:2]
+    for got in (paced, lock):
+        assert np.array_equal(got[2], ref[0]) and np.array_equal(got[3], ref[1])
+    srv = sssp.Server(hbm_budget_bytes=1_000_000, max_live=1, chunk_steps=1)
+    with pytest.raises(sssp.PEError):
+        srv.set_pacing(0)
     srv.close()
 
 
