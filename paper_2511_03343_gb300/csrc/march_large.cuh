@@ -47,6 +47,12 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
   return s;
 }
 
+// A hint that moves the 128-byte line holding p into the L2 (no registers held; p is always an
+// element of the arrays the pass reads).  Operands are fetched this way a tile before their
+// register loads -- pass A: the sources of tile c + 2 during tile c; pass B: the sink operands of
+// tile + 1 during tile -- so those loads find their data in the L2 instead of waiting for HBM.
+__device__ __forceinline__ void l2_prefetch(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // Tables of the two-pass transform: per-pass Stockham twiddles of the P- and Q-point FFTs
 // and w_{2L}^q, q in [0, 2L), each as a hi + lo pair of floats (float-float): a twiddle's
 // FP32 representation error is the same in every transform, so it adds up coherently over
@@ -205,6 +211,22 @@ __device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC
     }
     __syncthreads();
     if (c + 1 < NA) loadA(c + 1);
+    if (c + 2 < NA) {  // the 16-point lines of tile c + 2's sources, one line per thread
+      constexpr int LPR = TC / 16;  // lines per row of the tile
+      const int c2 = c + 2;
+      const int cb2 = c2 < NA - 1 ? c2 * TC : QH - TC + 1;
+      const int n1 = t / LPR, col0 = cb2 + 16 * (t % LPR);
+      int lo, hi;
+      if (n1 < P / 2) {
+        lo = Q * n1 + col0;
+        hi = lo + 15;
+      } else {
+        hi = 2 * L - Q * n1 - col0;
+        lo = hi - 15;
+      }
+      src.l2(lo < 1 ? 1 : lo);
+      src.l2(hi > L - 1 ? L - 1 : hi);
+    }
     const float2* F = tfft<C::LOG2P, C::RSP, 1>(bufA, bufB, twP);
 #pragma unroll
     for (int q = 0; q < PT; ++q) {
@@ -280,6 +302,22 @@ __device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC
       if (target(tile, q, tg, ng)) snk.prefetch(q, tg);
     }
     if (tile + 1 < NBT) loadB(tile + 1);
+    if (SNK::kL2 && tile + 1 < NBT) {  // the lines of tile + 1's sink operands, one per thread
+      constexpr int LPK = TR / 16;          // lines per output column k2 and side
+      constexpr int NL1 = (Q / 2) * LPK;    // lines per side (own rows, partner rows)
+      const int side = t / NL1, i = t % NL1, j2 = i / LPK;
+      const int k0 = rowof(tile + 1, 16 * (i % LPK));
+      int lo, hi;
+      if (side == 0) {
+        lo = k0 + P * j2;
+        hi = lo + 15;
+      } else {
+        hi = P - k0 + P * j2;
+        lo = hi - 15;
+      }
+      snk.l2(lo < 0 ? 0 : lo);
+      snk.l2(hi > L - 1 ? L - 1 : hi);
+    }
     const float2* F = tfft<C::LOG2Q, C::RSQ, 1>(bufA, bufB, twQ);
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
@@ -311,6 +349,7 @@ __device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC
 struct SrcArr {  // x_m = a[m]
   const float2* a;
   __device__ __forceinline__ float2 operator()(int m, bool) const { return a[m]; }
+  __device__ __forceinline__ void l2(int m) const { l2_prefetch(a + m); }
 };
 struct SrcV {  // x_m = V_m a[m] (V real, or V + i Vi)
   const float2* a;
@@ -319,6 +358,11 @@ struct SrcV {  // x_m = V_m a[m] (V real, or V + i Vi)
   __device__ __forceinline__ float2 operator()(int m, bool) const {
     const float2 x = a[m];
     return Vi ? cmul(make_float2(__ldg(V + m), __ldg(Vi + m)), x) : __ldg(V + m) * x;
+  }
+  __device__ __forceinline__ void l2(int m) const {
+    l2_prefetch(a + m);
+    l2_prefetch(V + m);
+    if (Vi) l2_prefetch(Vi + m);
   }
 };
 struct SrcStage {  // x_m = t0_m = A_m y_m; on the first visit also t0[m] = w[m] = x_m
@@ -334,22 +378,34 @@ struct SrcStage {  // x_m = t0_m = A_m y_m; on the first visit also t0[m] = w[m]
     }
     return v;
   }
+  __device__ __forceinline__ void l2(int m) const {
+    l2_prefetch(A + m);
+    l2_prefetch(y + m);
+  }
 };
 struct SrcScaled {  // x_m = s y_m
   const float2* y;
   float s;
   __device__ __forceinline__ float2 operator()(int m, bool) const { return s * y[m]; }
+  __device__ __forceinline__ void l2(int m) const { l2_prefetch(y + m); }
 };
 // A sink takes put(q, k, S_k) for its q-th output of a tile; prefetch(q, k) is called for the
 // same (q, k) before the tile's FFT, so a sink can load its own operands early.
 struct SnkArr {
+  static constexpr bool kL2 = false;  // write-only: no operands to fetch
   float2* a;
+  __device__ __forceinline__ void l2(int) {}
   __device__ __forceinline__ void prefetch(int, int) {}
   __device__ __forceinline__ void put(int, int k, float2 v) { a[k] = v; }
 };
 // The partial sum w_j = t_0 + t_1 + .. is kept itself (not t_1 + .. beside t_0), so a term
 // streams B and w, and the stage's combine reads t_0 once: y <- R y + beta (w - t_0).
 struct SnkTerm {  // t_m = B_k S_k: w += t_m, X = t_m, and the norm partials of the stop test
+  static constexpr bool kL2 = true;
+  __device__ __forceinline__ void l2(int k) {
+    l2_prefetch(B + k);
+    l2_prefetch(w + k);
+  }
   const float2* B;
   float2* w;
   float2* X;
@@ -373,8 +429,10 @@ struct SnkTerm {  // t_m = B_k S_k: w += t_m, X = t_m, and the norm partials of 
   }
 };
 struct SnkTL {  // TL row: -10 log10 |u_n|^2 + 10 log10 r, n = 1..N
+  static constexpr bool kL2 = false;
   float* row;
   float lr;
+  __device__ __forceinline__ void l2(int) {}
   __device__ __forceinline__ void prefetch(int, int) {}
   __device__ __forceinline__ void put(int, int k, float2 v) {
     if (k >= 1) row[k - 1] = fmaf(-10.f, log10f(cabs2(v)), lr);
@@ -500,10 +558,13 @@ __global__ void __launch_bounds__(kLargeNT, 1)
 struct SrcIn {  // x_m = in[m - 1]
   const float2* in;
   __device__ __forceinline__ float2 operator()(int m, bool) const { return in[m - 1]; }
+  __device__ __forceinline__ void l2(int m) const { l2_prefetch(in + m - 1); }
 };
 struct SnkScaled {
+  static constexpr bool kL2 = false;
   float2* out;
   float s;
+  __device__ __forceinline__ void l2(int) {}
   __device__ __forceinline__ void prefetch(int, int) {}
   __device__ __forceinline__ void put(int, int k, float2 v) { out[k] = s * v; }
 };
