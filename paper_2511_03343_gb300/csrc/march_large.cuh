@@ -49,8 +49,9 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
 
 // A hint that moves the 128-byte line holding p into the L2 (no registers held; p is always an
 // element of the arrays the pass reads).  Operands are fetched this way a tile before their
-// register loads -- pass A: the sources of tile c + 2 during tile c; pass B: the sink operands of
-// tile + 1 during tile -- so those loads find their data in the L2 instead of waiting for HBM.
+// register loads -- pass A: the sources of tile 1 before tile 0, of tile c + 2 during tile c;
+// pass B: the sink operands of tile 0 before the pass, of tile + 1 during tile -- so those
+// loads find their data in the L2 instead of waiting for HBM.
 __device__ __forceinline__ void l2_prefetch(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 // Tables of the two-pass transform: per-pass Stockham twiddles of the P- and Q-point FFTs
@@ -201,6 +202,22 @@ __device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC
       pre[q] = z;
     }
   };
+  auto l2A = [&](int c2) {  // the 16-point lines of tile c2's sources, one line per thread
+    constexpr int LPR = TC / 16;  // lines per row of the tile
+    const int cb2 = c2 < NA - 1 ? c2 * TC : QH - TC + 1;
+    const int n1 = t / LPR, col0 = cb2 + 16 * (t % LPR);
+    int lo, hi;
+    if (n1 < P / 2) {
+      lo = Q * n1 + col0;
+      hi = lo + 15;
+    } else {
+      hi = 2 * L - Q * n1 - col0;
+      lo = hi - 15;
+    }
+    src.l2(lo < 1 ? 1 : lo);
+    src.l2(hi > L - 1 ? L - 1 : hi);
+  };
+  if (NA > 1) l2A(1);
   loadA(0);
   for (int c = 0; c < NA; ++c) {
     const int cb = c < NA - 1 ? c * TC : QH - TC + 1;
@@ -211,22 +228,7 @@ __device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC
     }
     __syncthreads();
     if (c + 1 < NA) loadA(c + 1);
-    if (c + 2 < NA) {  // the 16-point lines of tile c + 2's sources, one line per thread
-      constexpr int LPR = TC / 16;  // lines per row of the tile
-      const int c2 = c + 2;
-      const int cb2 = c2 < NA - 1 ? c2 * TC : QH - TC + 1;
-      const int n1 = t / LPR, col0 = cb2 + 16 * (t % LPR);
-      int lo, hi;
-      if (n1 < P / 2) {
-        lo = Q * n1 + col0;
-        hi = lo + 15;
-      } else {
-        hi = 2 * L - Q * n1 - col0;
-        lo = hi - 15;
-      }
-      src.l2(lo < 1 ? 1 : lo);
-      src.l2(hi > L - 1 ? L - 1 : hi);
-    }
+    if (c + 2 < NA) l2A(c + 2);
     const float2* F = tfft<C::LOG2P, C::RSP, 1>(bufA, bufB, twP);
 #pragma unroll
     for (int q = 0; q < PT; ++q) {
@@ -245,6 +247,23 @@ __device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC
   // (rows 0 and P/2 are their own partners: only their first Q/2 outputs are kept).
   constexpr int NBT = (P / 2) / TR + 1;  // the last tile ends at row P/2 (its other rows: done)
   auto rowof = [&](int tile, int sl) { return (tile < NBT - 1 ? tile * TR : P / 2 - TR + 1) + sl; };
+  auto l2B = [&](int tile) {  // the lines of a tile's sink operands, one per thread
+    constexpr int LPK = TR / 16;          // lines per output column k2 and side
+    constexpr int NL1 = (Q / 2) * LPK;    // lines per side (own rows, partner rows)
+    const int side = t / NL1, i = t % NL1, j2 = i / LPK;
+    const int k0 = rowof(tile, 16 * (i % LPK));
+    int lo, hi;
+    if (side == 0) {
+      lo = k0 + P * j2;
+      hi = lo + 15;
+    } else {
+      hi = P - k0 + P * j2;
+      lo = hi - 15;
+    }
+    snk.l2(lo < 0 ? 0 : lo);
+    snk.l2(hi > L - 1 ? L - 1 : hi);
+  };
+  if (SNK::kL2) l2B(0);
   auto loadB = [&](int tile) {
 #pragma unroll
     for (int q = 0; q < PH; ++q) {  // own stored half, columns [0, Q/2)
@@ -302,22 +321,7 @@ __device__ void dst_global(float2* W, const LargeTabs& tb, float2* sm, const SRC
       if (target(tile, q, tg, ng)) snk.prefetch(q, tg);
     }
     if (tile + 1 < NBT) loadB(tile + 1);
-    if (SNK::kL2 && tile + 1 < NBT) {  // the lines of tile + 1's sink operands, one per thread
-      constexpr int LPK = TR / 16;          // lines per output column k2 and side
-      constexpr int NL1 = (Q / 2) * LPK;    // lines per side (own rows, partner rows)
-      const int side = t / NL1, i = t % NL1, j2 = i / LPK;
-      const int k0 = rowof(tile + 1, 16 * (i % LPK));
-      int lo, hi;
-      if (side == 0) {
-        lo = k0 + P * j2;
-        hi = lo + 15;
-      } else {
-        hi = P - k0 + P * j2;
-        lo = hi - 15;
-      }
-      snk.l2(lo < 0 ? 0 : lo);
-      snk.l2(hi > L - 1 ? L - 1 : hi);
-    }
+    if (SNK::kL2 && tile + 1 < NBT) l2B(tile + 1);
     const float2* F = tfft<C::LOG2Q, C::RSQ, 1>(bufA, bufB, twQ);
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
