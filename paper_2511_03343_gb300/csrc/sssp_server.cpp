@@ -34,6 +34,7 @@
 //                        its starter one order lower, up to 8 times.
 // The values used are reported by pe_server_request_params.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -398,7 +399,8 @@ pe_status pe_server_step(pe_server* s, int* live_out, int* queued_out, int* comp
     for (auto& l : s->live) {
       const double w = std::min(double(s->max_weight), std::max(1.0, std::floor(cmax / step_cost(l.req->r))));
       plans.push_back(l.plan);
-      steps.push_back(int(std::min<long long>((long long)(double(s->chunk) * w), l.req->r.steps - l.done)));
+      const long long n = std::min<long long>((long long)(double(s->chunk) * w), l.req->r.steps - l.done);
+      steps.push_back(int(std::min<long long>(n, INT_MAX)));
     }
     pe_status st = pe_march_batch_steps(plans.data(), steps.data(), int(plans.size()));
     if (st != PE_OK) return sfail(s, st, pe_last_error(plans[0]));
