@@ -192,3 +192,31 @@ def test_admission_radius_estimate_matches_dense_eigenvalues(L):
         checked.append(max(np.max(np.abs(np.linalg.eigvals(
             -bj * ((2.0 / (N + 1)) * S @ np.diag(1.0 / (1.0 + bj * g.lam)) @ S) @ np.diag(V)))) for bj in plan.b))
     assert max(checked) > 1.0 and min(checked) < 1.0  # both sides of the decision were exercised
+
+
+def test_server_pacing_host_checks(L):
+    """The serving loop's pacing limit is validated on the host (no GPU work)."""
+    from paper_2511_03343_gb300 import sssp
+    srv = sssp.Server(hbm_budget_bytes=10_000_000, max_live=4, chunk_steps=10)
+    srv.set_pacing(1)
+    srv.set_pacing(4096)
+    for bad in (0, -3, 4097):
+        with pytest.raises(sssp.PEError) as e:
+            srv.set_pacing(bad)
+        assert e.value.status == sssp.PE_ERR_ARG
+    srv.close()
+    assert sssp.lib().pe_server_set_pacing(None, 8) == sssp.PE_ERR_ARG
+
+
+def test_shape_entry_points_reject_null_plans(L):
+    """The shape and autotuner entry points check their pointers before any device work."""
+    import ctypes
+    from paper_2511_03343_gb300 import sssp
+    lib = sssp.lib()
+    n, u = ctypes.c_int(7), ctypes.c_int(7)
+    assert lib.pe_plan_set_cluster_shape(None, 8, 0) == sssp.PE_ERR_ARG
+    assert lib.pe_plan_get_cluster_shape(None, ctypes.byref(n), ctypes.byref(u)) == sssp.PE_ERR_ARG
+    assert lib.pe_plan_set_shape(None, 8) == sssp.PE_ERR_ARG
+    assert lib.pe_march_batch_autotune(None, 1, 4, None, None, None) == sssp.PE_ERR_ARG
+    assert sssp.SHAPE_NAMES[3:] == ("cluster8_pull", "cluster8_push", "cluster16_pull", "cluster16_push")
+    assert len(sssp.SHAPE_NAMES) == 7  # PE_AUTOTUNE_SHAPES in include/sssp.h
