@@ -1244,8 +1244,8 @@ pe_status pe_plan_set_cluster_shape(pe_plan* p, int ncta, int push) {
   if (push < -1 || push > 1) return fail(p, PE_ERR_ARG, "push must be -1 (default), 0 (pull) or 1 (push)");
   if (p->user_bc != PE_BC_DIRICHLET || !sssp_cluster::shape_supported(p->log2L, ncta, push))
     return fail(p, PE_ERR_ARG,
-                "cluster shapes: Dirichlet grids with N + 1 in [4096, 32768]; ncta 0, the size's default or "
-                "16 for N + 1 in {8192, 16384}");
+                "cluster shapes: Dirichlet grids with N + 1 in [4096, 32768]; ncta 0 (the size's default), "
+                "8 (N + 1 <= 16384) or 16 (N + 1 >= 8192)");
   int a = 0, b = 0;
   PE_CUDA(p, sssp_cluster::max_active_clusters(p->log2L, false, &a, ncta, push));
   PE_CUDA(p, sssp_cluster::max_active_clusters(p->log2L, true, &b, ncta, push));
